@@ -1,0 +1,149 @@
+"""Pins for the seeded input generators (colour codes, DEMs, sampler, schedules).
+
+Facts from Sec. II.A: the triangular colour code has n qubits, (n-1)/2 plaquettes, even-weight
+commuting plaquettes, n-1 independent generators and k = 1; for odd distance d it has
+n = (3d^2+1)/4 qubits. Eq. 1 gives s = H e mod 2.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_15743_gb300 import dem as D
+from tests.helpers import gf2_nullspace, gf2_rank
+
+
+@pytest.mark.parametrize("d", [3, 5, 7, 9, 11, 13, 15])
+def test_colour_code_counts(d):
+    H, logical, coords = D.color_code_666(d)
+    n = H.ncols
+    assert n == (3 * d * d + 1) // 4
+    assert H.nrows == (n - 1) // 2
+    w = np.diff(H.rowptr)
+    assert set(w.tolist()) <= {4, 6}
+    assert (w == 4).sum() == 3 * (d - 1) // 2, "boundary squares"
+    assert (w == 6).sum() == H.nrows - 3 * (d - 1) // 2, "bulk hexagons"
+    col = np.bincount(H.colidx, minlength=n)
+    assert col.max() <= 3 and col.min() >= 1
+    assert len(logical) == d
+
+
+@pytest.mark.parametrize("d", [3, 5, 7, 9, 11])
+def test_colour_code_algebra(d):
+    H, logical, _ = D.color_code_666(d)
+    A = H.to_dense().astype(np.int64)
+    n = A.shape[1]
+    assert not ((A @ A.T) % 2).any(), "plaquettes must overlap evenly (X and Z generators commute)"
+    r = gf2_rank(A)
+    assert r == (n - 1) // 2
+    assert n - 2 * r == 1, "k = 1 logical qubit"
+    Lv = np.zeros(n, np.uint8)
+    Lv[logical] = 1
+    assert not (A @ Lv % 2).any(), "logical commutes with every plaquette"
+    assert gf2_rank(np.vstack([A, Lv])) == r + 1, "logical is not a product of plaquettes"
+
+
+@pytest.mark.parametrize("d", [3, 5, 7])
+def test_colour_code_distance(d):
+    """Minimum weight of x in ker(H) with odd overlap with the logical equals d."""
+    H, logical, _ = D.color_code_666(d)
+    A = H.to_dense()
+    N = gf2_nullspace(A)
+    Lv = np.zeros(A.shape[1], np.uint8)
+    Lv[logical] = 1
+    k = N.shape[0]
+    best = 10 ** 9
+    chunk = 1 << 14
+    for start in range(0, 1 << k, chunk):
+        idx = np.arange(start, min(1 << k, start + chunk), dtype=np.int64)
+        coeff = ((idx[:, None] >> np.arange(k)) & 1).astype(np.uint8)
+        X = (coeff.astype(np.int64) @ N.astype(np.int64)) % 2
+        odd = (X @ Lv) % 2 == 1
+        if odd.any():
+            best = min(best, int(X[odd].sum(axis=1).min()))
+    assert best == d
+
+
+def test_code_capacity_workload_shape():
+    dm = D.build_workload("cc666_d5_codecap")
+    assert (dm.m, dm.n, dm.H.nnz) == (9, 19, 42)
+    assert dm.L.nnz == 5
+    assert np.allclose(dm.priors, 0.05)
+
+
+def test_phenomenological_shape():
+    dm = D.build_workload("cc666_d9_pheno")
+    assert dm.m == 30 * 10 and dm.n == 61 * 9 + 30 * 9
+    assert dm.H.nnz == 1944
+    rowdeg = np.diff(dm.H.rowptr)
+    coldeg = np.bincount(dm.H.colidx, minlength=dm.n)
+    assert rowdeg.max() <= 8
+    # the final (perfect) layer's detectors see only the last noisy round's measurement error
+    assert (rowdeg[:30 * 9] >= 5).all() and (rowdeg[30 * 9:] == 1).all()
+    assert coldeg.max() == 3
+    assert (coldeg[61 * 9:] == 2).all()
+
+
+def test_phenomenological_matches_measurement_record():
+    """Simulate the noisy plaquette outcomes round by round and XOR consecutive rounds."""
+    d, R = 5, 4
+    dm = D.phenomenological_dem(d, R, 0.02, 0.03)
+    Hc, logical, _ = D.color_code_666(d)
+    A = Hc.to_dense().astype(np.int64)
+    nq, mp = A.shape[1], A.shape[0]
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        data = rng.random((R, nq)) < 0.1
+        meas = rng.random((R, mp)) < 0.1
+        frame = np.zeros(nq, np.int64)
+        prev = np.zeros(mp, np.int64)
+        det = []
+        for r in range(R + 1):
+            if r < R:
+                frame = (frame + data[r]) % 2
+            out = (A @ frame) % 2
+            if r < R:
+                out = (out + meas[r]) % 2
+            det.append((out + prev) % 2)
+            prev = out
+        det = np.concatenate(det)
+        e = np.concatenate([data.reshape(-1), meas.reshape(-1)]).astype(np.uint8)[None, :]
+        s, o = D.syndromes_of(dm, e)
+        assert np.array_equal(D.unpack_bits(s, dm.m)[0], det)
+        obs = int(frame[logical].sum() % 2)
+        assert int(D.unpack_bits(o, 1)[0, 0]) == obs
+
+
+def test_sampler_parity_and_rate():
+    dm = D.build_workload("cc666_d9_pheno")
+    syn, obs, err = D.sample(dm, 3000, 11, return_errors=True, chunk=1000)
+    A = dm.H.to_dense().astype(np.int64)
+    Lm = dm.L.to_dense().astype(np.int64)
+    s_ref = (err.astype(np.int64) @ A.T) % 2
+    o_ref = (err.astype(np.int64) @ Lm.T) % 2
+    assert np.array_equal(D.unpack_bits(syn, dm.m), s_ref)
+    assert np.array_equal(D.unpack_bits(obs, dm.k), o_ref)
+    rate = err.mean()
+    assert abs(rate - 0.01) < 5 * np.sqrt(0.01 * 0.99 / err.size)
+    # same seed, same stream
+    syn2, obs2 = D.sample(dm, 3000, 11, chunk=1000)
+    assert np.array_equal(syn, syn2) and np.array_equal(obs, obs2)
+
+
+def test_pack_roundtrip_and_padding():
+    rng = np.random.default_rng(0)
+    for nb in [1, 31, 32, 33, 300, 819]:
+        bits = (rng.random((7, nb)) < 0.5).astype(np.uint8)
+        p = D.pack_bits(bits)
+        assert p.shape == (7, (nb + 31) // 32)
+        assert np.array_equal(D.unpack_bits(p, nb), bits)
+        if nb % 32:
+            assert (p[:, -1] >> (nb % 32) == 0).all()
+
+
+def test_schedules_are_permutations():
+    P = D.schedules(819, 16, 3)
+    assert P.shape == (16, 819)
+    for row in P:
+        assert np.array_equal(np.sort(row), np.arange(819))
+    assert len({tuple(r) for r in P}) == 16
+    nat = D.schedules(19, 1, 0, natural=True)
+    assert np.array_equal(nat[0], np.arange(19))

@@ -1,0 +1,51 @@
+"""The oracle's pins are strong enough: each planted mistake makes at least one pin fail.
+
+Every case below edits a copy of the oracle's C source (a dropped term, a flipped sign, a wrong
+index, a transposed operand), compiles it on the CPU, and runs the pin suites against that build
+in a child pytest process. The child run must fail. The shipped oracle is untouched.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "syndrome sign dropped": ("int neg = s[c];", "int neg = 0;"),
+    "message sign test inverted": ("if (x < 0.0f) neg ^= 1;", "if (x > 0.0f) neg ^= 1;"),
+    "own edge kept in the check minimum": ("        if (e == own) continue;\n        float x", "        float x"),
+    "own message kept in the exclusion sum": ("        if (k2 != k) a = a + mcv[k2];\n      msg[g->col_edge[b + k]] = store_msg",
+                                              "        a = a + mcv[k2];\n      msg[g->col_edge[b + k]] = store_msg"),
+    "scaling factor not applied": ("float mag = alpha * mn;", "float mag = mn;"),
+    "posterior without the prior": ("    float L = lam[v];                       /* posterior */",
+                                    "    float L = 0.0f;                         /* posterior */"),
+    "schedule ignored": ("    int v = (int)perm[idx];\n    int b = g->colptr[v], deg = g->colptr[v + 1] - b;\n    for (int k = 0; k < deg; ++k) {         /* check",
+                         "    int v = idx;\n    int b = g->colptr[v], deg = g->colptr[v + 1] - b;\n    for (int k = 0; k < deg; ++k) {         /* check"),
+    "prior LLR transposed": ("log((1.0 - priors[j]) / priors[j])", "log(priors[j] / (1.0 - priors[j]))"),
+    "heaviest candidate chosen": ("if (chosen < 0 || W < bestW) { bestW = W; chosen = i; }",
+                                  "if (chosen < 0 || W > bestW) { bestW = W; chosen = i; }"),
+    "average not normalised": ("(!isfinite(post[j]) ? post[j] : (nrm == 0.0f ? 0.0f : post[j] / nrm))",
+                               "(!isfinite(post[j]) ? post[j] : post[j])"),
+    "LSD grows along the worst column": ("if (w->col_root[j] < 0 && (best < 0 || ranks_before(soft, j, best))) best = j;",
+                                         "if (w->col_root[j] < 0 && (best < 0 || ranks_before(soft, best, j))) best = j;"),
+    "LSD right-hand side misread": ("int val = w->mat[pr * wd + ncol];", "int val = w->mat[pr * wd + 0];"),
+    "correction limit off by one": ("if (nconv >= M) { t_stop = t; break; }", "if (nconv > M) { t_stop = t; break; }"),
+}
+
+PIN_SUITES = ["tests/test_oracle_bp.py", "tests/test_oracle_decoder.py", "tests/test_oracle_lsd.py"]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) >= 1, f"mutation site not found: {name}"
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_mut.so"))
+    env = dict(os.environ, VIBE_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PIN_SUITES],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
