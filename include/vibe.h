@@ -1,0 +1,160 @@
+/*
+ * vibe.h -- C ABI of the GB300 (sm_103a) VibeLSD decoding library, libvibe.so.
+ *
+ * VibeLSD (arXiv 2508.15743): a batch of syndromes of a detector error model (check matrix H,
+ * logical matrix L, priors p_j; Sec. II.B, Eq. 1) is decoded by an ensemble of K serial-schedule
+ * min-sum BP members (Sec. III.A-B, Appendix A Algorithm 1), each with its own permutation of the
+ * columns (Sec. III.D.1). Once M members converge the rest stop and the most likely candidate is
+ * kept (Sec. III.D.2 steps 3-4); when none converges, the normalised average of the members' LLRs
+ * (Sec. III.D.2 step 5) drives LSD post-processing (Sec. III.C).
+ *
+ * Conventions for every entry point:
+ *  - All sizes are in elements. Bit-packed vectors are arrays of uint32 words with bit b of word w
+ *    holding entry 32*w + b; padding bits past the last entry must be zero on input and are zero
+ *    on output.
+ *  - Pointers named d_* are device pointers (cudaMalloc or equivalent, on the handle's device);
+ *    pointers named h_* or without a prefix are host pointers. The library never frees caller memory.
+ *  - Functions return VIBE_OK (0) or a negative VIBE_ERR_* code; vibe_last_error() then describes
+ *    the failure for the calling thread. Per-shot outcomes never fail a call: they go in
+ *    vibe_shot_stats.status.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ */
+#ifndef VIBE_H
+#define VIBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VIBE_OK 0
+#define VIBE_ERR_INVALID (-1) /* malformed matrix, bad sizes or parameters */
+#define VIBE_ERR_NOMEM (-2)   /* a device or host allocation failed */
+#define VIBE_ERR_CUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define VIBE_ERR_UNSUPPORTED (-4) /* valid input beyond this build's limits (see vibe_create) */
+
+#define VIBE_STATUS_OK 0
+#define VIBE_STATUS_UNSOLVABLE 1 /* syndrome outside the column span of H; correction is zero */
+
+/* Sparse binary matrix in CSR form, host memory; copied by vibe_create. colidx ascending, no
+ * duplicates within a row. */
+typedef struct {
+  int32_t nrows;
+  int32_t ncols;
+  const int32_t* rowptr; /* nrows + 1 entries, rowptr[0] = 0 */
+  const int32_t* colidx; /* rowptr[nrows] entries in [0, ncols) */
+} vibe_csr;
+
+/* Decoder parameters (Sec. III.D.1 steps 1-2 and 5; Algorithm 1 inputs). */
+typedef struct {
+  int32_t max_iter;  /* T: BP iterations per member, >= 1 */
+  float alpha;       /* min-sum scaling factor in (0, 1], applied to every check-to-variable message */
+  int32_t M;         /* correction limit, 1 <= M <= K and M <= 32 */
+  int32_t lsd_order; /* 0 = LSD-0; q > 0 searches the 2^q settings of the first q free columns of each
+                        cluster for the lowest prior weight (q <= 10) */
+  int32_t msg_fp16;  /* 0: FP32 messages; 1: FP16 storage of variable-to-check messages, FP32 arithmetic */
+  uint64_t seed;     /* seeds the schedules when vibe_create gets schedules == NULL */
+} vibe_params;
+
+/* Per-shot record, 12 bytes. */
+typedef struct {
+  uint8_t status;           /* VIBE_STATUS_* */
+  uint8_t lsd_invoked;      /* 1 if no member converged and LSD produced the correction */
+  uint8_t n_converged;      /* candidates kept: min(M, members converged when BP stopped) */
+  uint8_t chosen_member;    /* member whose correction was kept; 255 when LSD decided */
+  uint16_t iters;           /* iteration at which the ensemble stopped; T when fewer than M converged */
+  uint16_t largest_cluster; /* columns in the largest LSD cluster (0 without LSD) */
+  uint32_t n_clusters;      /* final LSD clusters (0 without LSD) */
+} vibe_shot_stats;
+
+/* Indices into the optional counters array of vibe_decode (uint64, accumulated, never reset). */
+#define VIBE_CNT_SHOTS 0       /* shots decoded */
+#define VIBE_CNT_FAILURES 1    /* shots whose L*e differs from the given observables */
+#define VIBE_CNT_LSD 2         /* shots sent to LSD */
+#define VIBE_CNT_PAIR_ITERS 3  /* BP sweeps executed, summed over (shot, member) pairs */
+#define VIBE_CNT_UNSOLVABLE 4
+#define VIBE_NUM_COUNTERS 8
+
+typedef struct vibe_handle vibe_handle;
+
+/*
+ * vibe_create -- offline setup (Sec. III.D.1).
+ *   H: m x n check matrix (detectors x mechanisms); L: k x n logical matrix (k <= 1024);
+ *   priors: n doubles p_j in (0, 0.5); the prior LLRs log((1-p)/p) are evaluated in double on the
+ *   host and rounded once to float.
+ *   K: ensemble size, 1..255. schedules: K x n uint32 permutations of 0..n-1 (member i processes
+ *   columns in the order schedules[i*n .. i*n+n-1]); NULL draws them on the device from params->seed
+ *   (member i: SplitMix64 started at seed + (i+1)*0xD1B54A32D192ED03, Durstenfeld shuffle taking
+ *   j = high 64 bits of next()*(k+1) for k = n-1 down to 1).
+ *   Uses the current CUDA device. Copies everything it is given; the device tables (CSR/CSC of H,
+ *   per-member dependency wavefronts, message images) stay resident until vibe_destroy.
+ *   Limits of this build (VIBE_ERR_UNSUPPORTED beyond them): n < 2^24, m < 2^24, every row of H has
+ *   at most 255 entries, every column at most 32, and one shot's BP state (messages, posteriors,
+ *   syndrome) must fit in 200 KB of shared memory.
+ *   Errors: VIBE_ERR_INVALID (NULL pointers, malformed CSR, a row with no entry, priors outside
+ *   (0, 0.5), bad K/params, schedules not permutations), VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
+ *   On error *out is set to NULL and nothing is leaked.
+ */
+int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int32_t K,
+                const uint32_t* schedules, const vibe_params* params, vibe_handle** out);
+
+/*
+ * vibe_decode -- online decoding of B shots (Sec. III.D.2), asynchronous on `stream`.
+ *   d_syndromes: B x ceil(m/32) words (device). Outputs (device, caller-owned):
+ *   d_corrections: B x ceil(n/32) words, the correction e with H e = s for solvable shots;
+ *   d_logical: B x ceil(k/32) words, L e mod 2 (may be NULL); d_stats: B records (may be NULL);
+ *   d_soft: B x n floats (may be NULL): the chosen member's final posterior LLRs, or for LSD shots
+ *   the normalised LLR average that ranked the columns;
+ *   d_observables: B x ceil(k/32) true logical flips (may be NULL) -- with d_counters, counts
+ *   shots whose L e differs; d_counters: VIBE_NUM_COUNTERS uint64 accumulators (may be NULL).
+ *   The handle's workspace is allocated on the first call and grown when a larger batch needs it;
+ *   calls with a batch no larger than an earlier one allocate nothing. Large batches run in chunks.
+ *   Calls on one handle must not overlap in time (the workspace is shared); use one handle per stream.
+ *   Errors: VIBE_ERR_INVALID (NULL handle/required pointer, B < 0), VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
+ *   B = 0 is a no-op.
+ */
+int vibe_decode(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
+                uint32_t* d_logical, vibe_shot_stats* d_stats, float* d_soft,
+                const uint32_t* d_observables, uint64_t* d_counters, void* stream);
+
+/*
+ * vibe_decode_host -- the same decoding with host buffers (pageable or pinned). Copies the
+ * syndromes (and observables) to the device, decodes, copies the results back and waits for the
+ * stream. Device staging buffers belong to the handle and grow like its workspace.
+ *   h_counters, if not NULL, receives this call's counters (not accumulated across calls).
+ */
+int vibe_decode_host(vibe_handle* h, const uint32_t* h_syndromes, int64_t B, uint32_t* h_corrections,
+                     uint32_t* h_logical, vibe_shot_stats* h_stats, const uint32_t* h_observables,
+                     uint64_t* h_counters, void* stream);
+
+/*
+ * vibe_get_wavefronts -- the dependency wavefronts built for one member (Sec. III.D.1 step 4):
+ *   level(v) = 1 + max{level(u) : u before v in the member's order and u, v share a check}, so the
+ *   columns of one level share no check and may be updated together with results identical to the
+ *   serial order. order_out: n column indices grouped by level (host); level_offsets_out: n + 1
+ *   entries, level l holds order_out[level_offsets_out[l] .. level_offsets_out[l+1]); *nlevels_out
+ *   the level count. Synchronous. Errors: VIBE_ERR_INVALID, VIBE_ERR_CUDA.
+ */
+int vibe_get_wavefronts(vibe_handle* h, int32_t member, uint32_t* order_out,
+                        uint32_t* level_offsets_out, int32_t* nlevels_out);
+
+/*
+ * vibe_profile -- start (enable != 0) or stop recording CUDA events around every kernel that
+ * vibe_decode launches on the caller's stream; clears the totals. vibe_profile_read waits for the
+ * last recorded event and returns the summed device time (ms) of the BP ensemble kernel and of the
+ * LSD kernel since the last vibe_profile call, and how many of each were launched.
+ */
+int vibe_profile(vibe_handle* h, int32_t enable);
+int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp_launches, int64_t* lsd_launches);
+
+/* vibe_destroy -- frees every device and host resource of the handle. NULL is accepted. */
+int vibe_destroy(vibe_handle* h);
+
+/* Message describing the calling thread's most recent error ("" if none). Owned by the library. */
+const char* vibe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIBE_H */

@@ -1,0 +1,204 @@
+// K0 -- Tanner-graph builder (offline setup, Sec. III.D.1).
+//
+// From the CSR of H it builds, on the device: the CSC of H (checks ascending per column), the packed
+// per-column edge table csc_ent used by the BP kernel, the padded message image (prior LLR of each
+// edge's column, +inf padding), and for every ensemble member the dependency wavefronts of its
+// serial schedule: level(v) = 1 + max{level(u) : u before v in the member's order, u and v share a
+// check}. Columns of one level touch disjoint checks, so updating a level in any order gives the
+// same floats as the serial order of Algorithm 1 (serial branch).
+#include "vibe_internal.cuh"
+
+namespace vibe {
+namespace {
+
+__global__ void k_col_count(const int32_t* __restrict__ colidx, int E, int32_t* __restrict__ cnt) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+    atomicAdd(&cnt[colidx[e]], 1);
+}
+
+// Exclusive scan of cnt[0..n) into out[0..n], one CTA (used once per handle).
+__global__ void k_scan_single(const int32_t* __restrict__ cnt, int n, int32_t* __restrict__ out) {
+  __shared__ int32_t part[1024];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < n ? cnt[i] : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      int add = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < n) out[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+// Scatter every edge into its column as (check << 8) | slot, slot = position inside the check row.
+__global__ void k_csc_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int m,
+                           const int32_t* __restrict__ colptr, int32_t* __restrict__ fill,
+                           uint32_t* __restrict__ packed) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    for (int e = rowptr[c]; e < rowptr[c + 1]; ++e) {
+      int v = colidx[e];
+      int pos = atomicAdd(&fill[v], 1);
+      packed[colptr[v] + pos] = ((uint32_t)c << 8) | (uint32_t)(e - rowptr[c]);
+    }
+  }
+}
+
+// Sort each column's entries by check (insertion sort, degree <= 32) and emit rowidx and csc_ent.
+__global__ void k_csc_finish(int n, int DP, const int32_t* __restrict__ colptr, uint32_t* __restrict__ packed,
+                             int32_t* __restrict__ rowidx, uint32_t* __restrict__ csc_ent) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int b = colptr[v], d = colptr[v + 1] - b;
+    for (int i = 1; i < d; ++i) {
+      uint32_t x = packed[b + i];
+      int j = i - 1;
+      while (j >= 0 && packed[b + j] > x) { packed[b + j + 1] = packed[b + j]; --j; }
+      packed[b + j + 1] = x;
+    }
+    for (int k = 0; k < DP; ++k) {
+      uint32_t x = k < d ? packed[b + k] : 0u;
+      csc_ent[(size_t)v * DP + k] = x;
+      if (k < d) rowidx[b + k] = (int32_t)(x >> 8);
+    }
+  }
+}
+
+template <typename MT>
+__device__ __forceinline__ MT to_msg(float x);
+template <>
+__device__ __forceinline__ float to_msg<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __half to_msg<__half>(float x) { return __float2half_rn(x); }
+
+template <typename MT>
+__global__ void k_msg_init(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int m, int RP,
+                           const float* __restrict__ lam, MT* __restrict__ out) {
+  long long total = (long long)m * RP;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t / RP), slot = (int)(t % RP);
+    int deg = rowptr[c + 1] - rowptr[c];
+    float x = slot < deg ? lam[colidx[rowptr[c] + slot]] : __int_as_float(0x7f800000);
+    out[t] = to_msg<MT>(x);
+  }
+}
+
+// One thread per member: dependency levels of its schedule, then a stable counting sort into levels
+// and, inside each level, by column degree (lanes of a warp then see similar work).
+__global__ void k_levels(const uint32_t* __restrict__ perm, int n, int m, int K, const int32_t* __restrict__ colptr,
+                         const int32_t* __restrict__ rowidx, uint32_t* __restrict__ sched,
+                         uint32_t* __restrict__ lvl_off, int32_t* __restrict__ nlev, int32_t* __restrict__ scratch) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K) return;
+  size_t per = (size_t)m + 3 * (size_t)n + 1;
+  int32_t* last = scratch + per * i;       // m: level of the latest column seen at each check
+  int32_t* lev = last + m;                 // n
+  int32_t* cnt = lev + n;                  // n + 1
+  int32_t* tmp = cnt + n + 1;              // n
+  for (int c = 0; c < m; ++c) last[c] = -1;
+  const uint32_t* p = perm + (size_t)i * n;
+  int nl = 0;
+  for (int t = 0; t < n; ++t) {
+    int v = (int)p[t];
+    int l = 0;
+    for (int e = colptr[v]; e < colptr[v + 1]; ++e) l = max(l, last[rowidx[e]] + 1);
+    for (int e = colptr[v]; e < colptr[v + 1]; ++e) last[rowidx[e]] = l;
+    lev[v] = l;
+    nl = max(nl, l + 1);
+  }
+  for (int l = 0; l <= nl; ++l) cnt[l] = 0;
+  for (int v = 0; v < n; ++v) cnt[lev[v]]++;
+  uint32_t* off = lvl_off + (size_t)i * (n + 1);
+  int run = 0;
+  for (int l = 0; l < nl; ++l) { off[l] = run; int c = cnt[l]; cnt[l] = run; run += c; }
+  off[nl] = run;
+  for (int v = 0; v < n; ++v) tmp[cnt[lev[v]]++] = v;   // stable: ascending v inside a level
+  uint32_t* out = sched + (size_t)i * n;
+  for (int l = 0; l < nl; ++l) {
+    int b = off[l], e = off[l + 1];
+    int dc[kMaxColDeg + 2];
+    for (int d = 0; d <= kMaxColDeg + 1; ++d) dc[d] = 0;
+    for (int t = b; t < e; ++t) { int v = tmp[t]; dc[colptr[v + 1] - colptr[v]]++; }
+    int r = b;
+    for (int d = 0; d <= kMaxColDeg; ++d) { int c = dc[d]; dc[d] = r; r += c; }
+    for (int t = b; t < e; ++t) {
+      int v = tmp[t];
+      int d = colptr[v + 1] - colptr[v];
+      out[dc[d]++] = (uint32_t)v | ((uint32_t)d << 24);
+    }
+  }
+  nlev[i] = nl;
+}
+
+__device__ __forceinline__ uint64_t splitmix64_next(uint64_t& st) {
+  uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_seeded_schedules(uint32_t* __restrict__ perm, int n, int K, uint64_t seed) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K) return;
+  uint32_t* p = perm + (size_t)i * n;
+  uint64_t st = seed + (uint64_t)(i + 1) * 0xD1B54A32D192ED03ull;
+  for (int j = 0; j < n; ++j) p[j] = (uint32_t)j;
+  for (int k = n - 1; k >= 1; --k) {
+    uint64_t r = splitmix64_next(st);
+    uint64_t j = __umul64hi(r, (uint64_t)(k + 1));
+    uint32_t t = p[k]; p[k] = p[j]; p[j] = t;
+  }
+}
+
+inline int grid_for(long long work, int threads) {
+  long long g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 65535) g = 65535;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s) {
+  k_seeded_schedules<<<(K + 63) / 64, 64, 0, s>>>(d_perm, n, K, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K, const uint32_t* d_perm,
+                         int RP, int DP, int msg_fp16, const float* d_lam, int32_t* d_colptr, int32_t* d_rowidx,
+                         uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint32_t* d_lvl_off,
+                         int32_t* d_nlev, int32_t* d_scratch, cudaStream_t s) {
+  // scratch layout: cnt[n] | fill[n] | packed[E] ; later reused by k_levels (K*(m+3n+1))
+  int E = 0;
+  cudaError_t err = cudaMemcpyAsync(&E, d_rowptr + m, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (err != cudaSuccess) return err;
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
+  int32_t* cnt = d_scratch;
+  int32_t* fill = cnt + n;
+  uint32_t* packed = reinterpret_cast<uint32_t*>(fill + n);
+  if ((err = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 2 * (size_t)n, s)) != cudaSuccess) return err;
+  k_col_count<<<grid_for(E, 256), 256, 0, s>>>(d_colidx, E, cnt);
+  k_scan_single<<<1, 1024, 0, s>>>(cnt, n, d_colptr);
+  k_csc_fill<<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_colptr, fill, packed);
+  k_csc_finish<<<grid_for(n, 128), 128, 0, s>>>(n, DP, d_colptr, packed, d_rowidx, d_csc_ent);
+  if (msg_fp16)
+    k_msg_init<__half><<<grid_for((long long)m * RP, 256), 256, 0, s>>>(d_rowptr, d_colidx, m, RP, d_lam,
+                                                                       static_cast<__half*>(d_msg_init));
+  else
+    k_msg_init<float><<<grid_for((long long)m * RP, 256), 256, 0, s>>>(d_rowptr, d_colidx, m, RP, d_lam,
+                                                                      static_cast<float*>(d_msg_init));
+  k_levels<<<(K + 31) / 32, 32, 0, s>>>(d_perm, n, m, K, d_colptr, d_rowidx, d_sched, d_lvl_off, d_nlev, d_scratch);
+  return cudaGetLastError();
+}
+
+}  // namespace vibe

@@ -1,0 +1,106 @@
+// Internal declarations shared by the CUDA translation units of libvibe.so.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vibe.h"
+
+namespace vibe {
+
+constexpr int kBpWarpsPerCta = 4;   // persistent BP kernel: warps per CTA, one shot per warp
+constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
+constexpr int kMaxRowDeg = 255;     // slot index of an edge inside its check row fits in 8 bits
+constexpr int kMaxColDeg = 32;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Device-resident tables of one decoding problem (owned by the handle).
+struct Tables {
+  int m, n, k, E, K;
+  int RP;        // row pitch of the padded message image: max row degree rounded up to 8
+  int DP;        // column pitch of csc_ent: max column degree rounded up to 4 (4, 8, 16 or 32)
+  int mw, nw, kw;
+  int W;         // words of a bit vector over the checks: ceil(m/32)
+  const int32_t* rowptr;   // H CSR
+  const int32_t* colidx;
+  const int32_t* colptr;   // H CSC, checks ascending in each column
+  const int32_t* rowidx;
+  const uint32_t* csc_ent; // n*DP: (check << 8) | slot-in-row, ascending check, zero padded
+  const float* lam;        // n prior LLRs
+  const void* msg_init;    // m*RP messages (float or half): lambda of the edge's column, +inf padding
+  const uint32_t* sched;   // K*n: column | (degree << 24), grouped by wavefront level
+  const uint32_t* lvl_off; // K*(n+1): level offsets into sched
+  const int32_t* nlev;     // K level counts
+  const int32_t* lrowptr;  // L CSR
+  const int32_t* lcolidx;
+};
+
+struct BpArgs {
+  Tables t;
+  int T, M;
+  float alpha;
+  int want_soft;
+  // per-warp shared-memory layout, bytes
+  int warp_smem, off_msg, off_post, off_s, off_par, off_cand;
+  // batch (one chunk)
+  const uint32_t* syn;
+  uint32_t nshots;
+  uint32_t* corr;
+  uint32_t* logical;
+  vibe_shot_stats* stats;
+  float* soft;
+  const uint32_t* obs;
+  unsigned long long* counters;
+  // work distribution and hand-off to LSD
+  unsigned int* next_shot;
+  unsigned int* lsd_count;
+  uint32_t* lsd_shots;
+  float* lsd_soft;
+  // per-warp global scratch: n floats (LLR accumulator) + M*n floats (candidate posteriors)
+  float* scratch;
+  long long scratch_pitch;
+};
+
+struct LsdArgs {
+  Tables t;
+  int T, order, want_soft;
+  int CW;                  // words of a bit vector over a cluster's columns: ceil(n/32)
+  const uint32_t* syn;
+  uint32_t* corr;
+  uint32_t* logical;
+  vibe_shot_stats* stats;
+  float* soft;
+  const uint32_t* obs;
+  unsigned long long* counters;
+  const unsigned int* lsd_count;
+  const uint32_t* lsd_shots;
+  const float* lsd_soft;
+  unsigned int* lsd_next;
+  // per-CTA global scratch: basis m*W words, combinations m*CW words, 2*n u64 sort buffers
+  uint32_t* scratch;
+  long long scratch_pitch; // 32-bit words per CTA
+};
+
+// K0: graph builder (vibe_graph.cu)
+cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K,
+                         const uint32_t* d_perm, int RP, int DP, int msg_fp16, const float* d_lam,
+                         int32_t* d_colptr, int32_t* d_rowidx, uint32_t* d_csc_ent, void* d_msg_init,
+                         uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev, int32_t* d_scratch,
+                         cudaStream_t s);
+cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
+cudaError_t check_permutations(const uint32_t* d_perm, int n, int K, int32_t* d_scratch, int* h_bad,
+                               cudaStream_t s);
+
+// K1: persistent BP + ensemble selection (vibe_bp.cu)
+size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, int* off_msg, int* off_post, int* off_s,
+                          int* off_par, int* off_cand);
+cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
+cudaError_t bp_occupancy(const Tables& t, int msg_fp16, size_t cta_smem, int* blocks_per_sm);
+
+// K3: LSD (vibe_lsd.cu)
+size_t lsd_smem_bytes(const Tables& t);
+cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s);
+cudaError_t lsd_occupancy(const Tables& t, int* blocks_per_sm);
+
+}  // namespace vibe
