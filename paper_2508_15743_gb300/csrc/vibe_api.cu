@@ -244,7 +244,6 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   const int maxcol = *std::max_element(coldeg.begin(), coldeg.end());
   if (maxrow > vibe::kMaxRowDeg) return fail(VIBE_ERR_UNSUPPORTED, "a row of H has %d > 255 entries", maxrow);
   if (maxcol > vibe::kMaxColDeg) return fail(VIBE_ERR_UNSUPPORTED, "a column of H has %d > 32 entries", maxcol);
-  if (p->lsd_order > 0) return fail(VIBE_ERR_UNSUPPORTED, "lsd_order > 0 is not built yet");
   if (schedules) {
     std::vector<unsigned char> seen(n);
     for (int i = 0; i < K; ++i) {

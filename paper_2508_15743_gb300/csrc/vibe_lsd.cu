@@ -21,6 +21,8 @@
 namespace vibe {
 namespace {
 
+constexpr int kFreeRows = 10;   // largest LSD order: records kept for the first 10 free columns
+
 struct LsdShared {
   uint32_t* key;      // n  reliability key (sortable bits of the soft value)
   int32_t* col_root;  // n  a check of the column's cluster, -1 if free
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
   const size_t sort_off = ((size_t)m * W + (size_t)m * a.CW + 1) & ~(size_t)1;   // 8-byte aligned
   unsigned long long* sortA = reinterpret_cast<unsigned long long*>(basis + sort_off);  // n
   unsigned long long* sortB = sortA + n;                                    // n
+  uint32_t* freecomb = reinterpret_cast<uint32_t*>(sortB + n);              // per warp (kFreeRows+1) * CW
   const int CW = a.CW;
   const unsigned int total = *a.lsd_count;
 
@@ -381,8 +384,12 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
           Bv[pos] = key;
         }
         __syncwarp();
-        // OSD-0: eliminate the columns in reliability order, recording each row's columns
+        // OSD-0: eliminate the columns in reliability order, recording each row's columns. A column
+        // that reduces to zero is free; its record (itself plus the pivots that sum to it) is kept for
+        // the first `order` free columns.
         uint32_t x[WP], comb[WP];
+        uint32_t* fc = freecomb + (size_t)warp * (kFreeRows + 1) * CW;
+        int nfree = 0;
         for (int tp = 0; tp < kap; ++tp) {
           const int j = (int)(Bv[tp] & 0xffffffffull);
           load_column<WP>(t, j, x, lane);
@@ -393,6 +400,15 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
           if (any_bits<WP>(x)) {
             const int p = lowest_bit<WP>(x, lane);
             append_row<WP, true>(x, comb, p, r, S, basis, combrow, W, CW, &S.b_head[r], &S.b_tail[r], lane);
+          } else {
+            if (nfree < a.order) {
+#pragma unroll
+              for (int qq = 0; qq < WP; ++qq) {
+                const int w = lane + 32 * qq;
+                if (w < CW) fc[(size_t)nfree * CW + w] = comb[qq];
+              }
+            }
+            ++nfree;
           }
         }
         // reduce the cluster's syndrome; the recorded columns are the solution
@@ -410,15 +426,62 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
           comb[qq] = 0u;
         }
         reduce<WP, true>(x, comb, S.b_head[r], S, basis, combrow, W, CW, lane);
+        const int q = min(a.order, nfree);
+        if (q == 0) {
 #pragma unroll
-        for (int qq = 0; qq < WP; ++qq) {
-          uint32_t cbits = comb[qq];
-          while (cbits) {
-            const int b = __ffs(cbits) - 1;
-            cbits &= cbits - 1;
-            const int tp = (lane + 32 * qq) * 32 + b;
-            if (tp < kap) {
-              const int j = (int)(Bv[tp] & 0xffffffffull);
+          for (int qq = 0; qq < WP; ++qq) {
+            uint32_t cbits = comb[qq];
+            while (cbits) {
+              const int b = __ffs(cbits) - 1;
+              cbits &= cbits - 1;
+              const int tp = (lane + 32 * qq) * 32 + b;
+              if (tp < kap) {
+                const int j = (int)(Bv[tp] & 0xffffffffull);
+                atomicOr(&S.ebits[j >> 5], 1u << (j & 31));
+              }
+            }
+          }
+        } else {
+          // order-q search: setting a (bit b = free column b) gives x0 XOR the records of the set free
+          // columns. Row kFreeRows holds x0. A[u] = (column << 32) | mask for the u-th column of the
+          // cluster in ascending column index, mask bit 0 = x0, bit b+1 = record of free column b.
+#pragma unroll
+          for (int qq = 0; qq < WP; ++qq) {
+            const int w = lane + 32 * qq;
+            if (w < CW) fc[(size_t)kFreeRows * CW + w] = comb[qq];
+          }
+          __syncwarp();
+          for (int tp = lane; tp < kap; tp += 32) {
+            const uint32_t j = (uint32_t)(Bv[tp] & 0xffffffffull);
+            int u = 0;
+            for (int v2 = 0; v2 < kap; ++v2) u += (uint32_t)(Bv[v2] & 0xffffffffull) < j;
+            uint32_t mask = (fc[(size_t)kFreeRows * CW + (tp >> 5)] >> (tp & 31)) & 1u;
+            for (int b = 0; b < q; ++b) mask |= ((fc[(size_t)b * CW + (tp >> 5)] >> (tp & 31)) & 1u) << (b + 1);
+            A[u] = ((unsigned long long)j << 32) | mask;
+          }
+          __syncwarp();
+          float bestW = __int_as_float(0x7f800000);
+          int bestA = 0x7fffffff;
+          for (int set = lane; set < (1 << q); set += 32) {
+            const uint32_t sel = ((uint32_t)set << 1) | 1u;
+            float Wt = 0.0f;
+            for (int u = 0; u < kap; ++u) {
+              const unsigned long long au = A[u];
+              if (__popc((uint32_t)au & sel) & 1) Wt = __fadd_rn(Wt, __ldg(t.lam + (au >> 32)));
+            }
+            if (Wt < bestW) { bestW = Wt; bestA = set; }   // ascending settings per lane: ties keep the lower
+          }
+#pragma unroll
+          for (int off = 16; off >= 1; off >>= 1) {
+            const float ow = __shfl_xor_sync(kFull, bestW, off);
+            const int oa = __shfl_xor_sync(kFull, bestA, off);
+            if (ow < bestW || (ow == bestW && oa < bestA)) { bestW = ow; bestA = oa; }
+          }
+          const uint32_t sel = ((uint32_t)bestA << 1) | 1u;
+          for (int u = lane; u < kap; u += 32) {
+            const unsigned long long au = A[u];
+            if (__popc((uint32_t)au & sel) & 1) {
+              const uint32_t j = (uint32_t)(au >> 32);
               atomicOr(&S.ebits[j >> 5], 1u << (j & 31));
             }
           }
@@ -486,7 +549,8 @@ size_t lsd_smem_bytes(const Tables& t) {
 long long lsd_scratch_words(const Tables& t) {
   const long long CW = (t.n + 31) / 32;
   const long long head = ((long long)t.m * t.W + (long long)t.m * CW + 1) & ~1LL;
-  return (head + 4LL * t.n + 2 + 1) & ~1LL;   // even, so every CTA's slice stays 8-byte aligned
+  const long long free_rows = (long long)(kLsdThreads / 32) * (kFreeRows + 1) * CW;
+  return (head + 4LL * t.n + free_rows + 2 + 1) & ~1LL;   // even: every CTA's slice stays 8-byte aligned
 }
 
 cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s) {

@@ -24,9 +24,9 @@ def V():
     return vibe
 
 
-def run_gpu(V, dm, perms, syn, T, alpha, M, fp16=False, want_soft=True, obs=None, K=None, seed=0):
+def run_gpu(V, dm, perms, syn, T, alpha, M, fp16=False, want_soft=True, obs=None, K=None, seed=0, order=0):
     K = perms.shape[0] if perms is not None else K
-    dec = V.Decoder(dm, K, perms, T=T, alpha=alpha, M=M, msg_fp16=fp16, seed=seed)
+    dec = V.Decoder(dm, K, perms, T=T, alpha=alpha, M=M, msg_fp16=fp16, seed=seed, lsd_order=order)
     syn_t = torch.from_numpy(np.ascontiguousarray(syn).view(np.int32)).cuda()
     obs_t = None if obs is None else torch.from_numpy(np.ascontiguousarray(obs).view(np.int32)).cuda()
     cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
@@ -128,6 +128,18 @@ def test_alpha_one_and_codecap_d7(V):
     g = run_gpu(V, dm, perms, syn, 12, 1.0, 2)
     r = oracle.decode(dm, perms, syn, 12, 1.0, 2, nthreads=8)
     assert_same(g, r, what="d7 alpha 1")
+
+
+@pytest.mark.parametrize("order", [1, 3, 5, 10])
+def test_lsd_higher_order(V, order):
+    dm = D.phenomenological_dem(7, 5, 0.02, 0.02)
+    syn, obs = D.sample(dm, 1200, 40 + order)
+    perms = D.schedules(dm.n, 8, 3)
+    g = run_gpu(V, dm, perms, syn, 10, 0.625, 3, order=order)
+    r = oracle.decode(dm, perms, syn, 10, 0.625, 3, lsd_order=order, nthreads=8)
+    assert_same(g, r, what=f"LSD order {order}")
+    r0 = oracle.decode(dm, perms, syn, 10, 0.625, 3, lsd_order=0, nthreads=8)
+    assert (r0["corrections"] != r["corrections"]).any(axis=1).sum() > 0, "the search must change some shots"
 
 
 def test_seeded_schedules_match_definition(V):
