@@ -148,6 +148,31 @@ int vibe_get_wavefronts(vibe_handle* h, int32_t member, uint32_t* order_out,
 int vibe_profile(vibe_handle* h, int32_t enable);
 int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp_launches, int64_t* lsd_launches);
 
+/*
+ * vibe_decode_noalloc -- vibe_decode for callers that must not allocate device memory while they
+ * decode: a control loop that has to keep a fixed memory footprint once running, a process sharing
+ * the GPU under a hard memory budget, or code running where the CUDA allocator may not be entered.
+ * The paper has no counterpart; this is an operational variant of vibe_decode.
+ *   It runs the same BP ensemble and LSD kernels but takes all of their scratch from one static
+ *   device array of 64 MiB that every GPU loading the library holds until the process exits. It
+ *   calls no cudaMalloc/cudaFree and allocates nothing on the host; the handle must already exist.
+ *   Inputs and outputs are as for vibe_decode (d_logical and d_stats may be NULL); no soft output,
+ *   observables or counters.
+ *   Limit: B shots need B*(4n+4) bytes beside a fixed part that depends on the problem
+ *   (counters, one n-float accumulator per BP warp, one row set per LSD CTA); a batch that does not
+ *   fit returns VIBE_ERR_UNSUPPORTED with the largest batch that does (about 15,000 shots for the
+ *   d=9 phenomenological problem) -- split larger batches into several calls.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with the
+ *   handle's device current; make that first call before any stream capture.
+ *   Every call on a device shares the one array, and its contents persist between calls (the call
+ *   clears the counters it needs). Calls whose work overlaps on the GPU -- on different streams or
+ *   from different threads without ordering -- race on it and must be serialised by the caller.
+ *   Errors: VIBE_ERR_INVALID (NULL handle/pointers, B < 0, handle's device not current),
+ *   VIBE_ERR_UNSUPPORTED (batch too large), VIBE_ERR_CUDA. B = 0 is a no-op.
+ */
+int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
+                        uint32_t* d_logical, vibe_shot_stats* d_stats, void* stream);
+
 /* vibe_destroy -- frees every device and host resource of the handle. NULL is accepted. */
 int vibe_destroy(vibe_handle* h);
 

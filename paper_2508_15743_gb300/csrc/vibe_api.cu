@@ -442,3 +442,23 @@ int vibe_destroy(vibe_handle* h) {
 }
 
 }  // extern "C"
+
+// Read-only access to a handle's resident problem for the library's other host translation units.
+namespace vibe {
+
+int handle_view(const vibe_handle* h, HandleView* v) {
+  if (!h || !v) return fail(VIBE_ERR_INVALID, "NULL handle");
+  v->t = h->t;
+  v->device = h->device;
+  v->T = h->T; v->M = h->M; v->lsd_order = h->lsd_order; v->msg_fp16 = h->msg_fp16; v->alpha = h->alpha;
+  v->warp_smem = h->warp_smem; v->off_msg = h->off_msg; v->off_post = h->off_post; v->off_s = h->off_s;
+  v->off_par = h->off_par; v->off_cand = h->off_cand;
+  v->bp_grid = h->bp_grid();
+  v->lsd_grid = h->lsd_grid();
+  v->num_sms = h->num_sms;
+  return VIBE_OK;
+}
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+}  // namespace vibe

@@ -82,6 +82,19 @@ struct LsdArgs {
   long long scratch_pitch; // 32-bit words per CTA
 };
 
+// A handle's resident problem and launch configuration, as other host files see it (vibe_api.cu).
+struct HandleView {
+  Tables t;
+  int device, num_sms;
+  int T, M, lsd_order, msg_fp16;
+  float alpha;
+  int warp_smem, off_msg, off_post, off_s, off_par, off_cand;
+  int bp_grid, lsd_grid;
+};
+int handle_view(const vibe_handle* h, HandleView* v);
+int set_error(int code, const char* msg);
+long long lsd_scratch_words(const Tables& t);
+
 // K0: graph builder (vibe_graph.cu)
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K,
                          const uint32_t* d_perm, int RP, int DP, int msg_fp16, const float* d_lam,
@@ -89,8 +102,6 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
                          uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev, int32_t* d_scratch,
                          cudaStream_t s);
 cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
-cudaError_t check_permutations(const uint32_t* d_perm, int n, int K, int32_t* d_scratch, int* h_bad,
-                               cudaStream_t s);
 
 // K1: persistent BP + ensemble selection (vibe_bp.cu)
 size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, int* off_msg, int* off_post, int* off_s,

@@ -1,0 +1,114 @@
+// vibe_decode_noalloc: decoding for callers that must not allocate device memory while they decode.
+//
+// vibe_decode grows a per-handle workspace with cudaMalloc on its first call and whenever a batch
+// outgrows it. Some callers cannot allow that: a control loop that must keep a fixed memory
+// footprint once it is running, a process that shares the GPU under a hard memory budget, or code
+// that runs where the CUDA allocator may not be entered. For them this entry point decodes with
+// scratch memory that exists from the moment the library is loaded: one file-scope device array of
+// kStaticBytes (64 MiB) on every GPU that loads the library, held until the process exits.
+//
+// The kernels are the same BP ensemble and LSD kernels vibe_decode runs; only their scratch
+// (shot and LSD counters, the LSD hand-off queue, the per-warp LLR accumulators, the per-CTA LSD
+// rows) is carved out of the static array instead of the handle's workspace.
+#include <cstdio>
+#include <mutex>
+
+#include "vibe_internal.cuh"
+
+namespace {
+
+constexpr size_t kStaticBytes = size_t(64) << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_lock;
+void* g_scratch_addr[kMaxDevices] = {};   // device address of g_static_scratch, per device
+
+// Host code only sees a host-side stand-in for g_static_scratch; the device address comes from
+// cudaGetSymbolAddress, resolved once per device with that device current.
+int scratch_address(int device, unsigned char** out) {
+  if (device < 0 || device >= kMaxDevices) return vibe::set_error(VIBE_ERR_UNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> g(g_lock);
+  if (!g_scratch_addr[device]) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != device)
+      return vibe::set_error(VIBE_ERR_INVALID, "the handle's device must be current");
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
+    g_scratch_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+  return VIBE_OK;
+}
+
+inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
+                                   uint32_t* d_logical, vibe_shot_stats* d_stats, void* stream) {
+  vibe::HandleView v;
+  int rc = vibe::handle_view(h, &v);
+  if (rc != VIBE_OK) return rc;
+  if (B < 0) return vibe::set_error(VIBE_ERR_INVALID, "negative batch");
+  if (B == 0) return VIBE_OK;
+  if (!d_syndromes || !d_corrections) return vibe::set_error(VIBE_ERR_INVALID, "NULL syndromes or corrections");
+  const vibe::Tables& t = v.t;
+  // Fixed part: counters, one n-float accumulator per BP warp, one row set per LSD CTA. The LSD CTAs
+  // are capped at one per SM so the fixed part stays small; the rest holds the LSD hand-off queue.
+  const int bp_grid = v.bp_grid;
+  const int lsd_grid = v.lsd_grid < v.num_sms ? v.lsd_grid : v.num_sms;
+  const size_t ctrl_b = 256;
+  const size_t bp_b = up256((size_t)bp_grid * vibe::kBpWarpsPerCta * (size_t)t.n * sizeof(float));
+  const size_t lsd_b = up256((size_t)lsd_grid * (size_t)vibe::lsd_scratch_words(t) * sizeof(uint32_t));
+  const size_t fixed = ctrl_b + bp_b + lsd_b;
+  const size_t per_shot = (size_t)t.n * sizeof(float) + sizeof(uint32_t);
+  const long long max_b = fixed + 512 < kStaticBytes ? (long long)((kStaticBytes - fixed - 512) / per_shot) : 0;
+  if (B > max_b) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "batch of %lld shots exceeds the 64 MiB static workspace (at most %lld for this problem)",
+             (long long)B, max_b);
+    return vibe::set_error(VIBE_ERR_UNSUPPORTED, msg);
+  }
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != v.device)
+    return vibe::set_error(VIBE_ERR_INVALID, "the handle's device must be current");
+  unsigned char* base = nullptr;
+  if ((rc = scratch_address(v.device, &base)) != VIBE_OK) return rc;
+  unsigned int* ctrl = reinterpret_cast<unsigned int*>(base);
+  float* bp_scratch = reinterpret_cast<float*>(base + ctrl_b);
+  uint32_t* lsd_scratch = reinterpret_cast<uint32_t*>(base + ctrl_b + bp_b);
+  uint32_t* lsd_shots = reinterpret_cast<uint32_t*>(base + fixed);
+  float* lsd_soft = reinterpret_cast<float*>(base + fixed + up256((size_t)B * sizeof(uint32_t)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // the array keeps the previous call's contents: the counters must start at zero
+  cudaError_t e = cudaMemsetAsync(ctrl, 0, ctrl_b, s);
+  if (e != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
+  vibe::BpArgs a{};
+  a.t = t;
+  a.T = v.T; a.M = v.M; a.alpha = v.alpha; a.want_soft = 0;
+  a.warp_smem = v.warp_smem; a.off_msg = v.off_msg; a.off_post = v.off_post; a.off_s = v.off_s;
+  a.off_par = v.off_par; a.off_cand = v.off_cand;
+  a.syn = d_syndromes; a.nshots = (uint32_t)B; a.corr = d_corrections; a.logical = d_logical; a.stats = d_stats;
+  a.soft = nullptr; a.obs = nullptr; a.counters = nullptr;
+  a.next_shot = ctrl; a.lsd_count = ctrl + 1; a.lsd_shots = lsd_shots; a.lsd_soft = lsd_soft;
+  a.scratch = bp_scratch;
+  a.scratch_pitch = t.n;
+  const long long need_ctas = (B + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta;
+  const int grid = (int)(need_ctas < bp_grid ? need_ctas : bp_grid);
+  if ((e = vibe::launch_bp(a, v.msg_fp16, grid, s)) != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
+  vibe::LsdArgs l{};
+  l.t = t;
+  l.T = v.T; l.order = v.lsd_order; l.want_soft = 0;
+  l.CW = (t.n + 31) / 32;
+  l.syn = d_syndromes; l.corr = d_corrections; l.logical = d_logical; l.stats = d_stats; l.soft = nullptr;
+  l.obs = nullptr; l.counters = nullptr;
+  l.lsd_count = ctrl + 1; l.lsd_shots = lsd_shots; l.lsd_soft = lsd_soft; l.lsd_next = ctrl + 2;
+  l.scratch = lsd_scratch;
+  l.scratch_pitch = vibe::lsd_scratch_words(t);
+  if ((e = vibe::launch_lsd(l, lsd_grid, s)) != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
+  return VIBE_OK;
+}

@@ -56,6 +56,8 @@ def _load():
     lib.vibe_decode.restype = ctypes.c_int
     lib.vibe_decode_host.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
     lib.vibe_decode_host.restype = ctypes.c_int
+    lib.vibe_decode_noalloc.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+    lib.vibe_decode_noalloc.restype = ctypes.c_int
     lib.vibe_get_wavefronts.argtypes = [vp, i32, vp, vp, vp]
     lib.vibe_get_wavefronts.restype = ctypes.c_int
     lib.vibe_profile.argtypes = [vp, i32]
@@ -137,6 +139,12 @@ def vibe_decode_host(h, h_syndromes, B, h_corrections, h_logical=None, h_stats=N
                      h_counters=None, stream=None):
     _check(_lib.vibe_decode_host(h, _ptr(h_syndromes), int(B), _ptr(h_corrections), _ptr(h_logical),
                                  _ptr(h_stats), _ptr(h_observables), _ptr(h_counters), _stream_ptr(stream)))
+
+
+def vibe_decode_noalloc(h, d_syndromes, B, d_corrections, d_logical=None, d_stats=None, stream=None):
+    """vibe_decode with the library's static device scratch instead of a per-handle workspace."""
+    _check(_lib.vibe_decode_noalloc(h, _ptr(d_syndromes), int(B), _ptr(d_corrections), _ptr(d_logical),
+                                    _ptr(d_stats), _stream_ptr(stream)))
 
 
 def vibe_get_wavefronts(h, member, n):
