@@ -85,7 +85,7 @@ struct vibe_handle {
   float* lam = nullptr;
   void* msg_init = nullptr;
   // launch configuration
-  int warp_smem = 0, off_msg = 0, off_post = 0, off_s = 0, off_par = 0, off_cand = 0;
+  vibe::BpLayout L{};
   int bp_blocks_per_sm = 0, lsd_blocks_per_sm = 0;
   // workspace (grown on demand)
   long long ws_chunk = 0;
@@ -143,7 +143,7 @@ int ensure_workspace(vibe_handle* h, long long need) {
   VIBE_CUDA(dalloc(&h->ctrl, 4), "workspace");
   VIBE_CUDA(dalloc(&h->lsd_shots, (size_t)chunk), "workspace");
   VIBE_CUDA(dalloc(&h->lsd_soft, (size_t)chunk * t.n), "workspace");
-  VIBE_CUDA(dalloc(&h->bp_scratch, (size_t)bp_warps * (size_t)(1 + h->M) * t.n), "workspace");
+  VIBE_CUDA(dalloc(&h->bp_scratch, (size_t)bp_warps * (size_t)(2 + h->M) * t.n), "workspace");
   VIBE_CUDA(dalloc(&h->lsd_scratch, (size_t)h->lsd_grid() * (size_t)vibe::lsd_scratch_words(t)), "workspace");
   h->ws_chunk = chunk;
   return VIBE_OK;
@@ -170,8 +170,8 @@ int decode_device(vibe_handle* h, const uint32_t* syn, long long B, uint32_t* co
     vibe::BpArgs a{};
     a.t = t;
     a.T = h->T; a.M = h->M; a.alpha = h->alpha; a.want_soft = soft != nullptr;
-    a.warp_smem = h->warp_smem; a.off_msg = h->off_msg; a.off_post = h->off_post; a.off_s = h->off_s;
-    a.off_par = h->off_par; a.off_cand = h->off_cand;
+    a.warp_smem = h->L.warp_smem; a.off_msg = h->L.off_msg; a.off_dec = h->L.off_dec;
+    a.off_s = h->L.off_s; a.off_par = h->L.off_par; a.off_cand = h->L.off_cand;
     a.syn = syn + (size_t)b0 * t.mw;
     a.nshots = (uint32_t)nb;
     a.corr = corr + (size_t)b0 * t.nw;
@@ -185,7 +185,7 @@ int decode_device(vibe_handle* h, const uint32_t* syn, long long B, uint32_t* co
     a.lsd_shots = h->lsd_shots;
     a.lsd_soft = h->lsd_soft;
     a.scratch = h->bp_scratch;
-    a.scratch_pitch = (long long)(1 + h->M) * t.n;
+    a.scratch_pitch = (long long)(2 + h->M) * t.n;
     const int bp_grid = (int)std::min<long long>(h->bp_grid(), (nb + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (h->profiling) { e0 = next_event(h); e1 = next_event(h); e2 = next_event(h); }
@@ -318,9 +318,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   t.csc_ent = h->csc_ent; t.lam = h->lam; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
   t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
 
-  const size_t wsm = vibe::bp_warp_smem_bytes(t, h->M, h->msg_fp16, &h->off_msg, &h->off_post, &h->off_s, &h->off_par,
-                                              &h->off_cand);
-  h->warp_smem = (int)wsm;
+  const size_t wsm = vibe::bp_warp_smem_bytes(t, h->M, h->msg_fp16, &h->L);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (wsm * vibe::kBpWarpsPerCta > (size_t)optin)
@@ -451,8 +449,7 @@ int handle_view(const vibe_handle* h, HandleView* v) {
   v->t = h->t;
   v->device = h->device;
   v->T = h->T; v->M = h->M; v->lsd_order = h->lsd_order; v->msg_fp16 = h->msg_fp16; v->alpha = h->alpha;
-  v->warp_smem = h->warp_smem; v->off_msg = h->off_msg; v->off_post = h->off_post; v->off_s = h->off_s;
-  v->off_par = h->off_par; v->off_cand = h->off_cand;
+  v->L = h->L;
   v->bp_grid = h->bp_grid();
   v->lsd_grid = h->lsd_grid();
   v->num_sms = h->num_sms;

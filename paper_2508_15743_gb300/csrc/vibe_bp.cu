@@ -19,6 +19,8 @@
 // Arithmetic is the oracle's to the bit: fixed per-node operation order, __fadd_rn/__fmul_rn (no
 // contraction), min and sign exact. Stored messages are never -0 (a sum that starts at lambda_v > 0
 // cannot round to -0 in FP32; FP16 stores map -0 to +0), so the sign bit of a message equals x < 0.
+#include <type_traits>
+
 #include "vibe_internal.cuh"
 
 namespace vibe {
@@ -29,43 +31,36 @@ struct Msg;
 
 template <>
 struct Msg<float> {
-  static constexpr uint32_t kInf = 0x7f800000u;
-  // min |x| (as ordered bit patterns) and XOR of the raw words over 8 slots, skipping slot `skip`
-  __device__ __forceinline__ static void scan8(const float* row8, int skip, uint32_t& mn, uint32_t& sg) {
+  // Minimum magnitude (as a float) and XOR of the raw words over 8 slots starting at row8.
+  __device__ __forceinline__ static void scan8(const float* row8, float& mn, uint32_t& sg) {
     const float4 a = reinterpret_cast<const float4*>(row8)[0];
     const float4 b = reinterpret_cast<const float4*>(row8)[1];
-    uint32_t u[8] = {__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(a.z), __float_as_uint(a.w),
-                     __float_as_uint(b.x), __float_as_uint(b.y), __float_as_uint(b.z), __float_as_uint(b.w)};
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint32_t keep = (j != skip) ? 0xffffffffu : 0u;
-      mn = min(mn, (u[j] & 0x7fffffffu) | ~keep);
-      sg ^= u[j] & keep;
-    }
+    const float m01 = fminf(fabsf(a.x), fabsf(a.y)), m23 = fminf(fabsf(a.z), fabsf(a.w));
+    const float m45 = fminf(fabsf(b.x), fabsf(b.y)), m67 = fminf(fabsf(b.z), fabsf(b.w));
+    mn = fminf(mn, fminf(fminf(m01, m23), fminf(m45, m67)));
+    sg ^= __float_as_uint(a.x) ^ __float_as_uint(a.y) ^ __float_as_uint(a.z) ^ __float_as_uint(a.w) ^
+          __float_as_uint(b.x) ^ __float_as_uint(b.y) ^ __float_as_uint(b.z) ^ __float_as_uint(b.w);
   }
-  __device__ __forceinline__ static float min_value(uint32_t mn) { return __uint_as_float(mn); }
   __device__ __forceinline__ static uint32_t sign(uint32_t sg) { return sg >> 31; }
+  __device__ __forceinline__ static void set_inf(float* p) { *p = __int_as_float(0x7f800000); }
   __device__ __forceinline__ static void store(float* p, float x) { *p = x; }
 };
 
 template <>
 struct Msg<__half> {
-  static constexpr uint32_t kInf = 0x7c00u;
-  __device__ __forceinline__ static void scan8(const __half* row8, int skip, uint32_t& mn, uint32_t& sg) {
+  __device__ __forceinline__ static void scan8(const __half* row8, float& mn, uint32_t& sg) {
     const uint4 q = *reinterpret_cast<const uint4*>(row8);
-    uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint32_t h = (w[j >> 1] >> ((j & 1) * 16)) & 0xffffu;
-      uint32_t keep = (j != skip) ? 0xffffffffu : 0u;
-      mn = min(mn, (h & 0x7fffu) | ~keep);
-      sg ^= h & keep;
-    }
-  }
-  __device__ __forceinline__ static float min_value(uint32_t mn) {
-    return __half2float(__ushort_as_half((unsigned short)mn));
+    const __half2 h0 = __habs2(*reinterpret_cast<const __half2*>(&q.x));
+    const __half2 h1 = __habs2(*reinterpret_cast<const __half2*>(&q.y));
+    const __half2 h2 = __habs2(*reinterpret_cast<const __half2*>(&q.z));
+    const __half2 h3 = __habs2(*reinterpret_cast<const __half2*>(&q.w));
+    const __half2 hm = __hmin2(__hmin2(h0, h1), __hmin2(h2, h3));
+    mn = fminf(mn, __half2float(__hmin(__low2half(hm), __high2half(hm))));
+    const uint32_t x = q.x ^ q.y ^ q.z ^ q.w;
+    sg ^= x ^ (x >> 16);
   }
   __device__ __forceinline__ static uint32_t sign(uint32_t sg) { return (sg >> 15) & 1u; }
+  __device__ __forceinline__ static void set_inf(__half* p) { *reinterpret_cast<unsigned short*>(p) = 0x7c00u; }
   __device__ __forceinline__ static void store(__half* p, float x) {
     unsigned short h = __half_as_ushort(__float2half_rn(x));
     if (h == 0x8000u) h = 0;
@@ -77,11 +72,18 @@ __device__ __forceinline__ bool is_finite_bits(float x) {
   return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
 }
 
-// One serial-V column update (R2, R3 of the oracle): check-to-variable messages from the current
-// variable-to-check messages of the other columns, posterior, literal exclusion sums, decision.
-template <typename MT, int DP>
+// One serial-V column update (readings R2, R3 of the oracle): check-to-variable messages from the
+// current variable-to-check messages of the other columns, posterior, literal exclusion sums, decision.
+// RPC = row pitch in 8-slot chunks (0: read it from the tables).
+//
+// Exclusion of the column's own message from its check rows: a check is touched by exactly one
+// column per wavefront level, so the updating lane owns the row until the level ends. It overwrites
+// its own slot with +inf (magnitude that never wins a minimum, sign bit 0), takes the minimum
+// magnitude and the XOR of the sign bits over the whole row, and later stores its new message in
+// the same slot. Minimum and parity equal those over the other slots exactly.
+template <typename MT, int DP, int RPC>
 __device__ __forceinline__ void update_column(uint32_t v, int deg, const Tables& t, float alpha, MT* msgs,
-                                              float* post, const uint8_t* s8, uint8_t* par8) {
+                                              uint8_t* dec8, const uint8_t* s8, uint8_t* par8, float* lpost) {
   uint32_t ent[DP];
   const uint4* ce = reinterpret_cast<const uint4*>(t.csc_ent + (size_t)v * DP);
 #pragma unroll
@@ -90,19 +92,25 @@ __device__ __forceinline__ void update_column(uint32_t v, int deg, const Tables&
     ent[4 * q + 0] = x.x; ent[4 * q + 1] = x.y; ent[4 * q + 2] = x.z; ent[4 * q + 3] = x.w;
   }
   const float lamv = __ldg(t.lam + v);
-  const int RP = t.RP;
+  const uint32_t RP = RPC ? (uint32_t)RPC * 8u : (uint32_t)t.RP;
   float mcv[DP];
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
     mcv[k] = 0.0f;
     if (k < deg) {
       const uint32_t c = ent[k] >> 8;
-      const int slot = (int)(ent[k] & 0xffu);
-      const MT* row = msgs + (size_t)c * RP;
-      uint32_t mn = Msg<MT>::kInf, sg = 0;
-      for (int ch = 0; ch < RP; ch += 8) Msg<MT>::scan8(row + ch, slot - ch, mn, sg);
+      MT* row = msgs + c * RP;
+      Msg<MT>::set_inf(row + (ent[k] & 0xffu));
+      float mn = __int_as_float(0x7f800000);
+      uint32_t sg = 0;
+      if (RPC) {
+#pragma unroll
+        for (int ch = 0; ch < RPC; ++ch) Msg<MT>::scan8(row + 8 * ch, mn, sg);
+      } else {
+        for (uint32_t ch = 0; ch < RP; ch += 8) Msg<MT>::scan8(row + ch, mn, sg);
+      }
       const uint32_t neg = Msg<MT>::sign(sg) ^ (uint32_t)s8[c];
-      const float mag = __fmul_rn(alpha, Msg<MT>::min_value(mn));
+      const float mag = __fmul_rn(alpha, mn);
       mcv[k] = neg ? -mag : mag;
     }
   }
@@ -118,22 +126,22 @@ __device__ __forceinline__ void update_column(uint32_t v, int deg, const Tables&
 #pragma unroll
       for (int k2 = k + 1; k2 < DP; ++k2)
         if (k2 < deg) a = __fadd_rn(a, mcv[k2]);
-      Msg<MT>::store(msgs + (size_t)(ent[k] >> 8) * RP + (ent[k] & 0xffu), a);
+      Msg<MT>::store(msgs + (ent[k] >> 8) * RP + (ent[k] & 0xffu), a);
       pre = __fadd_rn(pre, mcv[k]);
     }
   }
-  const bool e_new = L <= 0.0f;
-  const bool e_old = post[v] <= 0.0f;
-  if (e_new != e_old) {
+  const uint8_t e_new = L <= 0.0f;
+  if (e_new != dec8[v]) {
 #pragma unroll
     for (int k = 0; k < DP; ++k)
       if (k < deg) par8[ent[k] >> 8] ^= 1u;
+    dec8[v] = e_new;
   }
-  post[v] = L;
+  if (lpost) lpost[v] = L;
 }
 
-template <typename MT, int DP>
-__global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
+template <typename MT, int DP, int RPC>
+__global__ void __launch_bounds__(kBpWarpsPerCta * 32, 16 / kBpWarpsPerCta) k_bp(const BpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Tables& t = a.t;
   const int lane = threadIdx.x & 31;
@@ -141,15 +149,17 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
   const long long gw = (long long)blockIdx.x * kBpWarpsPerCta + wcta;
   unsigned char* base = smem + (size_t)wcta * a.warp_smem;
   MT* msgs = reinterpret_cast<MT*>(base + a.off_msg);
-  float* post = reinterpret_cast<float*>(base + a.off_post);
+  uint8_t* dec8 = base + a.off_dec;
   uint8_t* s8 = base + a.off_s;
   uint8_t* par8 = base + a.off_par;
   uint32_t* cand = reinterpret_cast<uint32_t*>(base + a.off_cand);
-  float* acc = a.scratch + gw * a.scratch_pitch;  // n floats
-  float* cand_post = acc + t.n;                    // M * n floats (only with want_soft)
+  float* acc = a.scratch + gw * a.scratch_pitch;  // n floats: LLR average accumulator
+  float* lpost = acc + t.n;                        // n floats: the member's posterior when needed
+  float* cand_post = lpost + t.n;                  // M * n floats (only with want_soft)
 
   const int n = t.n, m = t.m, K = t.K, M = a.M, T = a.T, nw = t.nw, mw = t.mw;
   const int m4 = (m + 3) >> 2;
+  const int n4 = (n + 3) >> 2;
   const int msg_vec = (int)(((size_t)m * t.RP * sizeof(MT)) / 16);
   unsigned long long my_iters = 0, my_shots = 0, my_fail = 0;
 
@@ -198,12 +208,13 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
     for (int i = 0; i < K; ++i) {
       const int budget = ncand < M ? T : __shfl_sync(kFull, c_t, M - 1) - 1;
       if (budget <= 0) break;
-      // member init: messages = prior LLR image, posterior = lambda (decision 0), parity = s
+      // member init: messages from the prior image, decisions 0, parity = s
       {
         const uint4* src = reinterpret_cast<const uint4*>(t.msg_init);
         uint4* dst = reinterpret_cast<uint4*>(msgs);
         for (int q = lane; q < msg_vec; q += 32) dst[q] = __ldg(src + q);
-        for (int v = lane; v < n; v += 32) post[v] = __ldg(t.lam + v);
+        uint32_t* d32 = reinterpret_cast<uint32_t*>(dec8);
+        for (int q = lane; q < n4; q += 32) d32[q] = 0u;
         const uint32_t* s32 = reinterpret_cast<const uint32_t*>(s8);
         uint32_t* p32 = reinterpret_cast<uint32_t*>(par8);
         for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
@@ -214,11 +225,14 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
       const int nl = __ldg(t.nlev + i);
       int conv = 0;
       for (int it = 1; it <= budget; ++it) {
+        // the posterior is needed after the last possible sweep of a member that may end without
+        // converging (LLR average) and, for soft output, after every sweep
+        float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
         for (int l = 0; l < nl; ++l) {
           const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
           for (uint32_t idx = b + lane; idx < e; idx += 32) {
             const uint32_t ent = __ldg(sch + idx);
-            update_column<MT, DP>(ent & 0xffffffu, (int)(ent >> 24), t, a.alpha, msgs, post, s8, par8);
+            update_column<MT, DP, RPC>(ent & 0xffffffu, (int)(ent >> 24), t, a.alpha, msgs, dec8, s8, par8, lp);
           }
           __syncwarp();
         }
@@ -236,7 +250,7 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
         float W = 0.0f;
         for (int w = 0; w < nw; ++w) {
           const int v = 32 * w + lane;
-          const uint32_t word = __ballot_sync(kFull, v < n && post[v] <= 0.0f);
+          const uint32_t word = __ballot_sync(kFull, v < n && dec8[v] != 0);
           if (lane == 0) bits[w] = word;
           uint32_t x = word;
           while (x) {
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
         }
         if (a.want_soft) {
           float* dst = cand_post + (size_t)slot * n;
-          for (int v = lane; v < n; v += 32) dst[v] = post[v];
+          for (int v = lane; v < n; v += 32) dst[v] = lpost[v];
         }
         const float uW = __shfl_up_sync(kFull, c_W, 1);
         const int ut = __shfl_up_sync(kFull, c_t, 1), ui = __shfl_up_sync(kFull, c_i, 1);
@@ -261,18 +275,19 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
         // not converged after T sweeps and no candidate yet: add LLR^i / ||LLR^i|| (finite entries)
         float part = 0.0f;
         for (int v = lane; v < n; v += 32) {
-          const float x = post[v];
+          const float x = lpost[v];
           part = __fadd_rn(part, is_finite_bits(x) ? __fmul_rn(x, x) : 0.0f);
         }
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) part = __fadd_rn(part, __shfl_xor_sync(kFull, part, off));
         const float nrm = __fsqrt_rn(part);
         for (int v = lane; v < n; v += 32) {
-          const float x = post[v];
+          const float x = lpost[v];
           const float term = is_finite_bits(x) ? (nrm == 0.0f ? 0.0f : __fdiv_rn(x, nrm)) : x;
           acc[v] = __fadd_rn(i == 0 ? 0.0f : acc[v], term);
         }
       }
+      __syncwarp();
     }
 
     if (ncand > 0) {
@@ -334,76 +349,92 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32) k_bp(const BpArgs a) {
   }
 }
 
-template <typename MT>
-cudaError_t launch_dp(const BpArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = (size_t)a.warp_smem * kBpWarpsPerCta;
-  const dim3 block(kBpWarpsPerCta * 32);
-  cudaError_t err;
-  switch (a.t.DP) {
-#define VIBE_BP_CASE(D)                                                                             \
-  case D:                                                                                           \
-    err = cudaFuncSetAttribute(k_bp<MT, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (err != cudaSuccess) return err;                                                             \
-    k_bp<MT, D><<<grid, block, smem, s>>>(a);                                                       \
-    return cudaGetLastError();
-    VIBE_BP_CASE(4)
-    VIBE_BP_CASE(8)
-    VIBE_BP_CASE(16)
-    VIBE_BP_CASE(32)
-#undef VIBE_BP_CASE
-    default:
-      return cudaErrorInvalidValue;
+// RPC: row pitch in 8-slot chunks when it is 1, 2 or 4 (compile-time row scans), else 0.
+inline int rpc_of(const Tables& t) { return (t.RP == 8 || t.RP == 16 || t.RP == 32) ? t.RP / 8 : 0; }
+
+template <typename MT, int DP, int RPC>
+cudaError_t launch_one(const BpArgs& a, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(k_bp<MT, DP, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_bp<MT, DP, RPC><<<grid, kBpWarpsPerCta * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename MT, int DP, int RPC>
+cudaError_t occupancy_one(size_t smem, int* out) {
+  cudaError_t err = cudaFuncSetAttribute(k_bp<MT, DP, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bp<MT, DP, RPC>, kBpWarpsPerCta * 32, smem);
+}
+
+// Dispatch over (message type, column pitch, row chunks); F is launch_one or occupancy_one.
+template <typename MT, int DP, typename Fn>
+cudaError_t by_rpc(int rpc, Fn&& f) {
+  switch (rpc) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    default: return f(std::integral_constant<int, 0>{});
+  }
+}
+
+template <typename MT, typename Fn>
+cudaError_t by_dp(int DP, Fn&& f) {
+  switch (DP) {
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    case 32: return f(std::integral_constant<int, 32>{});
+    default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename MT>
-cudaError_t occupancy_dp(int DP, size_t smem, int* out) {
-  const int threads = kBpWarpsPerCta * 32;
-  cudaError_t err;
-  switch (DP) {
-#define VIBE_OCC_CASE(D)                                                                            \
-  case D:                                                                                           \
-    err = cudaFuncSetAttribute(k_bp<MT, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (err != cudaSuccess) return err;                                                             \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bp<MT, D>, threads, smem);
-    VIBE_OCC_CASE(4)
-    VIBE_OCC_CASE(8)
-    VIBE_OCC_CASE(16)
-    VIBE_OCC_CASE(32)
-#undef VIBE_OCC_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+cudaError_t launch_mt(const BpArgs& a, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)a.warp_smem * kBpWarpsPerCta;
+  return by_dp<MT>(a.t.DP, [&](auto dp) {
+    return by_rpc<MT, decltype(dp)::value>(rpc_of(a.t), [&](auto rpc) {
+      return launch_one<MT, decltype(dp)::value, decltype(rpc)::value>(a, grid, smem, s);
+    });
+  });
+}
+
+template <typename MT>
+cudaError_t occupancy_mt(const Tables& t, size_t smem, int* out) {
+  return by_dp<MT>(t.DP, [&](auto dp) {
+    return by_rpc<MT, decltype(dp)::value>(rpc_of(t), [&](auto rpc) {
+      return occupancy_one<MT, decltype(dp)::value, decltype(rpc)::value>(smem, out);
+    });
+  });
 }
 
 inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 }  // namespace
 
-size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, int* off_msg, int* off_post, int* off_s,
-                          int* off_par, int* off_cand) {
+size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, BpLayout* L) {
   size_t o = 0;
-  *off_msg = (int)o;
+  L->off_msg = (int)o;
   o = align16(o + (size_t)t.m * t.RP * (msg_fp16 ? 2 : 4));
-  *off_post = (int)o;
-  o = align16(o + (size_t)t.n * 4);
+  L->off_dec = (int)o;
+  o = align16(o + ((size_t)t.n + 3) / 4 * 4);
   const size_t m4 = ((size_t)t.m + 3) / 4 * 4;
-  *off_s = (int)o;
+  L->off_s = (int)o;
   o = align16(o + m4);
-  *off_par = (int)o;
+  L->off_par = (int)o;
   o = align16(o + m4);
-  *off_cand = (int)o;
+  L->off_cand = (int)o;
   o = align16(o + (size_t)M * t.nw * 4);
+  L->warp_smem = (int)o;
   return o;
 }
 
 cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s) {
-  return msg_fp16 ? launch_dp<__half>(a, grid, s) : launch_dp<float>(a, grid, s);
+  return msg_fp16 ? launch_mt<__half>(a, grid, s) : launch_mt<float>(a, grid, s);
 }
 
 cudaError_t bp_occupancy(const Tables& t, int msg_fp16, size_t cta_smem, int* blocks_per_sm) {
-  return msg_fp16 ? occupancy_dp<__half>(t.DP, cta_smem, blocks_per_sm)
-                  : occupancy_dp<float>(t.DP, cta_smem, blocks_per_sm);
+  return msg_fp16 ? occupancy_mt<__half>(t, cta_smem, blocks_per_sm) : occupancy_mt<float>(t, cta_smem, blocks_per_sm);
 }
 
 }  // namespace vibe

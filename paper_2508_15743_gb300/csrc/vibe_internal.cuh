@@ -9,7 +9,7 @@
 
 namespace vibe {
 
-constexpr int kBpWarpsPerCta = 4;   // persistent BP kernel: warps per CTA, one shot per warp
+constexpr int kBpWarpsPerCta = 2;   // persistent BP kernel: warps per CTA, one shot per warp
 constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
 constexpr int kMaxRowDeg = 255;     // slot index of an edge inside its check row fits in 8 bits
 constexpr int kMaxColDeg = 32;
@@ -42,7 +42,7 @@ struct BpArgs {
   float alpha;
   int want_soft;
   // per-warp shared-memory layout, bytes
-  int warp_smem, off_msg, off_post, off_s, off_par, off_cand;
+  int warp_smem, off_msg, off_dec, off_s, off_par, off_cand;
   // batch (one chunk)
   const uint32_t* syn;
   uint32_t nshots;
@@ -57,7 +57,8 @@ struct BpArgs {
   unsigned int* lsd_count;
   uint32_t* lsd_shots;
   float* lsd_soft;
-  // per-warp global scratch: n floats (LLR accumulator) + M*n floats (candidate posteriors)
+  // per-warp global scratch: n floats (LLR accumulator), n floats (posterior), M*n floats (candidate
+  // posteriors, only with want_soft)
   float* scratch;
   long long scratch_pitch;
 };
@@ -83,12 +84,16 @@ struct LsdArgs {
 };
 
 // A handle's resident problem and launch configuration, as other host files see it (vibe_api.cu).
+struct BpLayout {
+  int warp_smem, off_msg, off_dec, off_s, off_par, off_cand;
+};
+
 struct HandleView {
   Tables t;
   int device, num_sms;
   int T, M, lsd_order, msg_fp16;
   float alpha;
-  int warp_smem, off_msg, off_post, off_s, off_par, off_cand;
+  BpLayout L;
   int bp_grid, lsd_grid;
 };
 int handle_view(const vibe_handle* h, HandleView* v);
@@ -104,8 +109,7 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
 cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
 
 // K1: persistent BP + ensemble selection (vibe_bp.cu)
-size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, int* off_msg, int* off_post, int* off_s,
-                          int* off_par, int* off_cand);
+size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, BpLayout* L);
 cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
 cudaError_t bp_occupancy(const Tables& t, int msg_fp16, size_t cta_smem, int* blocks_per_sm);
 

@@ -56,12 +56,13 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   if (B == 0) return VIBE_OK;
   if (!d_syndromes || !d_corrections) return vibe::set_error(VIBE_ERR_INVALID, "NULL syndromes or corrections");
   const vibe::Tables& t = v.t;
-  // Fixed part: counters, one n-float accumulator per BP warp, one row set per LSD CTA. The LSD CTAs
+  // Fixed part: counters, two n-float rows per BP warp (LLR accumulator, posterior), one row set per
+  // LSD CTA. The LSD CTAs
   // are capped at one per SM so the fixed part stays small; the rest holds the LSD hand-off queue.
   const int bp_grid = v.bp_grid;
   const int lsd_grid = v.lsd_grid < v.num_sms ? v.lsd_grid : v.num_sms;
   const size_t ctrl_b = 256;
-  const size_t bp_b = up256((size_t)bp_grid * vibe::kBpWarpsPerCta * (size_t)t.n * sizeof(float));
+  const size_t bp_b = up256((size_t)bp_grid * vibe::kBpWarpsPerCta * 2 * (size_t)t.n * sizeof(float));
   const size_t lsd_b = up256((size_t)lsd_grid * (size_t)vibe::lsd_scratch_words(t) * sizeof(uint32_t));
   const size_t fixed = ctrl_b + bp_b + lsd_b;
   const size_t per_shot = (size_t)t.n * sizeof(float) + sizeof(uint32_t);
@@ -90,13 +91,13 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   vibe::BpArgs a{};
   a.t = t;
   a.T = v.T; a.M = v.M; a.alpha = v.alpha; a.want_soft = 0;
-  a.warp_smem = v.warp_smem; a.off_msg = v.off_msg; a.off_post = v.off_post; a.off_s = v.off_s;
-  a.off_par = v.off_par; a.off_cand = v.off_cand;
+  a.warp_smem = v.L.warp_smem; a.off_msg = v.L.off_msg; a.off_dec = v.L.off_dec;
+  a.off_s = v.L.off_s; a.off_par = v.L.off_par; a.off_cand = v.L.off_cand;
   a.syn = d_syndromes; a.nshots = (uint32_t)B; a.corr = d_corrections; a.logical = d_logical; a.stats = d_stats;
   a.soft = nullptr; a.obs = nullptr; a.counters = nullptr;
   a.next_shot = ctrl; a.lsd_count = ctrl + 1; a.lsd_shots = lsd_shots; a.lsd_soft = lsd_soft;
   a.scratch = bp_scratch;
-  a.scratch_pitch = t.n;
+  a.scratch_pitch = 2LL * t.n;
   const long long need_ctas = (B + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta;
   const int grid = (int)(need_ctas < bp_grid ? need_ctas : bp_grid);
   if ((e = vibe::launch_bp(a, v.msg_fp16, grid, s)) != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
