@@ -98,7 +98,7 @@ __device__ __forceinline__ void update_column(uint32_t v, int deg, const Tables&
   for (int k = 0; k < DP; ++k) {
     mcv[k] = 0.0f;
     if (k < deg) {
-      const uint32_t c = ent[k] >> 8;
+      const uint32_t c = ent[k] >> 9;
       MT* row = msgs + c * RP;
       Msg<MT>::set_inf(row + (ent[k] & 0xffu));
       float mn = __int_as_float(0x7f800000);
@@ -126,7 +126,7 @@ __device__ __forceinline__ void update_column(uint32_t v, int deg, const Tables&
 #pragma unroll
       for (int k2 = k + 1; k2 < DP; ++k2)
         if (k2 < deg) a = __fadd_rn(a, mcv[k2]);
-      Msg<MT>::store(msgs + (ent[k] >> 8) * RP + (ent[k] & 0xffu), a);
+      Msg<MT>::store(msgs + (ent[k] >> 9) * RP + (ent[k] & 0xffu), a);
       pre = __fadd_rn(pre, mcv[k]);
     }
   }
@@ -134,14 +134,21 @@ __device__ __forceinline__ void update_column(uint32_t v, int deg, const Tables&
   if (e_new != dec8[v]) {
 #pragma unroll
     for (int k = 0; k < DP; ++k)
-      if (k < deg) par8[ent[k] >> 8] ^= 1u;
+      if (k < deg) par8[ent[k] >> 9] ^= 1u;
     dec8[v] = e_new;
   }
   if (lpost) lpost[v] = L;
 }
 
+// Blocks per SM the register budget targets: FP16 states are small enough for 24 warps per SM,
+// FP32 states (twice the message bytes) fill shared memory at about 16-18.
+template <typename MT>
+struct MinBlocks { static constexpr int value = 16 / kBpWarpsPerCta; };
+template <>
+struct MinBlocks<__half> { static constexpr int value = 24 / kBpWarpsPerCta; };
+
 template <typename MT, int DP, int RPC>
-__global__ void __launch_bounds__(kBpWarpsPerCta * 32, 16 / kBpWarpsPerCta) k_bp(const BpArgs a) {
+__global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_bp(const BpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Tables& t = a.t;
   const int lane = threadIdx.x & 31;
@@ -220,6 +227,7 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32, 16 / kBpWarpsPerCta) k_bp
         for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
       }
       __syncwarp();
+
       const uint32_t* sch = t.sched + (size_t)i * n;
       const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
       const int nl = __ldg(t.nlev + i);

@@ -55,8 +55,9 @@ __global__ void k_csc_fill(const int32_t* __restrict__ rowptr, const int32_t* __
 }
 
 // Sort each column's entries by check (insertion sort, degree <= 32) and emit rowidx and csc_ent.
-__global__ void k_csc_finish(int n, int DP, const int32_t* __restrict__ colptr, uint32_t* __restrict__ packed,
-                             int32_t* __restrict__ rowidx, uint32_t* __restrict__ csc_ent) {
+__global__ void k_csc_finish(int n, int DP, int RP, int spc, const int32_t* __restrict__ colptr,
+                             uint32_t* __restrict__ packed, int32_t* __restrict__ rowidx,
+                             uint32_t* __restrict__ csc_ent) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     int b = colptr[v], d = colptr[v + 1] - b;
     for (int i = 1; i < d; ++i) {
@@ -67,7 +68,7 @@ __global__ void k_csc_finish(int n, int DP, const int32_t* __restrict__ colptr, 
     }
     for (int k = 0; k < DP; ++k) {
       uint32_t x = k < d ? packed[b + k] : 0u;
-      csc_ent[(size_t)v * DP + k] = x;
+      csc_ent[(size_t)v * DP + k] = k < d ? csc_entry(x >> 8, x & 0xffu, RP, spc) : 0u;
       if (k < d) rowidx[b + k] = (int32_t)(x >> 8);
     }
   }
@@ -83,11 +84,13 @@ __device__ __forceinline__ __half to_msg<__half>(float x) { return __float2half_
 template <typename MT>
 __global__ void k_msg_init(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int m, int RP,
                            const float* __restrict__ lam, MT* __restrict__ out) {
+  const int spc = 16 / (int)sizeof(MT);
   long long total = (long long)m * RP;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    int c = (int)(t / RP), slot = (int)(t % RP);
-    int deg = rowptr[c + 1] - rowptr[c];
+    const int c = (int)(t / RP), pos = (int)(t % RP);
+    const int slot = (int)row_position((uint32_t)c, (uint32_t)pos, RP, spc);   // the XOR swizzle is its own inverse
+    const int deg = rowptr[c + 1] - rowptr[c];
     float x = slot < deg ? lam[colidx[rowptr[c] + slot]] : __int_as_float(0x7f800000);
     out[t] = to_msg<MT>(x);
   }
@@ -190,7 +193,7 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
   k_col_count<<<grid_for(E, 256), 256, 0, s>>>(d_colidx, E, cnt);
   k_scan_single<<<1, 1024, 0, s>>>(cnt, n, d_colptr);
   k_csc_fill<<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_colptr, fill, packed);
-  k_csc_finish<<<grid_for(n, 128), 128, 0, s>>>(n, DP, d_colptr, packed, d_rowidx, d_csc_ent);
+  k_csc_finish<<<grid_for(n, 128), 128, 0, s>>>(n, DP, RP, msg_fp16 ? 8 : 4, d_colptr, packed, d_rowidx, d_csc_ent);
   if (msg_fp16)
     k_msg_init<__half><<<grid_for((long long)m * RP, 256), 256, 0, s>>>(d_rowptr, d_colidx, m, RP, d_lam,
                                                                        static_cast<__half*>(d_msg_init));

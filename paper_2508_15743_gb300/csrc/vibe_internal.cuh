@@ -11,9 +11,25 @@ namespace vibe {
 
 constexpr int kBpWarpsPerCta = 2;   // persistent BP kernel: warps per CTA, one shot per warp
 constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
-constexpr int kMaxRowDeg = 255;     // slot index of an edge inside its check row fits in 8 bits
+constexpr int kMaxRowDeg = 255;     // position of an edge inside its check row fits in 8 bits
 constexpr int kMaxColDeg = 32;
 constexpr uint32_t kFull = 0xffffffffu;
+
+// Position of slot `slot` of check row c inside the message image. A row is RP slots stored as
+// 16-byte chunks of `spc` slots (4 for float, 8 for half). When the row has 2, 4 or 8 chunks their
+// order is XOR-swizzled by the row index so that the same chunk of consecutive rows falls on all
+// eight 16-byte bank groups of shared memory (rows are read by lanes at random, one 16-byte load per
+// chunk). Used by the builder only; the BP kernel reads positions from csc_ent.
+__host__ __device__ inline uint32_t row_position(uint32_t c, uint32_t slot, int RP, int spc) {
+  const int nchunk = RP / spc;
+  const uint32_t sw = (nchunk == 2 || nchunk == 4 || nchunk == 8) ? (c * (uint32_t)nchunk / 8u) % (uint32_t)nchunk : 0u;
+  return slot ^ (sw * (uint32_t)spc);
+}
+
+// Packed csc_ent entry: check << 9 | position of the edge in the check's row of the message image.
+__host__ __device__ inline uint32_t csc_entry(uint32_t c, uint32_t slot, int RP, int spc) {
+  return (c << 9) | row_position(c, slot, RP, spc);
+}
 
 // Device-resident tables of one decoding problem (owned by the handle).
 struct Tables {
@@ -26,7 +42,7 @@ struct Tables {
   const int32_t* colidx;
   const int32_t* colptr;   // H CSC, checks ascending in each column
   const int32_t* rowidx;
-  const uint32_t* csc_ent; // n*DP: (check << 8) | slot-in-row, ascending check, zero padded
+  const uint32_t* csc_ent; // n*DP: csc_entry() of each edge, ascending check, zero padded
   const float* lam;        // n prior LLRs
   const void* msg_init;    // m*RP messages (float or half): lambda of the edge's column, +inf padding
   const uint32_t* sched;   // K*n: column | (degree << 24), grouped by wavefront level
