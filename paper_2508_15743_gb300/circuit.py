@@ -1,0 +1,305 @@
+"""Circuit-level detector error models for the 6.6.6 colour code (seeded-input side).
+
+The decoding problem of circuit-level noise (Sec. II.B): columns are independent fault mechanisms of
+a syndrome-extraction circuit, rows are detectors (parities of measurement outcomes that are fixed
+without noise). This module builds the circuit, propagates every single fault through it as a Pauli
+frame, and merges faults with identical detector and observable signatures. It holds none of the
+decoder's arithmetic.
+
+Circuit (our own schedule; the paper's circuits are third-party). Qubits: the n data qubits, then one
+ancilla per plaquette. Memory in basis B in {X, Z}: data prepared in the +1 eigenstate of B, then
+`rounds` rounds, each measuring all Z-type plaquettes and then all X-type plaquettes with the
+plaquette's ancilla:
+    Z block: reset ancillas | 6 CNOT layers data -> ancilla | measure ancillas (Z basis)
+    X block: reset ancillas | H ancillas | 6 CNOT layers ancilla -> data | H ancillas | measure
+CNOT layer k couples every plaquette with its neighbour in lattice direction k (the six neighbour
+offsets in counter-clockwise order), so no qubit takes part in two gates of one layer. Finally every
+data qubit is measured in basis B.
+
+Detectors: B-type plaquettes are deterministic from the first round (detector = outcome), the other
+type from the second (detector = XOR of consecutive outcomes); B-type plaquettes get a final detector
+comparing the data measurement's plaquette parity with the last round. The observable is the B-type
+logical (the weight-d boundary) read from the final data measurement.
+
+Noise, Si1000-style (Table I, with CNOT as the two-qubit gate): two-qubit depolarising p after each
+CNOT; one-qubit depolarising p/10 after each H and on every qubit idle during a gate layer; bit-flip
+2p after each reset (phase-flip for the |+> data preparation); outcome flip 5p on each measurement;
+one-qubit depolarising 2p on qubits idle during a measurement or reset layer. The Uniform model
+(Table II) uses p everywhere.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .dem import CSR, DEM, color_code_layout
+
+# counter-clockwise lattice directions around a plaquette centre
+_DIRS = ((1, 0), (0, 1), (-1, 1), (-1, 0), (0, -1), (1, -1))
+
+SI1000 = dict(cx=1.0, h=0.1, idle_gate=0.1, reset=2.0, meas=5.0, idle_mr=2.0)
+UNIFORM = dict(cx=1.0, h=1.0, idle_gate=0.0, reset=1.0, meas=1.0, idle_mr=0.0)
+
+# two-qubit Paulis (x1, z1, x2, z2) except the identity, for depolarising channels
+_P2 = [(a & 1, (a >> 1) & 1, b & 1, (b >> 1) & 1) for a in range(4) for b in range(4) if a or b]
+_P1 = [(1, 0), (1, 1), (0, 1)]   # X, Y, Z as (x, z)
+
+
+class _Builder:
+    """Layered circuit with a fault list; faults are simulated in parallel as packed Pauli frames."""
+
+    def __init__(self, nq):
+        self.nq = nq
+        self.moments = []   # list of (gates, faults); gates: list of (kind, args)
+        self.nmeas = 0
+
+    def moment(self):
+        self.moments.append(([], []))
+        return self.moments[-1]
+
+    def gate(self, kind, *args):
+        self.moments[-1][0].append((kind, args))
+        if kind == "M":
+            idx = list(range(self.nmeas, self.nmeas + len(args[0])))
+            self.nmeas += len(args[0])
+            return idx
+        return None
+
+    def fault(self, kind, args, p):
+        if p > 0:
+            self.moments[-1][1].append((kind, args, p))
+
+    def simulate(self):
+        """Measurement-flip record of every single fault: uint64 [nmeas, words], and fault probabilities."""
+        faults = []
+        for mi, (_, fl) in enumerate(self.moments):
+            for kind, args, p in fl:
+                if kind == "DEP1":
+                    for q in args:
+                        for (x, z) in _P1:
+                            faults.append((mi, "P", ((q, x, z),), p / 3.0))
+                elif kind == "DEP2":
+                    for (a, b) in args:
+                        for (x1, z1, x2, z2) in _P2:
+                            faults.append((mi, "P", ((a, x1, z1), (b, x2, z2)), p / 15.0))
+                elif kind == "X":
+                    for q in args:
+                        faults.append((mi, "P", ((q, 1, 0),), p))
+                elif kind == "Z":
+                    for q in args:
+                        faults.append((mi, "P", ((q, 0, 1),), p))
+                elif kind == "MFLIP":
+                    for k in args:
+                        faults.append((mi, "M", k, p))
+        F = len(faults)
+        W = (F + 63) // 64
+        X = np.zeros((self.nq, W), np.uint64)
+        Z = np.zeros((self.nq, W), np.uint64)
+        rec = np.zeros((self.nmeas, W), np.uint64)
+        by_moment = [[] for _ in self.moments]
+        for f, (mi, kind, args, p) in enumerate(faults):
+            by_moment[mi].append((f, kind, args))
+        for mi, (gates, _) in enumerate(self.moments):
+            for kind, args in gates:
+                if kind == "CX":
+                    for c, t in args[0]:
+                        X[t] ^= X[c]
+                        Z[c] ^= Z[t]
+                elif kind == "H":
+                    for q in args[0]:
+                        X[q], Z[q] = Z[q].copy(), X[q].copy()
+                elif kind == "R":
+                    for q in args[0]:
+                        X[q] = 0
+                        Z[q] = 0
+                elif kind == "M":
+                    qs, ks = args[0], args[1]
+                    for q, k in zip(qs, ks):
+                        rec[k] = X[q]
+            for f, kind, args in by_moment[mi]:
+                w, bit = f >> 6, np.uint64(1) << np.uint64(f & 63)
+                if kind == "P":
+                    for (q, x, z) in args:
+                        if x:
+                            X[q, w] ^= bit
+                        if z:
+                            Z[q, w] ^= bit
+                else:
+                    rec[args, w] ^= bit
+        probs = np.array([p for (_, _, _, p) in faults], np.float64)
+        return rec, probs
+
+
+def _unpack_rows(packed, F):
+    """uint64 [r, W] -> uint8 [r, F] bits (fault f is bit f % 64 of word f // 64)."""
+    by = packed.astype("<u8").view(np.uint8).reshape(packed.shape[0], -1)
+    return np.unpackbits(by, axis=1, bitorder="little")[:, :F]
+
+
+def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None) -> DEM:
+    """Detector error model of `rounds` rounds of the colour-code memory circuit in basis X or Z.
+
+    noise: "si1000", "uniform", or "custom" with `custom` a dict of per-location probabilities
+    (keys data_x / data_z: flips on data before each round, meas_z / meas_x: outcome flips of the
+    Z / X plaquette measurements, final_meas: flips of the data measurement) for testing.
+    """
+    qubits, plaqs = color_code_layout(d)
+    n, mp = len(qubits), len(plaqs)
+    qidx = {q: k for k, q in enumerate(qubits)}
+    anc = [n + P for P in range(mp)]
+    nq = n + mp
+    layers = []
+    for (di, dj) in _DIRS:
+        layers.append([(qidx[(i + di, j + dj)], n + P) for P, (i, j) in enumerate(plaqs) if (i + di, j + dj) in qidx])
+    sup = [[qidx[(i + di, j + dj)] for (di, dj) in _DIRS if (i + di, j + dj) in qidx] for (i, j) in plaqs]
+    logical = sorted(qidx[q] for q in qubits if q[1] == -1)
+    if noise == "si1000":
+        w = SI1000
+    elif noise == "uniform":
+        w = UNIFORM
+    elif noise == "custom":
+        w = None
+        custom = dict(custom or {})
+    else:
+        raise ValueError(noise)
+
+    B = _Builder(nq)
+    allq = list(range(nq))
+
+    def idle(busy, factor):
+        if w is None:
+            return
+        rest = [q for q in allq if q not in busy]
+        B.fault("DEP1", rest, factor * p)
+
+    # data preparation in the +1 eigenstate of the memory basis
+    B.moment()
+    B.gate("R", list(range(n)))
+    if basis == "X":
+        B.gate("H", list(range(n)))
+    if w is not None:
+        B.fault("Z" if basis == "X" else "X", list(range(n)), w["reset"] * p)
+        idle(set(range(n)), w["idle_mr"])
+    mz, mx = [], []
+    for r in range(rounds):
+        if w is None:
+            B.moment()
+            B.fault("X", list(range(n)), custom.get("data_x", 0.0))
+            B.fault("Z", list(range(n)), custom.get("data_z", 0.0))
+        # Z block
+        B.moment()
+        B.gate("R", anc)
+        if w is not None:
+            B.fault("X", anc, w["reset"] * p)
+            idle(set(anc), w["idle_mr"])
+        for L in layers:
+            B.moment()
+            B.gate("CX", L)
+            if w is not None:
+                B.fault("DEP2", L, w["cx"] * p)
+                idle({q for pr in L for q in pr}, w["idle_gate"])
+        B.moment()
+        ks = B.gate("M", anc, None)
+        B.moments[-1][0][-1] = ("M", (anc, ks))
+        mz.append(ks)
+        if w is not None:
+            B.fault("MFLIP", ks, w["meas"] * p)
+            idle(set(anc), w["idle_mr"])
+        else:
+            B.fault("MFLIP", ks, custom.get("meas_z", 0.0))
+        # X block
+        B.moment()
+        B.gate("R", anc)
+        if w is not None:
+            B.fault("X", anc, w["reset"] * p)
+            idle(set(anc), w["idle_mr"])
+        B.moment()
+        B.gate("H", anc)
+        if w is not None:
+            B.fault("DEP1", anc, w["h"] * p)
+            idle(set(anc), w["idle_gate"])
+        for L in layers:
+            B.moment()
+            B.gate("CX", [(a, q) for (q, a) in L])
+            if w is not None:
+                B.fault("DEP2", [(a, q) for (q, a) in L], w["cx"] * p)
+                idle({q for pr in L for q in pr}, w["idle_gate"])
+        B.moment()
+        B.gate("H", anc)
+        if w is not None:
+            B.fault("DEP1", anc, w["h"] * p)
+            idle(set(anc), w["idle_gate"])
+        B.moment()
+        ks = B.gate("M", anc, None)
+        B.moments[-1][0][-1] = ("M", (anc, ks))
+        mx.append(ks)
+        if w is not None:
+            B.fault("MFLIP", ks, w["meas"] * p)
+            idle(set(anc), w["idle_mr"])
+        else:
+            B.fault("MFLIP", ks, custom.get("meas_x", 0.0))
+    # final data measurement in the memory basis
+    B.moment()
+    if basis == "X":
+        B.gate("H", list(range(n)))
+    B.moment()
+    kd = B.gate("M", list(range(n)), None)
+    B.moments[-1][0][-1] = ("M", (list(range(n)), kd))
+    if w is not None:
+        B.fault("MFLIP", kd, w["meas"] * p)
+    else:
+        B.fault("MFLIP", kd, custom.get("final_meas", 0.0))
+
+    rec, probs = B.simulate()
+    # detectors as lists of measurement indices
+    det_meas, det_type = [], []
+    same, other = (mx, mz) if basis == "X" else (mz, mx)
+    obasis = "Z" if basis == "X" else "X"
+    for r in range(rounds):
+        for P in range(mp):
+            det_meas.append([same[r][P]] if r == 0 else [same[r][P], same[r - 1][P]])
+            det_type.append(basis)
+        if r > 0:
+            for P in range(mp):
+                det_meas.append([other[r][P], other[r - 1][P]])
+                det_type.append(obasis)
+    for P in range(mp):
+        det_meas.append([kd[q] for q in sup[P]] + ([same[rounds - 1][P]] if rounds > 0 else []))
+        det_type.append(basis)
+    obs_meas = [kd[q] for q in logical]
+    F = len(probs)
+    Wd = rec.shape[1]
+    D = np.zeros((len(det_meas) + 1, Wd), np.uint64)
+    for i, ms in enumerate(det_meas):
+        for k in ms:
+            D[i] ^= rec[k]
+    for k in obs_meas:
+        D[-1] ^= rec[k]
+    bits = _unpack_rows(D, F)                     # [ndet + 1, F]
+    keys = np.packbits(bits, axis=0, bitorder="little").T.copy()   # [F, bytes]
+    flips_det = bits[:-1].any(axis=0)
+    keep = np.nonzero(flips_det)[0]
+    void = np.ascontiguousarray(keys[keep]).view(np.dtype((np.void, keys.shape[1]))).ravel()
+    uniq, first, inv = np.unique(void, return_index=True, return_inverse=True)
+    order = np.argsort(first)                     # columns in order of first appearance
+    rank = np.empty_like(order)
+    rank[order] = np.arange(len(order))
+    col_of_fault = rank[inv]
+    ncol = len(uniq)
+    # combine independent mechanisms with the same signature: P(odd number) = (1 - prod(1 - 2 p_i)) / 2
+    logs = np.zeros(ncol)
+    np.add.at(logs, col_of_fault, np.log1p(-2.0 * probs[keep]))
+    pcol = 0.5 * (1.0 - np.exp(logs))
+    rep = keep[first[order]]                      # representative fault of each column
+    rows = [[] for _ in range(len(det_meas))]
+    lcols = []
+    for c, f in enumerate(rep):
+        for r in np.nonzero(bits[:-1, f])[0]:
+            rows[r].append(c)
+        if bits[-1, f]:
+            lcols.append(c)
+    H = CSR.from_rows(rows, ncol)
+    L = CSR.from_rows([lcols], ncol)
+    undetectable = float(probs[(~flips_det) & (bits[-1] == 1)].sum())
+    return DEM(H, L, pcol.astype(np.float64), name=f"cc666_d{d}_circuit_{noise}_{basis}_r{rounds}_p{p}",
+               meta={"d": d, "rounds": rounds, "p": p, "noise": noise, "basis": basis, "faults": F,
+                     "undetectable_logical_prob": undetectable, "det_type": det_type})

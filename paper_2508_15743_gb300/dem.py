@@ -93,18 +93,16 @@ class DEM:
 # Triangular 6.6.6 colour code (Sec. II.A)
 # --------------------------------------------------------------------------------------------
 
-def color_code_666(d: int):
-    """Triangular hexagonal-tiling colour code of odd distance d.
+def color_code_layout(d: int):
+    """Lattice layout of the distance-d triangular 6.6.6 colour code.
 
-    Construction: plaquette centres are the points (i, j) of the triangular lattice with
-    (i - j) = 0 mod 3; every other lattice point is a qubit (together they form the honeycomb's
-    vertices). The code occupies the closed lattice triangle i >= 0, j >= -1, i + j <= 3(d-1)/2 - 1,
-    whose three corners are qubits. A plaquette acts on its lattice neighbours inside the triangle:
-    six in the bulk, four on the boundary. This gives n = (3d^2 + 1)/4 qubits and (n - 1)/2
-    plaquettes (Sec. II.A).
+    Plaquette centres are the points (i, j) of the triangular lattice with (i - j) = 0 mod 3; every
+    other lattice point is a qubit (together they form the honeycomb's vertices). The code occupies
+    the closed lattice triangle i >= 0, j >= -1, i + j <= 3(d-1)/2 - 1, whose three corners are
+    qubits. A plaquette acts on its lattice neighbours inside the triangle: six in the bulk, four on
+    the boundary. This gives n = (3d^2 + 1)/4 qubits and (n - 1)/2 plaquettes (Sec. II.A).
 
-    Returns (H, L_support, coords): H the plaquette/qubit incidence as a CSR, L_support the sorted
-    qubit indices of the weight-d logical on the j = -1 boundary, coords the (i, j) of each qubit.
+    Returns (qubits, plaquettes): lists of (i, j) coordinates, in the index order used everywhere.
     """
     if d < 3 or d % 2 == 0:
         raise ValueError("distance must be odd and >= 3")
@@ -113,15 +111,24 @@ def color_code_666(d: int):
     c = side + a + b
     pts = [(i, j) for j in range(b, c - a + 1) for i in range(a, c - j + 1)]
     qubits = [p for p in pts if (p[0] - p[1]) % 3 != 0]
+    plaqs = [p for p in pts if (p[0] - p[1]) % 3 == 0]
+    return qubits, plaqs
+
+
+def color_code_666(d: int):
+    """Triangular hexagonal-tiling colour code of odd distance d (layout in color_code_layout).
+
+    Returns (H, L_support, coords): H the plaquette/qubit incidence as a CSR, L_support the sorted
+    qubit indices of the weight-d logical on the j = -1 boundary, coords the (i, j) of each qubit.
+    """
+    qubits, plaq_pts = color_code_layout(d)
     qidx = {q: k for k, q in enumerate(qubits)}
     plaqs = []
-    for (i, j) in pts:
-        if (i - j) % 3:
-            continue
+    for (i, j) in plaq_pts:
         sup = sorted(qidx[(i + di, j + dj)] for di, dj in _TRI_NEIGHBOURS if (i + di, j + dj) in qidx)
         plaqs.append(sup)
     H = CSR.from_rows(plaqs, len(qubits))
-    logical = sorted(qidx[q] for q in qubits if q[1] == b)
+    logical = sorted(qidx[q] for q in qubits if q[1] == -1)
     return H, np.asarray(logical, dtype=np.int32), qubits
 
 

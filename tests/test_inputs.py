@@ -147,3 +147,70 @@ def test_schedules_are_permutations():
     assert len({tuple(r) for r in P}) == 16
     nat = D.schedules(19, 1, 0, natural=True)
     assert np.array_equal(nat[0], np.arange(19))
+
+
+# ------------------------------------------------------------------------------------------------
+# Circuit-level detector error models (circuit.py)
+# ------------------------------------------------------------------------------------------------
+
+from paper_2508_15743_gb300 import circuit as C  # noqa: E402
+
+
+@pytest.mark.parametrize("d,R", [(3, 2), (5, 4), (9, 9)])
+def test_circuit_builder_reproduces_phenomenological_dem(d, R):
+    """Z memory with only data bit flips and Z-measurement flips is the phenomenological model:
+    the Pauli-frame builder must give the closed-form matrix, priors and logical, column for column."""
+    dm = C.circuit_dem(d, R, 0.0, noise="custom", basis="Z", custom=dict(data_x=0.01, meas_z=0.02))
+    ph = D.phenomenological_dem(d, R, 0.01, 0.02)
+    rows = [i for i, t in enumerate(dm.meta["det_type"]) if t == "Z"]
+    A = dm.H.to_dense()
+    assert not np.delete(A, rows, axis=0).any(), "X-type detectors see no X errors"
+    A = A[rows]
+    B = ph.H.to_dense()
+    assert A.shape == B.shape
+    la, lb = set(dm.L.row(0).tolist()), set(ph.L.row(0).tolist())
+    ka = sorted((tuple(A[:, j]), round(float(dm.priors[j]), 15), j in la) for j in range(dm.n))
+    kb = sorted((tuple(B[:, j]), round(float(ph.priors[j]), 15), j in lb) for j in range(ph.n))
+    assert ka == kb
+
+
+@pytest.mark.parametrize("basis", ["X", "Z"])
+def test_circuit_dem_invariants(basis):
+    dm = C.circuit_dem(5, 5, 1e-3, noise="si1000", basis=basis)
+    mp = 9
+    assert dm.m == mp * 2 * 5, "B-type: 5 rounds + final; other type: rounds 2..5"
+    coldeg = np.bincount(dm.H.colidx, minlength=dm.n)
+    assert coldeg.min() >= 1, "every column flips a detector"
+    assert np.diff(dm.H.rowptr).min() >= 1
+    assert ((dm.priors > 0) & (dm.priors < 0.5)).all()
+    assert dm.meta["undetectable_logical_prob"] == 0.0, "no single fault flips the logical unseen"
+    # columns are distinct signatures
+    A = dm.H.to_dense()
+    lcols = set(dm.L.row(0).tolist())
+    sig = {(tuple(A[:, j]), j in lcols) for j in range(dm.n)}
+    assert len(sig) == dm.n
+    # merged priors never exceed the sum of their parts: the total probability mass is at most the
+    # fault list's, and each column is a probability of an odd number of its faults
+    assert dm.priors.sum() < 5 * 1e-3 * dm.meta["faults"]
+
+
+def test_circuit_single_faults_get_valid_corrections():
+    """Every single fault of a d=3 circuit DEM gets a correction with H e = s (oracle, exhaustive).
+
+    The logical class is not pinned: the schedule's hook errors give pairs of single faults with the
+    same syndrome and different logical effect (circuit distance 2 at d = 3), and Si1000's unequal
+    priors let lighter multi-fault explanations win."""
+    import oracle
+    dm = C.circuit_dem(3, 3, 1e-3, noise="si1000", basis="X")
+    errs = np.eye(dm.n, dtype=np.uint8)
+    syn, obs = D.syndromes_of(dm, errs)
+    perms = D.schedules(dm.n, 8, 1)
+    out = oracle.decode(dm, perms, syn, 20, 0.625, 3, nthreads=8)
+    e = D.unpack_bits(out["corrections"], dm.n)
+    s2, _ = D.syndromes_of(dm, e)
+    assert np.array_equal(s2, syn)
+    A = dm.H.to_dense()
+    groups = {}
+    for j in range(dm.n):
+        groups.setdefault(tuple(A[:, j]), set()).add(j in set(dm.L.row(0).tolist()))
+    assert any(len(v) == 2 for v in groups.values()), "hook errors of this schedule (documented)"
