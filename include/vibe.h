@@ -36,6 +36,8 @@ extern "C" {
 
 #define VIBE_STATUS_OK 0
 #define VIBE_STATUS_UNSOLVABLE 1 /* syndrome outside the column span of H; correction is zero */
+#define VIBE_STATUS_BAD_PROBLEM 2 /* vibe_batch_decode: problem index outside 0..count-1; nothing decoded,
+                                     correction and logical words zero */
 
 /* Sparse binary matrix in CSR form, host memory; copied by vibe_create. colidx ascending, no
  * duplicates within a row. */
@@ -74,9 +76,11 @@ typedef struct {
 #define VIBE_CNT_LSD 2         /* shots sent to LSD */
 #define VIBE_CNT_PAIR_ITERS 3  /* BP sweeps executed, summed over (shot, member) pairs */
 #define VIBE_CNT_UNSOLVABLE 4
+#define VIBE_CNT_BAD_PROBLEM 5 /* vibe_batch_decode shots with an out-of-range problem index */
 #define VIBE_NUM_COUNTERS 8
 
 typedef struct vibe_handle vibe_handle;
+typedef struct vibe_batch vibe_batch; /* opaque: several handles decoded in one launch */
 
 /*
  * vibe_create -- offline setup (Sec. III.D.1).
@@ -172,6 +176,55 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
  */
 int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
                         uint32_t* d_logical, vibe_shot_stats* d_stats, void* stream);
+
+/*
+ * vibe_autotune -- times the decode of a sample batch (d_syndromes: B >= 1 shots, device) with a few
+ * persistent-grid sizes for the BP and LSD kernels (occupancy maximum, 3/4 and 1/2 of it for BP;
+ * maximum and half for LSD) and keeps the fastest for this handle. Decoding results do not depend
+ * on the grid sizes (shots are independent; each shot's arithmetic is fixed), only the time does.
+ * Synchronous; allocates a B-shot output buffer for the duration of the call and the workspace.
+ * The chosen sizes (CTAs per SM) are returned when the pointers are not NULL.
+ *   Errors: VIBE_ERR_INVALID, VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
+ */
+int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream,
+                  int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm);
+
+/*
+ * Mixed batches. The paper decodes one detector error model per run; a decoding service often holds
+ * several (code distances, noise models, X and Z memory) and receives shots for all of them. A
+ * vibe_batch groups up to 64 handles so that one pair of kernel launches decodes a batch whose shots
+ * belong to different problems: every shot names its problem, and each shot's decoding is exactly
+ * the decoding vibe_decode gives it with that problem's handle (same members, schedules, limits).
+ *
+ * vibe_batch_create -- handles[0..count) (1 <= count <= 64, non-NULL, created on the current
+ *   device, all with the same msg_fp16) are referenced, not copied: they must outlive the batch and
+ *   must not be destroyed first. The batch owns a device copy of their descriptors and its own
+ *   workspace. Errors: VIBE_ERR_INVALID (bad count/handles, mixed devices or message precisions,
+ *   device not current), VIBE_ERR_UNSUPPORTED (the largest problem's state with the batch's
+ *   descriptor table does not fit in shared memory), VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
+ */
+int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** out);
+
+/*
+ * vibe_batch_decode -- decodes B shots of mixed problems, asynchronous on `stream`.
+ *   d_problem: B int32 problem indices into the handles given to vibe_batch_create (device). Shot b's
+ *   syndrome is d_syndromes[b * syn_stride ...], its first ceil(m_p/32) words meaningful (padding bits
+ *   zero); syn_stride >= the largest ceil(m/32). d_corrections (corr_stride >= the largest
+ *   ceil(n/32)) receives ceil(n_p/32) words per shot; words past them are left untouched.
+ *   d_logical and d_observables (may be NULL) use log_stride >= the largest ceil(k/32) when given.
+ *   d_stats and d_counters as for vibe_decode; no soft output. A shot whose index is outside
+ *   0..count-1 is not decoded: its status is VIBE_STATUS_BAD_PROBLEM and its corr_stride correction
+ *   words (and log_stride logical words) are zero. Calls on one batch must not overlap in time.
+ *   Errors: VIBE_ERR_INVALID (NULL batch/required pointer, B < 0, strides too small), VIBE_ERR_NOMEM,
+ *   VIBE_ERR_CUDA. B = 0 is a no-op.
+ */
+int vibe_batch_decode(vibe_batch* b, const int32_t* d_problem, const uint32_t* d_syndromes, int32_t syn_stride,
+                      int64_t B, uint32_t* d_corrections, int32_t corr_stride, uint32_t* d_logical,
+                      int32_t log_stride, vibe_shot_stats* d_stats, const uint32_t* d_observables,
+                      uint64_t* d_counters, void* stream);
+
+/* vibe_batch_destroy -- frees the batch's device memory; the handles stay valid. NULL is accepted. */
+int vibe_batch_destroy(vibe_batch* b);
 
 /* vibe_destroy -- frees every device and host resource of the handle. NULL is accepted. */
 int vibe_destroy(vibe_handle* h);

@@ -1,7 +1,9 @@
 // Host side of the C ABI declared in include/vibe.h: input validation, the resident device tables
-// of a decoding problem, the batch workspace, and the launch sequence of one decode
-// (persistent BP ensemble -> LSD on the unresolved shots), chunked when a batch outgrows the workspace.
+// of a decoding problem, batch workspaces, the launch sequence of one decode (persistent BP ensemble
+// -> LSD on the unresolved shots, chunked when a batch outgrows the workspace), mixed batches over
+// several problems, kernel timing and the launch-size tuner.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,10 +14,7 @@
 
 #include "vibe_internal.cuh"
 
-namespace vibe {
-long long lsd_scratch_words(const Tables& t);
-}
-
+using vibe::Bounds;
 using vibe::Tables;
 
 namespace {
@@ -37,13 +36,13 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(VIBE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define VIBE_CUDA(call, what)                 \
-  do {                                        \
-    cudaError_t e_ = (call);                  \
+#define VIBE_CUDA(call, what)                          \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-constexpr size_t kWorkspaceBytes = size_t(4) << 30;   // LSD hand-off buffer budget per handle
+constexpr size_t kWorkspaceBytes = size_t(4) << 30;   // LSD hand-off buffer budget per workspace
 
 int check_csr(const vibe_csr* A, const char* name, bool rows_nonempty) {
   if (!A || !A->rowptr || (!A->colidx && A->nrows > 0)) return fail(VIBE_ERR_INVALID, "%s: NULL matrix", name);
@@ -70,47 +69,190 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
+// What one decode launch needs besides the batch buffers.
+struct Launch {
+  Tables one{};                     // host descriptor of a single-problem launch
+  bool mixed = false;               // shots name their problems (vibe_batch)
+  const Tables* d_desc = nullptr;   // ndem problem descriptors on the device
+  int ndem = 0;
+  Bounds bnd{};
+  int msg_fp16 = 0;
+  int device = 0, num_sms = 0;
+  int bp_blocks_per_sm = 0, lsd_blocks_per_sm = 0;
+  int bp_grid() const { return std::max(1, bp_blocks_per_sm * num_sms); }
+  int lsd_grid() const { return std::max(1, lsd_blocks_per_sm * num_sms); }
+};
+
+// Device memory a decode uses besides its inputs and outputs; grown on demand, reused afterwards.
+struct Workspace {
+  long long chunk = 0, chunk_max = 0;
+  int bp_warps = 0, lsd_ctas = 0, pitch_m = 0;
+  unsigned int* ctrl = nullptr;   // [0] next shot, [1] LSD count, [2] next LSD shot
+  uint32_t* lsd_shots = nullptr;
+  float* lsd_soft = nullptr;
+  float* bp_scratch = nullptr;
+  uint32_t* lsd_scratch = nullptr;
+
+  void release() {
+    cudaFree(ctrl); cudaFree(lsd_shots); cudaFree(lsd_soft); cudaFree(bp_scratch); cudaFree(lsd_scratch);
+    ctrl = nullptr; lsd_shots = nullptr; lsd_soft = nullptr; bp_scratch = nullptr; lsd_scratch = nullptr;
+    chunk = 0;
+  }
+  int ensure(const Launch& L, long long need) {
+    const long long want = std::min(need, chunk_max);
+    if (ctrl && want <= chunk && L.bp_grid() * vibe::kBpWarpsPerCta <= bp_warps && L.lsd_grid() <= lsd_ctas)
+      return VIBE_OK;
+    const long long c = std::max(want, chunk);
+    release();
+    const Bounds& b = L.bnd;
+    const int warps = L.bp_grid() * vibe::kBpWarpsPerCta;
+    VIBE_CUDA(dalloc(&ctrl, 4), "workspace");
+    VIBE_CUDA(dalloc(&lsd_shots, (size_t)c), "workspace");
+    VIBE_CUDA(dalloc(&lsd_soft, (size_t)c * b.n), "workspace");
+    VIBE_CUDA(dalloc(&bp_scratch, (size_t)warps * (size_t)(2 + b.M) * b.n), "workspace");
+    VIBE_CUDA(dalloc(&lsd_scratch, (size_t)L.lsd_grid() * (size_t)vibe::lsd_scratch_words(b)), "workspace");
+    chunk = c;
+    bp_warps = warps;
+    lsd_ctas = L.lsd_grid();
+    return VIBE_OK;
+  }
+  ~Workspace() { release(); }
+};
+
+// CUDA events around every kernel launch while enabled.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  long long bp_launches = 0, lsd_launches = 0;
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  ~Profiler() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct Batch {
+  const int32_t* dem_of_shot;
+  const uint32_t* syn;
+  int syn_stride;
+  long long B;
+  uint32_t* corr;
+  int corr_stride;
+  uint32_t* logical;
+  int log_stride;
+  vibe_shot_stats* stats;
+  float* soft;
+  int soft_stride;
+  const uint32_t* obs;
+  unsigned long long* counters;
+};
+
+int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, cudaStream_t s) {
+  int rc = ws.ensure(L, q.B);
+  if (rc != VIBE_OK) return rc;
+  for (long long b0 = 0; b0 < q.B; b0 += ws.chunk) {
+    const long long nb = std::min(ws.chunk, q.B - b0);
+    VIBE_CUDA(cudaMemsetAsync(ws.ctrl, 0, 4 * sizeof(unsigned int), s), "decode");
+    vibe::BpArgs a{};
+    a.one = L.one;
+    a.dems = L.d_desc; a.ndem = L.ndem; a.dem_of_shot = q.dem_of_shot ? q.dem_of_shot + b0 : nullptr;
+    a.bnd = L.bnd;
+    a.want_soft = q.soft != nullptr;
+    a.syn = q.syn + (size_t)b0 * q.syn_stride; a.syn_stride = q.syn_stride;
+    a.nshots = (uint32_t)nb;
+    a.corr = q.corr + (size_t)b0 * q.corr_stride; a.corr_stride = q.corr_stride;
+    a.logical = q.logical ? q.logical + (size_t)b0 * q.log_stride : nullptr; a.log_stride = q.log_stride;
+    a.stats = q.stats ? q.stats + b0 : nullptr;
+    a.soft = q.soft ? q.soft + (size_t)b0 * q.soft_stride : nullptr; a.soft_stride = q.soft_stride;
+    a.obs = q.obs ? q.obs + (size_t)b0 * q.log_stride : nullptr;
+    a.counters = q.counters;
+    a.next_shot = ws.ctrl; a.lsd_count = ws.ctrl + 1; a.lsd_shots = ws.lsd_shots; a.lsd_soft = ws.lsd_soft;
+    a.scratch = ws.bp_scratch;
+    a.scratch_pitch = (long long)(2 + L.bnd.M) * L.bnd.n;
+    const int bp_grid = (int)std::min<long long>(L.bp_grid(), (nb + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (prof.on) { e0 = prof.next(); e1 = prof.next(); e2 = prof.next(); }
+    if (e0) cudaEventRecord(e0, s);
+    VIBE_CUDA(vibe::launch_bp(a, L.msg_fp16, bp_grid, s), "BP kernel launch");
+    if (e1) cudaEventRecord(e1, s);
+    vibe::LsdArgs l{};
+    l.dems = L.d_desc; l.ndem = L.ndem; l.dem_of_shot = a.dem_of_shot; l.bnd = L.bnd;
+    l.want_soft = a.want_soft;
+    l.syn = a.syn; l.syn_stride = q.syn_stride;
+    l.corr = a.corr; l.corr_stride = q.corr_stride;
+    l.logical = a.logical; l.log_stride = q.log_stride;
+    l.stats = a.stats; l.soft = a.soft; l.soft_stride = q.soft_stride; l.obs = a.obs;
+    l.counters = q.counters;
+    l.lsd_count = ws.ctrl + 1; l.lsd_shots = ws.lsd_shots; l.lsd_soft = ws.lsd_soft; l.lsd_next = ws.ctrl + 2;
+    l.scratch = ws.lsd_scratch;
+    l.scratch_pitch = vibe::lsd_scratch_words(L.bnd);
+    VIBE_CUDA(vibe::launch_lsd(l, L.lsd_grid(), s), "LSD kernel launch");
+    if (e2) cudaEventRecord(e2, s);
+    prof.bp_launches++;
+    prof.lsd_launches++;
+  }
+  return VIBE_OK;
+}
+
+// Occupancy-limited launch sizes for a launch configuration; fails if a kernel cannot be resident.
+int size_launch(Launch& L) {
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, L.device);
+  const size_t bp_smem = vibe::bp_cta_smem_bytes(L.bnd, L.mixed ? L.ndem : 0);
+  if (bp_smem > (size_t)optin)
+    return fail(VIBE_ERR_UNSUPPORTED, "BP state of one shot (%d bytes per warp) does not fit in shared memory",
+                L.bnd.warp_smem);
+  if (vibe::lsd_smem_bytes(L.bnd, L.ndem) > (size_t)optin)
+    return fail(VIBE_ERR_UNSUPPORTED, "LSD state of one shot does not fit in shared memory");
+  VIBE_CUDA(vibe::bp_occupancy(L.bnd, L.mixed ? L.ndem : 0, L.msg_fp16, &L.bp_blocks_per_sm), "BP occupancy");
+  VIBE_CUDA(vibe::lsd_occupancy(L.bnd, L.ndem, &L.lsd_blocks_per_sm), "LSD occupancy");
+  if (L.bp_blocks_per_sm < 1 || L.lsd_blocks_per_sm < 1)
+    return fail(VIBE_ERR_UNSUPPORTED, "kernels cannot be resident with this problem size");
+  return VIBE_OK;
+}
+
+Bounds bounds_of(const Tables& t) {
+  Bounds b{};
+  b.m = t.m; b.n = t.n; b.W = t.W; b.nw = t.nw; b.kw = t.kw; b.M = t.M; b.DP = t.DP; b.RP = t.RP;
+  b.warp_smem = t.warp_smem; b.lsd_order = t.lsd_order;
+  return b;
+}
+
+void widen(Bounds& b, const Tables& t) {
+  b.m = std::max(b.m, t.m); b.n = std::max(b.n, t.n); b.W = std::max(b.W, t.W); b.nw = std::max(b.nw, t.nw);
+  b.kw = std::max(b.kw, t.kw); b.M = std::max(b.M, t.M); b.DP = std::max(b.DP, t.DP);
+  b.RP = b.RP == t.RP ? b.RP : 0;
+  b.warp_smem = std::max(b.warp_smem, t.warp_smem); b.lsd_order = std::max(b.lsd_order, t.lsd_order);
+}
+
 }  // namespace
 
 struct vibe_handle {
   int device = 0;
-  int num_sms = 0;
-  Tables t{};
-  int T = 0, M = 0, lsd_order = 0, msg_fp16 = 0;
-  float alpha = 0.f;
+  Tables t{};                 // host copy of the problem descriptor
+  Tables* d_desc = nullptr;   // device copy
+  Launch L;
+  Workspace ws;
+  Profiler prof;
   // resident tables
   int32_t *rowptr = nullptr, *colidx = nullptr, *colptr = nullptr, *rowidx = nullptr;
   int32_t *lrowptr = nullptr, *lcolidx = nullptr, *nlev = nullptr;
   uint32_t *csc_ent = nullptr, *sched = nullptr, *lvl_off = nullptr, *perm = nullptr;
   float* lam = nullptr;
   void* msg_init = nullptr;
-  // launch configuration
-  vibe::BpLayout L{};
-  int bp_blocks_per_sm = 0, lsd_blocks_per_sm = 0;
-  // workspace (grown on demand)
-  long long ws_chunk = 0;
-  long long chunk_max = 0;
-  unsigned int* ctrl = nullptr;           // [0] next shot, [1] LSD count, [2] next LSD shot
-  uint32_t* lsd_shots = nullptr;
-  float* lsd_soft = nullptr;
-  float* bp_scratch = nullptr;
-  uint32_t* lsd_scratch = nullptr;
   unsigned long long* tmp_counters = nullptr;
   // host-buffer staging
   long long stage_cap = 0;
   uint32_t *st_syn = nullptr, *st_corr = nullptr, *st_log = nullptr, *st_obs = nullptr;
   vibe_shot_stats* st_stats = nullptr;
-  // kernel timing
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  long long bp_launches = 0, lsd_launches = 0;
 
-  void release_workspace() {
-    cudaFree(ctrl); cudaFree(lsd_shots); cudaFree(lsd_soft); cudaFree(bp_scratch); cudaFree(lsd_scratch);
-    ctrl = nullptr; lsd_shots = nullptr; lsd_soft = nullptr; bp_scratch = nullptr; lsd_scratch = nullptr;
-    ws_chunk = 0;
-  }
   void release_stage() {
     cudaFree(st_syn); cudaFree(st_corr); cudaFree(st_log); cudaFree(st_obs); cudaFree(st_stats);
     st_syn = st_corr = st_log = st_obs = nullptr; st_stats = nullptr; stage_cap = 0;
@@ -119,97 +261,51 @@ struct vibe_handle {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(device);
-    release_workspace();
+    ws.release();
     release_stage();
     cudaFree(tmp_counters);
     cudaFree(rowptr); cudaFree(colidx); cudaFree(colptr); cudaFree(rowidx); cudaFree(lrowptr); cudaFree(lcolidx);
     cudaFree(nlev); cudaFree(csc_ent); cudaFree(sched); cudaFree(lvl_off); cudaFree(perm); cudaFree(lam);
-    cudaFree(msg_init);
-    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    cudaFree(msg_init); cudaFree(d_desc);
     cudaSetDevice(prev);
   }
-  int bp_grid() const { return std::max(1, bp_blocks_per_sm * num_sms); }
-  int lsd_grid() const { return std::max(1, lsd_blocks_per_sm * num_sms); }
 };
 
-namespace {
+struct vibe_batch {
+  int device = 0;
+  std::vector<vibe_handle*> hs;
+  Tables* d_desc = nullptr;
+  Launch L;
+  Workspace ws;
+  Profiler prof;
+  ~vibe_batch() {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    ws.release();
+    cudaFree(d_desc);
+    cudaSetDevice(prev);
+  }
+};
 
-int ensure_workspace(vibe_handle* h, long long need) {
-  const long long chunk = std::min(need, h->chunk_max);
-  if (h->ctrl && chunk <= h->ws_chunk) return VIBE_OK;
-  h->release_workspace();
-  const Tables& t = h->t;
-  const long long bp_warps = (long long)h->bp_grid() * vibe::kBpWarpsPerCta;
-  VIBE_CUDA(dalloc(&h->ctrl, 4), "workspace");
-  VIBE_CUDA(dalloc(&h->lsd_shots, (size_t)chunk), "workspace");
-  VIBE_CUDA(dalloc(&h->lsd_soft, (size_t)chunk * t.n), "workspace");
-  VIBE_CUDA(dalloc(&h->bp_scratch, (size_t)bp_warps * (size_t)(2 + h->M) * t.n), "workspace");
-  VIBE_CUDA(dalloc(&h->lsd_scratch, (size_t)h->lsd_grid() * (size_t)vibe::lsd_scratch_words(t)), "workspace");
-  h->ws_chunk = chunk;
+namespace vibe {
+
+int handle_view(const vibe_handle* h, HandleView* v) {
+  if (!h || !v) return fail(VIBE_ERR_INVALID, "NULL handle");
+  v->t = h->t;
+  v->d_desc = h->d_desc;
+  v->bnd = h->L.bnd;
+  v->device = h->device;
+  v->num_sms = h->L.num_sms;
+  v->msg_fp16 = h->L.msg_fp16;
+  v->bp_grid = h->L.bp_grid();
+  v->lsd_grid = h->L.lsd_grid();
   return VIBE_OK;
 }
 
-cudaEvent_t next_event(vibe_handle* h) {
-  if (h->ev_used == h->ev_pool.size()) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    h->ev_pool.push_back(e);
-  }
-  return h->ev_pool[h->ev_used++];
-}
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
-int decode_device(vibe_handle* h, const uint32_t* syn, long long B, uint32_t* corr, uint32_t* logical,
-                  vibe_shot_stats* stats, float* soft, const uint32_t* obs, unsigned long long* counters,
-                  cudaStream_t s) {
-  int rc = ensure_workspace(h, B);
-  if (rc != VIBE_OK) return rc;
-  const Tables& t = h->t;
-  for (long long b0 = 0; b0 < B; b0 += h->ws_chunk) {
-    const long long nb = std::min(h->ws_chunk, B - b0);
-    VIBE_CUDA(cudaMemsetAsync(h->ctrl, 0, 4 * sizeof(unsigned int), s), "decode");
-    vibe::BpArgs a{};
-    a.t = t;
-    a.T = h->T; a.M = h->M; a.alpha = h->alpha; a.want_soft = soft != nullptr;
-    a.warp_smem = h->L.warp_smem; a.off_msg = h->L.off_msg; a.off_dec = h->L.off_dec;
-    a.off_s = h->L.off_s; a.off_par = h->L.off_par; a.off_cand = h->L.off_cand;
-    a.syn = syn + (size_t)b0 * t.mw;
-    a.nshots = (uint32_t)nb;
-    a.corr = corr + (size_t)b0 * t.nw;
-    a.logical = logical ? logical + (size_t)b0 * t.kw : nullptr;
-    a.stats = stats ? stats + b0 : nullptr;
-    a.soft = soft ? soft + (size_t)b0 * t.n : nullptr;
-    a.obs = obs ? obs + (size_t)b0 * t.kw : nullptr;
-    a.counters = counters;
-    a.next_shot = h->ctrl;
-    a.lsd_count = h->ctrl + 1;
-    a.lsd_shots = h->lsd_shots;
-    a.lsd_soft = h->lsd_soft;
-    a.scratch = h->bp_scratch;
-    a.scratch_pitch = (long long)(2 + h->M) * t.n;
-    const int bp_grid = (int)std::min<long long>(h->bp_grid(), (nb + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-    if (h->profiling) { e0 = next_event(h); e1 = next_event(h); e2 = next_event(h); }
-    if (e0) cudaEventRecord(e0, s);
-    VIBE_CUDA(vibe::launch_bp(a, h->msg_fp16, bp_grid, s), "BP kernel launch");
-    if (e1) cudaEventRecord(e1, s);
-    vibe::LsdArgs l{};
-    l.t = t;
-    l.T = h->T; l.order = h->lsd_order; l.want_soft = soft != nullptr;
-    l.CW = (t.n + 31) / 32;
-    l.syn = a.syn; l.corr = a.corr; l.logical = a.logical; l.stats = a.stats; l.soft = a.soft; l.obs = a.obs;
-    l.counters = counters;
-    l.lsd_count = h->ctrl + 1; l.lsd_shots = h->lsd_shots; l.lsd_soft = h->lsd_soft; l.lsd_next = h->ctrl + 2;
-    l.scratch = h->lsd_scratch;
-    l.scratch_pitch = vibe::lsd_scratch_words(t);
-    VIBE_CUDA(vibe::launch_lsd(l, h->lsd_grid(), s), "LSD kernel launch");
-    if (e2) cudaEventRecord(e2, s);
-    h->bp_launches++;
-    h->lsd_launches++;
-  }
-  return VIBE_OK;
-}
-
-}  // namespace
+}  // namespace vibe
 
 extern "C" {
 
@@ -235,7 +331,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   if (p->msg_fp16 != 0 && p->msg_fp16 != 1) return fail(VIBE_ERR_INVALID, "msg_fp16 must be 0 or 1");
   for (int j = 0; j < n; ++j)
     if (!(priors[j] > 0.0 && priors[j] < 0.5)) return fail(VIBE_ERR_INVALID, "prior %d = %g outside (0, 0.5)", j, priors[j]);
-  if (n >= (1 << 24) || m >= (1 << 24)) return fail(VIBE_ERR_UNSUPPORTED, "n and m must be below 2^24");
+  if (n >= (1 << 23) || m >= (1 << 23)) return fail(VIBE_ERR_UNSUPPORTED, "n and m must be below 2^23");
   const int E = H->rowptr[m];
   int maxrow = 0;
   for (int r = 0; r < m; ++r) maxrow = std::max(maxrow, H->rowptr[r + 1] - H->rowptr[r]);
@@ -263,14 +359,17 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   auto bail = [&](int code) { delete h; return code; };
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
-  if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+  h->L.device = h->device;
+  if ((e = cudaDeviceGetAttribute(&h->L.num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
     return bail(cuda_fail(e, "device query"));
-  h->T = p->max_iter; h->M = p->M; h->alpha = p->alpha; h->lsd_order = p->lsd_order; h->msg_fp16 = p->msg_fp16;
+  h->L.msg_fp16 = p->msg_fp16;
   Tables& t = h->t;
   t.m = m; t.n = n; t.k = k; t.E = E; t.K = K;
   t.RP = std::max(8, (maxrow + 7) / 8 * 8);
   t.DP = maxcol <= 4 ? 4 : maxcol <= 8 ? 8 : maxcol <= 16 ? 16 : 32;
   t.mw = (m + 31) / 32; t.nw = (n + 31) / 32; t.kw = (k + 31) / 32; t.W = t.mw;
+  t.T = p->max_iter; t.M = p->M; t.lsd_order = p->lsd_order; t.alpha = p->alpha;
+  vibe::bp_warp_smem_bytes(&t, p->msg_fp16);
   const int Lnnz = L->rowptr[k];
   const size_t msg_bytes = (size_t)m * t.RP * (p->msg_fp16 ? 2 : 4);
   const size_t lev_scratch = std::max<size_t>(2 * (size_t)n + E, (size_t)K * ((size_t)m + 3 * (size_t)n + 1));
@@ -292,6 +391,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   VIBE_TRY(dalloc(&h->perm, (size_t)K * n), "tables");
   VIBE_TRY(dalloc(&h->lam, n), "tables");
   VIBE_TRY(cudaMalloc(&h->msg_init, std::max<size_t>(msg_bytes, 16)), "tables");
+  VIBE_TRY(dalloc(&h->d_desc, 1), "tables");
   VIBE_TRY(dalloc(&scratch, lev_scratch), "tables");
   VIBE_TRY(dalloc(&h->tmp_counters, VIBE_NUM_COUNTERS), "tables");
   VIBE_TRY(cudaMemcpyAsync(h->rowptr, H->rowptr, sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, s), "upload");
@@ -308,29 +408,22 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   VIBE_TRY(vibe::build_tables(h->rowptr, h->colidx, m, n, K, h->perm, t.RP, t.DP, p->msg_fp16, h->lam, h->colptr,
                               h->rowidx, h->csc_ent, h->msg_init, h->sched, h->lvl_off, h->nlev, scratch, s),
            "graph builder");
+  t.rowptr = h->rowptr; t.colidx = h->colidx; t.colptr = h->colptr; t.rowidx = h->rowidx;
+  t.csc_ent = h->csc_ent; t.lam = h->lam; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
+  t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
+  VIBE_TRY(cudaMemcpyAsync(h->d_desc, &t, sizeof(Tables), cudaMemcpyHostToDevice, s), "upload");
   VIBE_TRY(cudaStreamSynchronize(s), "graph builder");
   cudaFree(scratch);
   scratch = nullptr;
   cudaStreamDestroy(s);
   s = nullptr;
 #undef VIBE_TRY
-  t.rowptr = h->rowptr; t.colidx = h->colidx; t.colptr = h->colptr; t.rowidx = h->rowidx;
-  t.csc_ent = h->csc_ent; t.lam = h->lam; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
-  t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
-
-  const size_t wsm = vibe::bp_warp_smem_bytes(t, h->M, h->msg_fp16, &h->L);
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  if (wsm * vibe::kBpWarpsPerCta > (size_t)optin)
-    return bail(fail(VIBE_ERR_UNSUPPORTED, "BP state of one shot (%zu bytes) does not fit in shared memory", wsm));
-  if (vibe::lsd_smem_bytes(t) > (size_t)optin)
-    return bail(fail(VIBE_ERR_UNSUPPORTED, "LSD state does not fit in shared memory"));
-  if ((e = vibe::bp_occupancy(t, h->msg_fp16, wsm * vibe::kBpWarpsPerCta, &h->bp_blocks_per_sm)) != cudaSuccess)
-    return bail(cuda_fail(e, "BP occupancy"));
-  if ((e = vibe::lsd_occupancy(t, &h->lsd_blocks_per_sm)) != cudaSuccess) return bail(cuda_fail(e, "LSD occupancy"));
-  if (h->bp_blocks_per_sm < 1 || h->lsd_blocks_per_sm < 1)
-    return bail(fail(VIBE_ERR_UNSUPPORTED, "kernels cannot be resident with this problem size"));
-  h->chunk_max = std::max<long long>(1, (long long)(kWorkspaceBytes / ((size_t)n * 4 + 8)));
+  h->L.one = t;
+  h->L.d_desc = h->d_desc;
+  h->L.ndem = 1;
+  h->L.bnd = bounds_of(t);
+  if ((rc = size_launch(h->L)) != VIBE_OK) return bail(rc);
+  h->ws.chunk_max = std::max<long long>(1, (long long)(kWorkspaceBytes / ((size_t)n * 4 + 8)));
   *out = h;
   return VIBE_OK;
 }
@@ -343,8 +436,10 @@ int vibe_decode(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, uint32_t
   if (B == 0) return VIBE_OK;
   if (!d_syndromes || !d_corrections) return fail(VIBE_ERR_INVALID, "NULL syndromes or corrections");
   if (B > 0x7fffffffLL) return fail(VIBE_ERR_INVALID, "batch too large");
-  return decode_device(h, d_syndromes, B, d_corrections, d_logical, d_stats, d_soft, d_observables,
-                       reinterpret_cast<unsigned long long*>(d_counters), static_cast<cudaStream_t>(stream));
+  const Tables& t = h->t;
+  Batch q{nullptr, d_syndromes, t.mw, B, d_corrections, t.nw, d_logical, t.kw, d_stats, d_soft, t.n,
+          d_observables, reinterpret_cast<unsigned long long*>(d_counters)};
+  return run_decode(h->L, h->ws, h->prof, q, static_cast<cudaStream_t>(stream));
 }
 
 int vibe_decode_host(vibe_handle* h, const uint32_t* h_syndromes, int64_t B, uint32_t* h_corrections,
@@ -357,7 +452,7 @@ int vibe_decode_host(vibe_handle* h, const uint32_t* h_syndromes, int64_t B, uin
   const Tables& t = h->t;
   if (h_counters) VIBE_CUDA(cudaMemsetAsync(h->tmp_counters, 0, sizeof(uint64_t) * VIBE_NUM_COUNTERS, s), "counters");
   if (B > 0) {
-    const long long chunk = std::min<long long>(B, h->chunk_max);
+    const long long chunk = std::min<long long>(B, h->ws.chunk_max);
     if (chunk > h->stage_cap) {
       h->release_stage();
       VIBE_CUDA(dalloc(&h->st_syn, (size_t)chunk * t.mw), "staging");
@@ -374,8 +469,9 @@ int vibe_decode_host(vibe_handle* h, const uint32_t* h_syndromes, int64_t B, uin
       if (h_observables)
         VIBE_CUDA(cudaMemcpyAsync(h->st_obs, h_observables + (size_t)b0 * t.kw, sizeof(uint32_t) * nb * t.kw,
                                   cudaMemcpyHostToDevice, s), "H2D");
-      int rc = decode_device(h, h->st_syn, nb, h->st_corr, h->st_log, h->st_stats, nullptr,
-                             h_observables ? h->st_obs : nullptr, h_counters ? h->tmp_counters : nullptr, s);
+      Batch q{nullptr, h->st_syn, t.mw, nb, h->st_corr, t.nw, h->st_log, t.kw, h->st_stats, nullptr, t.n,
+              h_observables ? h->st_obs : nullptr, h_counters ? h->tmp_counters : nullptr};
+      int rc = run_decode(h->L, h->ws, h->prof, q, s);
       if (rc != VIBE_OK) return rc;
       VIBE_CUDA(cudaMemcpyAsync(h_corrections + (size_t)b0 * t.nw, h->st_corr, sizeof(uint32_t) * nb * t.nw,
                                 cudaMemcpyDeviceToHost, s), "D2H");
@@ -409,28 +505,73 @@ int vibe_get_wavefronts(vibe_handle* h, int32_t member, uint32_t* order_out, uin
 
 int vibe_profile(vibe_handle* h, int32_t enable) {
   if (!h) return fail(VIBE_ERR_INVALID, "NULL handle");
-  h->profiling = enable != 0;
-  h->ev_used = 0;
-  h->bp_launches = 0;
-  h->lsd_launches = 0;
+  h->prof.on = enable != 0;
+  h->prof.used = 0;
+  h->prof.bp_launches = 0;
+  h->prof.lsd_launches = 0;
   return VIBE_OK;
 }
 
-int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp_launches, int64_t* lsd_launches) {
-  if (!h) return fail(VIBE_ERR_INVALID, "NULL handle");
+static int profile_read(Profiler& P, double* bp_ms, double* lsd_ms, int64_t* nb, int64_t* nl) {
   double bp = 0.0, lsd = 0.0;
-  for (size_t i = 0; i + 3 <= h->ev_used; i += 3) {
+  for (size_t i = 0; i + 3 <= P.used; i += 3) {
     float a = 0.f, b = 0.f;
-    VIBE_CUDA(cudaEventSynchronize(h->ev_pool[i + 2]), "profile");
-    VIBE_CUDA(cudaEventElapsedTime(&a, h->ev_pool[i], h->ev_pool[i + 1]), "profile");
-    VIBE_CUDA(cudaEventElapsedTime(&b, h->ev_pool[i + 1], h->ev_pool[i + 2]), "profile");
+    VIBE_CUDA(cudaEventSynchronize(P.pool[i + 2]), "profile");
+    VIBE_CUDA(cudaEventElapsedTime(&a, P.pool[i], P.pool[i + 1]), "profile");
+    VIBE_CUDA(cudaEventElapsedTime(&b, P.pool[i + 1], P.pool[i + 2]), "profile");
     bp += a;
     lsd += b;
   }
   if (bp_ms) *bp_ms = bp;
   if (lsd_ms) *lsd_ms = lsd;
-  if (bp_launches) *bp_launches = h->bp_launches;
-  if (lsd_launches) *lsd_launches = h->lsd_launches;
+  if (nb) *nb = P.bp_launches;
+  if (nl) *nl = P.lsd_launches;
+  return VIBE_OK;
+}
+
+int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp_launches, int64_t* lsd_launches) {
+  if (!h) return fail(VIBE_ERR_INVALID, "NULL handle");
+  return profile_read(h->prof, bp_ms, lsd_ms, bp_launches, lsd_launches);
+}
+
+int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream, int32_t* bp_blocks_per_sm,
+                  int32_t* lsd_blocks_per_sm) {
+  if (!h || !d_syndromes || B < 1) return fail(VIBE_ERR_INVALID, "NULL handle/syndromes or empty sample");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Tables& t = h->t;
+  uint32_t* corr = nullptr;
+  VIBE_CUDA(dalloc(&corr, (size_t)B * t.nw), "autotune");
+  const int bp_max = h->L.bp_blocks_per_sm, lsd_max = h->L.lsd_blocks_per_sm;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_bp = bp_max, best_lsd = lsd_max;
+  int rc = VIBE_OK;
+  const int bp_try[] = {bp_max, (bp_max * 3 + 3) / 4, (bp_max + 1) / 2};
+  const int lsd_try[] = {lsd_max, std::max(1, lsd_max / 2)};
+  for (int bi = 0; bi < 3 && rc == VIBE_OK; ++bi)
+    for (int li = 0; li < 2 && rc == VIBE_OK; ++li) {
+      h->L.bp_blocks_per_sm = std::max(1, bp_try[bi]);
+      h->L.lsd_blocks_per_sm = std::max(1, lsd_try[li]);
+      Batch q{nullptr, d_syndromes, t.mw, B, corr, t.nw, nullptr, t.kw, nullptr, nullptr, t.n, nullptr, nullptr};
+      if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;   // warm-up (and workspace)
+      cudaEventRecord(e0, s);
+      if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_bp = h->L.bp_blocks_per_sm; best_lsd = h->L.lsd_blocks_per_sm; }
+    }
+  h->L.bp_blocks_per_sm = best_bp;
+  h->L.lsd_blocks_per_sm = best_lsd;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(corr);
+  if (rc != VIBE_OK) return rc;
+  if (bp_blocks_per_sm) *bp_blocks_per_sm = best_bp;
+  if (lsd_blocks_per_sm) *lsd_blocks_per_sm = best_lsd;
   return VIBE_OK;
 }
 
@@ -439,23 +580,68 @@ int vibe_destroy(vibe_handle* h) {
   return VIBE_OK;
 }
 
-}  // extern "C"
-
-// Read-only access to a handle's resident problem for the library's other host translation units.
-namespace vibe {
-
-int handle_view(const vibe_handle* h, HandleView* v) {
-  if (!h || !v) return fail(VIBE_ERR_INVALID, "NULL handle");
-  v->t = h->t;
-  v->device = h->device;
-  v->T = h->T; v->M = h->M; v->lsd_order = h->lsd_order; v->msg_fp16 = h->msg_fp16; v->alpha = h->alpha;
-  v->L = h->L;
-  v->bp_grid = h->bp_grid();
-  v->lsd_grid = h->lsd_grid();
-  v->num_sms = h->num_sms;
+int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** out) {
+  if (!out) return fail(VIBE_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!handles || count < 1 || count > vibe::kMaxDems)
+    return fail(VIBE_ERR_INVALID, "need 1..%d handles", vibe::kMaxDems);
+  for (int i = 0; i < count; ++i)
+    if (!handles[i]) return fail(VIBE_ERR_INVALID, "handle %d is NULL", i);
+  const vibe_handle* h0 = handles[0];
+  std::vector<Tables> desc(count);
+  Bounds b = bounds_of(h0->t);
+  for (int i = 0; i < count; ++i) {
+    const vibe_handle* h = handles[i];
+    if (h->device != h0->device) return fail(VIBE_ERR_INVALID, "handles live on different devices");
+    if (h->L.msg_fp16 != h0->L.msg_fp16) return fail(VIBE_ERR_INVALID, "handles mix FP16 and FP32 messages");
+    desc[i] = h->t;
+    widen(b, h->t);
+  }
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h0->device)
+    return fail(VIBE_ERR_INVALID, "the handles' device must be current");
+  vibe_batch* bt = new (std::nothrow) vibe_batch();
+  if (!bt) return fail(VIBE_ERR_NOMEM, "host allocation failed");
+  bt->device = h0->device;
+  bt->hs.assign(handles, handles + count);
+  cudaError_t e;
+  if ((e = dalloc(&bt->d_desc, count)) != cudaSuccess) { delete bt; return cuda_fail(e, "batch"); }
+  if ((e = cudaMemcpy(bt->d_desc, desc.data(), sizeof(Tables) * count, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    delete bt;
+    return cuda_fail(e, "batch");
+  }
+  bt->L.mixed = true;
+  bt->L.d_desc = bt->d_desc;
+  bt->L.ndem = count;
+  bt->L.bnd = b;
+  bt->L.msg_fp16 = h0->L.msg_fp16;
+  bt->L.device = h0->device;
+  bt->L.num_sms = h0->L.num_sms;
+  int rc = size_launch(bt->L);
+  if (rc != VIBE_OK) { delete bt; return rc; }
+  bt->ws.chunk_max = std::max<long long>(1, (long long)(kWorkspaceBytes / ((size_t)b.n * 4 + 8)));
+  *out = bt;
   return VIBE_OK;
 }
 
-int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+int vibe_batch_decode(vibe_batch* b, const int32_t* d_problem, const uint32_t* d_syndromes, int32_t syn_stride,
+                      int64_t B, uint32_t* d_corrections, int32_t corr_stride, uint32_t* d_logical, int32_t log_stride,
+                      vibe_shot_stats* d_stats, const uint32_t* d_observables, uint64_t* d_counters, void* stream) {
+  if (!b) return fail(VIBE_ERR_INVALID, "NULL batch");
+  if (B < 0) return fail(VIBE_ERR_INVALID, "negative batch");
+  if (B == 0) return VIBE_OK;
+  if (!d_problem || !d_syndromes || !d_corrections) return fail(VIBE_ERR_INVALID, "NULL problem ids, syndromes or corrections");
+  if (B > 0x7fffffffLL) return fail(VIBE_ERR_INVALID, "batch too large");
+  if (syn_stride < b->L.bnd.W || corr_stride < b->L.bnd.nw || ((d_logical || d_observables) && log_stride < b->L.bnd.kw))
+    return fail(VIBE_ERR_INVALID, "strides smaller than the largest problem's words");
+  Batch q{d_problem, d_syndromes, syn_stride, B, d_corrections, corr_stride, d_logical, log_stride, d_stats, nullptr,
+          b->L.bnd.n, d_observables, reinterpret_cast<unsigned long long*>(d_counters)};
+  return run_decode(b->L, b->ws, b->prof, q, static_cast<cudaStream_t>(stream));
+}
 
-}  // namespace vibe
+int vibe_batch_destroy(vibe_batch* b) {
+  delete b;
+  return VIBE_OK;
+}
+
+}  // extern "C"

@@ -81,18 +81,21 @@ __device__ __forceinline__ bool is_finite_bits(float x) {
 // its own slot with +inf (magnitude that never wins a minimum, sign bit 0), takes the minimum
 // magnitude and the XOR of the sign bits over the whole row, and later stores its new message in
 // the same slot. Minimum and parity equal those over the other slots exactly.
+// DP is the launch's largest column pitch; dp the problem's own (dp <= DP).
 template <typename MT, int DP, int RPC>
-__device__ __forceinline__ void update_column(uint32_t v, int deg, const Tables& t, float alpha, MT* msgs,
-                                              uint8_t* dec8, const uint8_t* s8, uint8_t* par8, float* lpost) {
+__device__ __forceinline__ void update_column(uint32_t v, int deg, const uint32_t* csc, int dp, const float* lam,
+                                              uint32_t rp, float alpha, MT* msgs, uint8_t* dec8, const uint8_t* s8,
+                                              uint8_t* par8, float* lpost) {
   uint32_t ent[DP];
-  const uint4* ce = reinterpret_cast<const uint4*>(t.csc_ent + (size_t)v * DP);
+  const uint4* ce = reinterpret_cast<const uint4*>(csc + (size_t)v * dp);
 #pragma unroll
   for (int q = 0; q < DP / 4; ++q) {
-    uint4 x = __ldg(ce + q);
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    if (4 * q < dp) x = __ldg(ce + q);
     ent[4 * q + 0] = x.x; ent[4 * q + 1] = x.y; ent[4 * q + 2] = x.z; ent[4 * q + 3] = x.w;
   }
-  const float lamv = __ldg(t.lam + v);
-  const uint32_t RP = RPC ? (uint32_t)RPC * 8u : (uint32_t)t.RP;
+  const float lamv = __ldg(lam + v);
+  const uint32_t RP = RPC ? (uint32_t)RPC * 8u : rp;
   float mcv[DP];
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
@@ -147,27 +150,224 @@ struct MinBlocks { static constexpr int value = 16 / kBpWarpsPerCta; };
 template <>
 struct MinBlocks<__half> { static constexpr int value = 24 / kBpWarpsPerCta; };
 
-template <typename MT, int DP, int RPC>
-__global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_bp(const BpArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Tables& t = a.t;
-  const int lane = threadIdx.x & 31;
-  const int wcta = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * kBpWarpsPerCta + wcta;
-  unsigned char* base = smem + (size_t)wcta * a.warp_smem;
-  MT* msgs = reinterpret_cast<MT*>(base + a.off_msg);
-  uint8_t* dec8 = base + a.off_dec;
-  uint8_t* s8 = base + a.off_s;
-  uint8_t* par8 = base + a.off_par;
-  uint32_t* cand = reinterpret_cast<uint32_t*>(base + a.off_cand);
-  float* acc = a.scratch + gw * a.scratch_pitch;  // n floats: LLR average accumulator
-  float* lpost = acc + t.n;                        // n floats: the member's posterior when needed
-  float* cand_post = lpost + t.n;                  // M * n floats (only with want_soft)
-
-  const int n = t.n, m = t.m, K = t.K, M = a.M, T = a.T, nw = t.nw, mw = t.mw;
+// Decodes one shot of problem t with the warp (the body of the persistent loop below).
+template <typename MT, int DP, int RPC, bool MIXED>
+__device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, uint32_t shot, unsigned char* base,
+                                            float* acc, float* lpost, float* cand_post, int lane,
+                                            unsigned long long& my_iters, unsigned long long& my_shots,
+                                            unsigned long long& my_fail) {
+  const int n = t.n, m = t.m, K = t.K, M = t.M, T = t.T, nw = t.nw, kw = t.kw;
   const int m4 = (m + 3) >> 2;
   const int n4 = (n + 3) >> 2;
   const int msg_vec = (int)(((size_t)m * t.RP * sizeof(MT)) / 16);
+  const uint32_t* csc = t.csc_ent;
+  const float* lam = t.lam;
+  const int dp = MIXED ? t.DP : DP;   // one problem: the pitch is the launch's
+  const uint32_t rp = (uint32_t)t.RP;
+  const float alpha = t.alpha;
+  MT* msgs = reinterpret_cast<MT*>(base + t.off_msg);
+  uint8_t* dec8 = base + t.off_dec;
+  uint8_t* s8 = base + t.off_s;
+  uint8_t* par8 = base + t.off_par;
+  uint32_t* cand = reinterpret_cast<uint32_t*>(base + t.off_cand);
+  const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
+  uint32_t any = 0;
+  for (int c = lane; c < 4 * m4; c += 32) {
+    uint32_t b = c < m ? (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u : 0u;
+    s8[c] = (uint8_t)b;
+    any |= b;
+  }
+  any = __any_sync(kFull, any);
+  __syncwarp();
+  ++my_shots;
+  uint32_t* out_corr = a.corr + (size_t)shot * a.corr_stride;
+
+  if (!any && !a.want_soft) {
+    // s = 0: every member converges in iteration 1 to e = 0; the first M are the candidates, all of
+    // weight 0, so member 0 is chosen.
+    for (int w = lane; w < nw; w += 32) out_corr[w] = 0u;
+    if (a.logical)
+      for (int w = lane; w < kw; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+    if (a.obs) {
+      uint32_t f = 0;
+      for (int w = lane; w < kw; w += 32) f |= a.obs[(size_t)shot * a.log_stride + w];
+      if (__any_sync(kFull, f) && lane == 0) ++my_fail;
+    }
+    if (a.stats && lane == 0) {
+      vibe_shot_stats st;
+      st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)M; st.chosen_member = 0;
+      st.iters = 1; st.largest_cluster = 0; st.n_clusters = 0;
+      a.stats[shot] = st;
+    }
+    return;
+  }
+
+  // candidate list, lane j holds entry j (sorted by iteration, then member)
+  int ncand = 0;
+  int c_t = 0, c_i = 0, c_slot = 0;
+  float c_W = 0.0f;
+
+  for (int i = 0; i < K; ++i) {
+    const int budget = ncand < M ? T : __shfl_sync(kFull, c_t, M - 1) - 1;
+    if (budget <= 0) break;
+    // member init: messages from the prior image, decisions 0, parity = s
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(t.msg_init);
+      uint4* dst = reinterpret_cast<uint4*>(msgs);
+      for (int q = lane; q < msg_vec; q += 32) dst[q] = __ldg(src + q);
+      uint32_t* d32 = reinterpret_cast<uint32_t*>(dec8);
+      for (int q = lane; q < n4; q += 32) d32[q] = 0u;
+      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(s8);
+      uint32_t* p32 = reinterpret_cast<uint32_t*>(par8);
+      for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
+    }
+    __syncwarp();
+
+    const uint32_t* sch = t.sched + (size_t)i * n;
+    const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
+    const int nl = __ldg(t.nlev + i);
+    int conv = 0;
+    for (int it = 1; it <= budget; ++it) {
+      // the posterior is needed after the last possible sweep of a member that may end without
+      // converging (LLR average) and, for soft output, after every sweep
+      float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
+      for (int l = 0; l < nl; ++l) {
+        const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
+        for (uint32_t idx = b + lane; idx < e; idx += 32) {
+          const uint32_t ent = __ldg(sch + idx);
+          update_column<MT, DP, RPC>(ent & 0xffffffu, (int)(ent >> 24), csc, dp, lam, rp, alpha, msgs, dec8, s8,
+                                     par8, lp);
+        }
+        __syncwarp();
+      }
+      ++my_iters;
+      uint32_t bad = 0;
+      const uint32_t* p32 = reinterpret_cast<const uint32_t*>(par8);
+      for (int q = lane; q < m4; q += 32) bad |= p32[q];
+      if (!__any_sync(kFull, bad)) { conv = it; break; }
+    }
+    if (conv) {
+      // insert (conv, i); i exceeds every member already listed, so it goes after equal iterations
+      const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
+      const int slot = ncand < M ? ncand : __shfl_sync(kFull, c_slot, M - 1);
+      uint32_t* bits = cand + (size_t)slot * nw;
+      float W = 0.0f;
+      for (int w = 0; w < nw; ++w) {
+        const int v = 32 * w + lane;
+        const uint32_t word = __ballot_sync(kFull, v < n && dec8[v] != 0);
+        if (lane == 0) bits[w] = word;
+        uint32_t x = word;
+        while (x) {
+          const int bpos = __ffs(x) - 1;
+          W = __fadd_rn(W, __ldg(lam + 32 * w + bpos));
+          x &= x - 1;
+        }
+      }
+      if (a.want_soft) {
+        float* dst = cand_post + (size_t)slot * n;
+        for (int v = lane; v < n; v += 32) dst[v] = lpost[v];
+      }
+      const float uW = __shfl_up_sync(kFull, c_W, 1);
+      const int ut = __shfl_up_sync(kFull, c_t, 1), ui = __shfl_up_sync(kFull, c_i, 1);
+      const int us = __shfl_up_sync(kFull, c_slot, 1);
+      const int last = min(ncand, M - 1);
+      if (lane > p && lane <= last) { c_W = uW; c_t = ut; c_i = ui; c_slot = us; }
+      if (lane == p) { c_W = W; c_t = conv; c_i = i; c_slot = slot; }
+      ncand = min(ncand + 1, M);
+      __syncwarp();
+    } else if (ncand == 0) {
+      // not converged after T sweeps and no candidate yet: add LLR^i / ||LLR^i|| (finite entries)
+      float part = 0.0f;
+      for (int v = lane; v < n; v += 32) {
+        const float x = lpost[v];
+        part = __fadd_rn(part, is_finite_bits(x) ? __fmul_rn(x, x) : 0.0f);
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) part = __fadd_rn(part, __shfl_xor_sync(kFull, part, off));
+      const float nrm = __fsqrt_rn(part);
+      for (int v = lane; v < n; v += 32) {
+        const float x = lpost[v];
+        const float term = is_finite_bits(x) ? (nrm == 0.0f ? 0.0f : __fdiv_rn(x, nrm)) : x;
+        acc[v] = __fadd_rn(i == 0 ? 0.0f : acc[v], term);
+      }
+    }
+    __syncwarp();
+  }
+
+  if (ncand > 0) {
+    // first minimum of W over the candidate list
+    float bw = lane < ncand ? c_W : __int_as_float(0x7f800000);
+    int bi = lane;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const float ow = __shfl_xor_sync(kFull, bw, off);
+      const int oi = __shfl_xor_sync(kFull, bi, off);
+      if (ow < bw || (ow == bw && oi < bi)) { bw = ow; bi = oi; }
+    }
+    const int slot = __shfl_sync(kFull, c_slot, bi);
+    const int member = __shfl_sync(kFull, c_i, bi);
+    const int iters = ncand == M ? __shfl_sync(kFull, c_t, M - 1) : T;
+    const uint32_t* bits = cand + (size_t)slot * nw;
+    for (int w = lane; w < nw; w += 32) out_corr[w] = bits[w];
+    if (a.want_soft) {
+      const float* src = cand_post + (size_t)slot * n;
+      float* dst = a.soft + (size_t)shot * a.soft_stride;
+      for (int v = lane; v < n; v += 32) dst[v] = src[v];
+    }
+    uint32_t fail = 0;
+    for (int rb = 0; rb < kw; ++rb) {
+      const int r = 32 * rb + lane;
+      uint32_t par = 0;
+      if (r < t.k)
+        for (int e = __ldg(t.lrowptr + r); e < __ldg(t.lrowptr + r + 1); ++e) {
+          const int j = __ldg(t.lcolidx + e);
+          par ^= (bits[j >> 5] >> (j & 31)) & 1u;
+        }
+      const uint32_t word = __ballot_sync(kFull, par != 0);
+      if (a.logical && lane == 0) a.logical[(size_t)shot * a.log_stride + rb] = word;
+      if (a.obs) fail |= word ^ a.obs[(size_t)shot * a.log_stride + rb];
+    }
+    if (fail && lane == 0) ++my_fail;
+    if (a.stats && lane == 0) {
+      vibe_shot_stats st;
+      st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)ncand;
+      st.chosen_member = (uint8_t)member; st.iters = (uint16_t)iters; st.largest_cluster = 0; st.n_clusters = 0;
+      a.stats[shot] = st;
+    }
+  } else {
+    // hand the averaged soft vector to the LSD kernel
+    uint32_t q = 0;
+    if (lane == 0) q = atomicAdd(a.lsd_count, 1u);
+    q = __shfl_sync(kFull, q, 0);
+    if (lane == 0) a.lsd_shots[q] = shot;
+    float* dst = a.lsd_soft + (size_t)q * a.bnd.n;
+    const float kf = (float)K;
+    for (int v = lane; v < n; v += 32) dst[v] = __fdiv_rn(acc[v], kf);
+  }
+  __syncwarp();
+}
+
+// MIXED: the shots of the launch name their problems (dem_of_shot); the problems' descriptors are
+// copied to shared memory after the warps' regions. Otherwise every shot decodes a.one, which the
+// kernel reads from its parameter space.
+template <typename MT, int DP, int RPC, bool MIXED>
+__global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_bp(const BpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wcta = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kBpWarpsPerCta + wcta;
+  Tables* sdem = reinterpret_cast<Tables*>(smem + (size_t)kBpWarpsPerCta * a.bnd.warp_smem);
+  if (MIXED) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(a.dems);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(sdem);
+    const int words = a.ndem * (int)(sizeof(Tables) / 4);
+    for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = __ldg(src + q);
+    __syncthreads();
+  }
+  unsigned char* base = smem + (size_t)wcta * a.bnd.warp_smem;
+  float* acc = a.scratch + gw * a.scratch_pitch;  // n floats: LLR average accumulator
+  float* lpost = acc + a.bnd.n;                    // n floats: the member's posterior when needed
+  float* cand_post = lpost + a.bnd.n;              // M * n floats (only with want_soft)
   unsigned long long my_iters = 0, my_shots = 0, my_fail = 0;
 
   for (;;) {
@@ -175,180 +375,30 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_b
     if (lane == 0) shot = atomicAdd(a.next_shot, 1u);
     shot = __shfl_sync(kFull, shot, 0);
     if (shot >= a.nshots) break;
-    const uint32_t* syn = a.syn + (size_t)shot * mw;
-    uint32_t any = 0;
-    for (int c = lane; c < 4 * m4; c += 32) {
-      uint32_t b = c < m ? (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u : 0u;
-      s8[c] = (uint8_t)b;
-      any |= b;
-    }
-    any = __any_sync(kFull, any);
-    __syncwarp();
-    ++my_shots;
-    uint32_t* out_corr = a.corr + (size_t)shot * nw;
-
-    if (!any && !a.want_soft) {
-      // s = 0: every member converges in iteration 1 to e = 0; the first M are the candidates, all of
-      // weight 0, so member 0 is chosen.
-      for (int w = lane; w < nw; w += 32) out_corr[w] = 0u;
-      if (a.logical)
-        for (int w = lane; w < t.kw; w += 32) a.logical[(size_t)shot * t.kw + w] = 0u;
-      if (a.obs) {
-        uint32_t f = 0;
-        for (int w = lane; w < t.kw; w += 32) f |= a.obs[(size_t)shot * t.kw + w];
-        if (__any_sync(kFull, f) && lane == 0) ++my_fail;
-      }
-      if (a.stats && lane == 0) {
-        vibe_shot_stats st;
-        st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)M; st.chosen_member = 0;
-        st.iters = 1; st.largest_cluster = 0; st.n_clusters = 0;
-        a.stats[shot] = st;
-      }
-      continue;
-    }
-
-    // candidate list, lane j holds entry j (sorted by iteration, then member)
-    int ncand = 0;
-    int c_t = 0, c_i = 0, c_slot = 0;
-    float c_W = 0.0f;
-
-    for (int i = 0; i < K; ++i) {
-      const int budget = ncand < M ? T : __shfl_sync(kFull, c_t, M - 1) - 1;
-      if (budget <= 0) break;
-      // member init: messages from the prior image, decisions 0, parity = s
-      {
-        const uint4* src = reinterpret_cast<const uint4*>(t.msg_init);
-        uint4* dst = reinterpret_cast<uint4*>(msgs);
-        for (int q = lane; q < msg_vec; q += 32) dst[q] = __ldg(src + q);
-        uint32_t* d32 = reinterpret_cast<uint32_t*>(dec8);
-        for (int q = lane; q < n4; q += 32) d32[q] = 0u;
-        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(s8);
-        uint32_t* p32 = reinterpret_cast<uint32_t*>(par8);
-        for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
-      }
-      __syncwarp();
-
-      const uint32_t* sch = t.sched + (size_t)i * n;
-      const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
-      const int nl = __ldg(t.nlev + i);
-      int conv = 0;
-      for (int it = 1; it <= budget; ++it) {
-        // the posterior is needed after the last possible sweep of a member that may end without
-        // converging (LLR average) and, for soft output, after every sweep
-        float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
-        for (int l = 0; l < nl; ++l) {
-          const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
-          for (uint32_t idx = b + lane; idx < e; idx += 32) {
-            const uint32_t ent = __ldg(sch + idx);
-            update_column<MT, DP, RPC>(ent & 0xffffffu, (int)(ent >> 24), t, a.alpha, msgs, dec8, s8, par8, lp);
-          }
-          __syncwarp();
+    if (MIXED) {
+      const int di = __ldg(a.dem_of_shot + shot);
+      if ((unsigned)di >= (unsigned)a.ndem) {
+        // problem index outside the launch's table: zero outputs, status BAD_PROBLEM, no decoding
+        for (int w = lane; w < a.corr_stride; w += 32) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
+        if (a.logical)
+          for (int w = lane; w < a.log_stride; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+        if (a.soft)
+          for (int j = lane; j < a.soft_stride; j += 32) a.soft[(size_t)shot * a.soft_stride + j] = 0.0f;
+        if (a.stats && lane == 0) {
+          vibe_shot_stats st;
+          st.status = VIBE_STATUS_BAD_PROBLEM; st.lsd_invoked = 0; st.n_converged = 0; st.chosen_member = 0;
+          st.iters = 0; st.largest_cluster = 0; st.n_clusters = 0;
+          a.stats[shot] = st;
         }
-        ++my_iters;
-        uint32_t bad = 0;
-        const uint32_t* p32 = reinterpret_cast<const uint32_t*>(par8);
-        for (int q = lane; q < m4; q += 32) bad |= p32[q];
-        if (!__any_sync(kFull, bad)) { conv = it; break; }
+        if (a.counters && lane == 0) atomicAdd(a.counters + VIBE_CNT_BAD_PROBLEM, 1ull);
+        continue;
       }
-      if (conv) {
-        // insert (conv, i); i exceeds every member already listed, so it goes after equal iterations
-        const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
-        const int slot = ncand < M ? ncand : __shfl_sync(kFull, c_slot, M - 1);
-        uint32_t* bits = cand + (size_t)slot * nw;
-        float W = 0.0f;
-        for (int w = 0; w < nw; ++w) {
-          const int v = 32 * w + lane;
-          const uint32_t word = __ballot_sync(kFull, v < n && dec8[v] != 0);
-          if (lane == 0) bits[w] = word;
-          uint32_t x = word;
-          while (x) {
-            const int bpos = __ffs(x) - 1;
-            W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
-            x &= x - 1;
-          }
-        }
-        if (a.want_soft) {
-          float* dst = cand_post + (size_t)slot * n;
-          for (int v = lane; v < n; v += 32) dst[v] = lpost[v];
-        }
-        const float uW = __shfl_up_sync(kFull, c_W, 1);
-        const int ut = __shfl_up_sync(kFull, c_t, 1), ui = __shfl_up_sync(kFull, c_i, 1);
-        const int us = __shfl_up_sync(kFull, c_slot, 1);
-        const int last = min(ncand, M - 1);
-        if (lane > p && lane <= last) { c_W = uW; c_t = ut; c_i = ui; c_slot = us; }
-        if (lane == p) { c_W = W; c_t = conv; c_i = i; c_slot = slot; }
-        ncand = min(ncand + 1, M);
-        __syncwarp();
-      } else if (ncand == 0) {
-        // not converged after T sweeps and no candidate yet: add LLR^i / ||LLR^i|| (finite entries)
-        float part = 0.0f;
-        for (int v = lane; v < n; v += 32) {
-          const float x = lpost[v];
-          part = __fadd_rn(part, is_finite_bits(x) ? __fmul_rn(x, x) : 0.0f);
-        }
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) part = __fadd_rn(part, __shfl_xor_sync(kFull, part, off));
-        const float nrm = __fsqrt_rn(part);
-        for (int v = lane; v < n; v += 32) {
-          const float x = lpost[v];
-          const float term = is_finite_bits(x) ? (nrm == 0.0f ? 0.0f : __fdiv_rn(x, nrm)) : x;
-          acc[v] = __fadd_rn(i == 0 ? 0.0f : acc[v], term);
-        }
-      }
-      __syncwarp();
-    }
-
-    if (ncand > 0) {
-      // first minimum of W over the candidate list
-      float bw = lane < ncand ? c_W : __int_as_float(0x7f800000);
-      int bi = lane;
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) {
-        const float ow = __shfl_xor_sync(kFull, bw, off);
-        const int oi = __shfl_xor_sync(kFull, bi, off);
-        if (ow < bw || (ow == bw && oi < bi)) { bw = ow; bi = oi; }
-      }
-      const int slot = __shfl_sync(kFull, c_slot, bi);
-      const int member = __shfl_sync(kFull, c_i, bi);
-      const int iters = ncand == M ? __shfl_sync(kFull, c_t, M - 1) : T;
-      const uint32_t* bits = cand + (size_t)slot * nw;
-      for (int w = lane; w < nw; w += 32) out_corr[w] = bits[w];
-      if (a.want_soft) {
-        const float* src = cand_post + (size_t)slot * n;
-        float* dst = a.soft + (size_t)shot * n;
-        for (int v = lane; v < n; v += 32) dst[v] = src[v];
-      }
-      uint32_t fail = 0;
-      for (int rb = 0; rb < t.kw; ++rb) {
-        const int r = 32 * rb + lane;
-        uint32_t par = 0;
-        if (r < t.k)
-          for (int e = __ldg(t.lrowptr + r); e < __ldg(t.lrowptr + r + 1); ++e) {
-            const int j = __ldg(t.lcolidx + e);
-            par ^= (bits[j >> 5] >> (j & 31)) & 1u;
-          }
-        const uint32_t word = __ballot_sync(kFull, par != 0);
-        if (a.logical && lane == 0) a.logical[(size_t)shot * t.kw + rb] = word;
-        if (a.obs) fail |= word ^ a.obs[(size_t)shot * t.kw + rb];
-      }
-      if (fail && lane == 0) ++my_fail;
-      if (a.stats && lane == 0) {
-        vibe_shot_stats st;
-        st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)ncand;
-        st.chosen_member = (uint8_t)member; st.iters = (uint16_t)iters; st.largest_cluster = 0; st.n_clusters = 0;
-        a.stats[shot] = st;
-      }
+      decode_shot<MT, DP, RPC, true>(a, sdem[di], shot, base, acc, lpost, cand_post, lane, my_iters, my_shots,
+                                     my_fail);
     } else {
-      // hand the averaged soft vector to the LSD kernel
-      uint32_t q = 0;
-      if (lane == 0) q = atomicAdd(a.lsd_count, 1u);
-      q = __shfl_sync(kFull, q, 0);
-      if (lane == 0) a.lsd_shots[q] = shot;
-      float* dst = a.lsd_soft + (size_t)q * n;
-      const float kf = (float)K;
-      for (int v = lane; v < n; v += 32) dst[v] = __fdiv_rn(acc[v], kf);
+      decode_shot<MT, DP, RPC, false>(a, a.one, shot, base, acc, lpost, cand_post, lane, my_iters, my_shots,
+                                      my_fail);
     }
-    __syncwarp();
   }
   if (lane == 0 && a.counters) {
     atomicAdd(a.counters + VIBE_CNT_SHOTS, my_shots);
@@ -357,26 +407,27 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_b
   }
 }
 
-// RPC: row pitch in 8-slot chunks when it is 1, 2 or 4 (compile-time row scans), else 0.
-inline int rpc_of(const Tables& t) { return (t.RP == 8 || t.RP == 16 || t.RP == 32) ? t.RP / 8 : 0; }
+// RPC: row pitch in 8-slot chunks when every problem of the launch has RP 8, 16 or 32, else 0.
+inline int rpc_of(const Bounds& b) { return (b.RP == 8 || b.RP == 16 || b.RP == 32) ? b.RP / 8 : 0; }
 
-template <typename MT, int DP, int RPC>
+inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename MT, int DP, int RPC, bool MIXED>
 cudaError_t launch_one(const BpArgs& a, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(k_bp<MT, DP, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = ensure_dyn_smem<k_bp<MT, DP, RPC, MIXED>>(smem);
   if (err != cudaSuccess) return err;
-  k_bp<MT, DP, RPC><<<grid, kBpWarpsPerCta * 32, smem, s>>>(a);
+  k_bp<MT, DP, RPC, MIXED><<<grid, kBpWarpsPerCta * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename MT, int DP, int RPC>
+template <typename MT, int DP, int RPC, bool MIXED>
 cudaError_t occupancy_one(size_t smem, int* out) {
-  cudaError_t err = cudaFuncSetAttribute(k_bp<MT, DP, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = ensure_dyn_smem<k_bp<MT, DP, RPC, MIXED>>(smem);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bp<MT, DP, RPC>, kBpWarpsPerCta * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bp<MT, DP, RPC, MIXED>, kBpWarpsPerCta * 32, smem);
 }
 
-// Dispatch over (message type, column pitch, row chunks); F is launch_one or occupancy_one.
-template <typename MT, int DP, typename Fn>
+template <typename Fn>
 cudaError_t by_rpc(int rpc, Fn&& f) {
   switch (rpc) {
     case 1: return f(std::integral_constant<int, 1>{});
@@ -386,7 +437,7 @@ cudaError_t by_rpc(int rpc, Fn&& f) {
   }
 }
 
-template <typename MT, typename Fn>
+template <typename Fn>
 cudaError_t by_dp(int DP, Fn&& f) {
   switch (DP) {
     case 4: return f(std::integral_constant<int, 4>{});
@@ -397,52 +448,59 @@ cudaError_t by_dp(int DP, Fn&& f) {
   }
 }
 
+// Mixed launches use the generic row scan (RPC 0) only, which keeps the number of instantiations down.
 template <typename MT>
 cudaError_t launch_mt(const BpArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = (size_t)a.warp_smem * kBpWarpsPerCta;
-  return by_dp<MT>(a.t.DP, [&](auto dp) {
-    return by_rpc<MT, decltype(dp)::value>(rpc_of(a.t), [&](auto rpc) {
-      return launch_one<MT, decltype(dp)::value, decltype(rpc)::value>(a, grid, smem, s);
+  const bool mixed = a.dem_of_shot != nullptr;
+  const size_t smem = bp_cta_smem_bytes(a.bnd, mixed ? a.ndem : 0);
+  return by_dp(a.bnd.DP, [&](auto dp) {
+    if (mixed) return launch_one<MT, decltype(dp)::value, 0, true>(a, grid, smem, s);
+    return by_rpc(rpc_of(a.bnd), [&](auto rpc) {
+      return launch_one<MT, decltype(dp)::value, decltype(rpc)::value, false>(a, grid, smem, s);
     });
   });
 }
 
 template <typename MT>
-cudaError_t occupancy_mt(const Tables& t, size_t smem, int* out) {
-  return by_dp<MT>(t.DP, [&](auto dp) {
-    return by_rpc<MT, decltype(dp)::value>(rpc_of(t), [&](auto rpc) {
-      return occupancy_one<MT, decltype(dp)::value, decltype(rpc)::value>(smem, out);
+cudaError_t occupancy_mt(const Bounds& b, int ndem, int* out) {
+  const size_t smem = bp_cta_smem_bytes(b, ndem);
+  return by_dp(b.DP, [&](auto dp) {
+    if (ndem > 0) return occupancy_one<MT, decltype(dp)::value, 0, true>(smem, out);
+    return by_rpc(rpc_of(b), [&](auto rpc) {
+      return occupancy_one<MT, decltype(dp)::value, decltype(rpc)::value, false>(smem, out);
     });
   });
 }
-
-inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 }  // namespace
 
-size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, BpLayout* L) {
+size_t bp_warp_smem_bytes(Tables* t, int msg_fp16) {
   size_t o = 0;
-  L->off_msg = (int)o;
-  o = align16(o + (size_t)t.m * t.RP * (msg_fp16 ? 2 : 4));
-  L->off_dec = (int)o;
-  o = align16(o + ((size_t)t.n + 3) / 4 * 4);
-  const size_t m4 = ((size_t)t.m + 3) / 4 * 4;
-  L->off_s = (int)o;
+  t->off_msg = (int)o;
+  o = align16(o + (size_t)t->m * t->RP * (msg_fp16 ? 2 : 4));
+  t->off_dec = (int)o;
+  o = align16(o + ((size_t)t->n + 3) / 4 * 4);
+  const size_t m4 = ((size_t)t->m + 3) / 4 * 4;
+  t->off_s = (int)o;
   o = align16(o + m4);
-  L->off_par = (int)o;
+  t->off_par = (int)o;
   o = align16(o + m4);
-  L->off_cand = (int)o;
-  o = align16(o + (size_t)M * t.nw * 4);
-  L->warp_smem = (int)o;
+  t->off_cand = (int)o;
+  o = align16(o + (size_t)t->M * t->nw * 4);
+  t->warp_smem = (int)o;
   return o;
+}
+
+size_t bp_cta_smem_bytes(const Bounds& b, int ndem) {
+  return (size_t)kBpWarpsPerCta * b.warp_smem + align16((size_t)ndem * sizeof(Tables));
 }
 
 cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s) {
   return msg_fp16 ? launch_mt<__half>(a, grid, s) : launch_mt<float>(a, grid, s);
 }
 
-cudaError_t bp_occupancy(const Tables& t, int msg_fp16, size_t cta_smem, int* blocks_per_sm) {
-  return msg_fp16 ? occupancy_mt<__half>(t, cta_smem, blocks_per_sm) : occupancy_mt<float>(t, cta_smem, blocks_per_sm);
+cudaError_t bp_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_per_sm) {
+  return msg_fp16 ? occupancy_mt<__half>(b, ndem, blocks_per_sm) : occupancy_mt<float>(b, ndem, blocks_per_sm);
 }
 
 }  // namespace vibe

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "vibe.h"
 
 namespace vibe {
@@ -13,6 +15,8 @@ constexpr int kBpWarpsPerCta = 2;   // persistent BP kernel: warps per CTA, one 
 constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
 constexpr int kMaxRowDeg = 255;     // position of an edge inside its check row fits in 8 bits
 constexpr int kMaxColDeg = 32;
+constexpr int kMaxDems = 64;        // decoding problems in one mixed launch
+constexpr int kMaxDevices = 64;
 constexpr uint32_t kFull = 0xffffffffu;
 
 // Position of slot `slot` of check row c inside the message image. A row is RP slots stored as
@@ -31,13 +35,17 @@ __host__ __device__ inline uint32_t csc_entry(uint32_t c, uint32_t slot, int RP,
   return (c << 9) | row_position(c, slot, RP, spc);
 }
 
-// Device-resident tables of one decoding problem (owned by the handle).
+// One decoding problem as the kernels see it: sizes, decoder parameters, the BP shared-memory layout
+// of one warp, and the device-resident tables (owned by the handle). Plain data, copied to the device.
 struct Tables {
   int m, n, k, E, K;
   int RP;        // row pitch of the padded message image: max row degree rounded up to 8
   int DP;        // column pitch of csc_ent: max column degree rounded up to 4 (4, 8, 16 or 32)
   int mw, nw, kw;
   int W;         // words of a bit vector over the checks: ceil(m/32)
+  int T, M, lsd_order;
+  float alpha;
+  int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // BP per-warp shared memory, bytes
   const int32_t* rowptr;   // H CSR
   const int32_t* colidx;
   const int32_t* colptr;   // H CSC, checks ascending in each column
@@ -52,69 +60,99 @@ struct Tables {
   const int32_t* lcolidx;
 };
 
+// Sizes that bound every problem of a launch (shared-memory layouts, strides, scratch pitches).
+struct Bounds {
+  int m, n, W, nw, kw, M, DP;
+  int RP;          // common row pitch if all problems share it, else 0
+  int warp_smem;   // largest BP per-warp layout
+  int lsd_order;   // largest LSD order
+};
+
 struct BpArgs {
-  Tables t;
-  int T, M;
-  float alpha;
+  Tables one;                  // the problem of every shot when dem_of_shot is NULL
+  const Tables* dems;          // device array of ndem problems (mixed launches)
+  int ndem;
+  const int32_t* dem_of_shot;  // problem of each shot (mixed launch), or NULL
+  Bounds bnd;
   int want_soft;
-  // per-warp shared-memory layout, bytes
-  int warp_smem, off_msg, off_dec, off_s, off_par, off_cand;
-  // batch (one chunk)
+  // batch (one chunk); strides in 32-bit words, soft stride in floats
   const uint32_t* syn;
+  int syn_stride;
   uint32_t nshots;
   uint32_t* corr;
+  int corr_stride;
   uint32_t* logical;
+  int log_stride;
   vibe_shot_stats* stats;
   float* soft;
+  int soft_stride;
   const uint32_t* obs;
   unsigned long long* counters;
   // work distribution and hand-off to LSD
   unsigned int* next_shot;
   unsigned int* lsd_count;
   uint32_t* lsd_shots;
-  float* lsd_soft;
+  float* lsd_soft;             // pitch bnd.n floats per queued shot
   // per-warp global scratch: n floats (LLR accumulator), n floats (posterior), M*n floats (candidate
-  // posteriors, only with want_soft)
+  // posteriors, only with want_soft); pitch in floats
   float* scratch;
   long long scratch_pitch;
 };
 
 struct LsdArgs {
-  Tables t;
-  int T, order, want_soft;
-  int CW;                  // words of a bit vector over a cluster's columns: ceil(n/32)
+  const Tables* dems;
+  int ndem;
+  const int32_t* dem_of_shot;
+  Bounds bnd;
+  int want_soft;
   const uint32_t* syn;
+  int syn_stride;
   uint32_t* corr;
+  int corr_stride;
   uint32_t* logical;
+  int log_stride;
   vibe_shot_stats* stats;
   float* soft;
+  int soft_stride;
   const uint32_t* obs;
   unsigned long long* counters;
   const unsigned int* lsd_count;
   const uint32_t* lsd_shots;
   const float* lsd_soft;
   unsigned int* lsd_next;
-  // per-CTA global scratch: basis m*W words, combinations m*CW words, 2*n u64 sort buffers
+  // per-CTA global scratch (see lsd_scratch_words)
   uint32_t* scratch;
   long long scratch_pitch; // 32-bit words per CTA
 };
 
 // A handle's resident problem and launch configuration, as other host files see it (vibe_api.cu).
-struct BpLayout {
-  int warp_smem, off_msg, off_dec, off_s, off_par, off_cand;
-};
-
 struct HandleView {
-  Tables t;
-  int device, num_sms;
-  int T, M, lsd_order, msg_fp16;
-  float alpha;
-  BpLayout L;
+  Tables t;                  // host copy of the descriptor
+  const Tables* d_desc;      // the same descriptor on the device
+  Bounds bnd;
+  int device, num_sms, msg_fp16;
   int bp_grid, lsd_grid;
 };
 int handle_view(const vibe_handle* h, HandleView* v);
+
+// Raises kernel Kern's dynamic shared-memory limit on the current device to at least `smem`. The
+// attribute call is made only when the limit must grow, so repeated launches (and launches recorded
+// into a CUDA graph after a first decode) make none.
+template <auto Kern>
+cudaError_t ensure_dyn_smem(size_t smem) {
+  static std::mutex mu;
+  static int limit[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= kMaxDevices) return cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  std::lock_guard<std::mutex> g(mu);
+  if (limit[dev] >= (int)smem) return cudaSuccess;
+  err = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess) limit[dev] = (int)smem;
+  return err;
+}
 int set_error(int code, const char* msg);
-long long lsd_scratch_words(const Tables& t);
 
 // K0: graph builder (vibe_graph.cu)
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K,
@@ -125,13 +163,16 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
 cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
 
 // K1: persistent BP + ensemble selection (vibe_bp.cu)
-size_t bp_warp_smem_bytes(const Tables& t, int M, int msg_fp16, BpLayout* L);
+size_t bp_warp_smem_bytes(Tables* t, int msg_fp16);   // fills t's layout fields, returns its size
+// ndem: descriptors a mixed launch keeps in shared memory; 0 for a single-problem launch.
+size_t bp_cta_smem_bytes(const Bounds& b, int ndem);
 cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
-cudaError_t bp_occupancy(const Tables& t, int msg_fp16, size_t cta_smem, int* blocks_per_sm);
+cudaError_t bp_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_per_sm);
 
 // K3: LSD (vibe_lsd.cu)
-size_t lsd_smem_bytes(const Tables& t);
+size_t lsd_smem_bytes(const Bounds& b, int ndem);
+long long lsd_scratch_words(const Bounds& b);
 cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s);
-cudaError_t lsd_occupancy(const Tables& t, int* blocks_per_sm);
+cudaError_t lsd_occupancy(const Bounds& b, int ndem, int* blocks_per_sm);
 
 }  // namespace vibe

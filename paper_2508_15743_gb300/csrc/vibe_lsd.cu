@@ -176,42 +176,49 @@ __device__ int merge_clusters(const LsdShared& S, int a, int b, int n) {
 template <int WP>
 __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Tables& t = a.t;
-  const int n = t.n, m = t.m, W = t.W, nw = t.nw;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kLsdThreads / 32;
+  // arrays sized by the launch's bounds; each shot uses the first m / n entries of its problem
+  const int mB = a.bnd.m, nB = a.bnd.n, WB = a.bnd.W, nwB = a.bnd.nw, CWB = (a.bnd.n + 31) / 32;
   LsdShared S;
+  Tables* sdem;
   {
     unsigned char* p = smem;
     auto take = [&](size_t bytes) { unsigned char* r = p; p += (bytes + 15) & ~(size_t)15; return r; };
-    S.best = reinterpret_cast<unsigned long long*>(take(8 * (size_t)m));
-    S.key = reinterpret_cast<uint32_t*>(take(4 * (size_t)n));
-    S.col_root = reinterpret_cast<int32_t*>(take(4 * (size_t)n));
-    S.col_next = reinterpret_cast<int32_t*>(take(4 * (size_t)n));
-    S.pend_next = reinterpret_cast<int32_t*>(take(4 * (size_t)n));
-    S.ck_par = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.rank = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.b_head = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.b_tail = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.piv_next = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.c_head = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.c_tail = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.c_cnt = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.p_head = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.p_tail = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.dlist = reinterpret_cast<int32_t*>(take(4 * (size_t)m));
-    S.sbits = reinterpret_cast<uint32_t*>(take(4 * (size_t)W));
-    S.ebits = reinterpret_cast<uint32_t*>(take(4 * (size_t)nw));
+    S.best = reinterpret_cast<unsigned long long*>(take(8 * (size_t)mB));
+    S.key = reinterpret_cast<uint32_t*>(take(4 * (size_t)nB));
+    S.col_root = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
+    S.col_next = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
+    S.pend_next = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
+    S.ck_par = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.rank = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.b_head = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.b_tail = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.piv_next = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.c_head = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.c_tail = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.c_cnt = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.p_head = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.p_tail = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.dlist = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
+    S.sbits = reinterpret_cast<uint32_t*>(take(4 * (size_t)WB));
+    S.ebits = reinterpret_cast<uint32_t*>(take(4 * (size_t)nwB));
     S.flags = reinterpret_cast<int32_t*>(take(4 * 8));
-    S.valid = take((size_t)m);
-    S.dirty = take((size_t)m);
+    S.valid = take((size_t)mB);
+    S.dirty = take((size_t)mB);
+    sdem = reinterpret_cast<Tables*>(take((size_t)a.ndem * sizeof(Tables)));
+  }
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(a.dems);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(sdem);
+    const int words = a.ndem * (int)(sizeof(Tables) / 4);
+    for (int q = tid; q < words; q += kLsdThreads) dst[q] = __ldg(src + q);
   }
   uint32_t* basis = a.scratch + (long long)blockIdx.x * a.scratch_pitch;   // m * W
-  uint32_t* combrow = basis + (size_t)m * W;                                // m * CW
-  const size_t sort_off = ((size_t)m * W + (size_t)m * a.CW + 1) & ~(size_t)1;   // 8-byte aligned
+  uint32_t* combrow = basis + (size_t)mB * WB;                              // m * CW
+  const size_t sort_off = ((size_t)mB * WB + (size_t)mB * CWB + 1) & ~(size_t)1;   // 8-byte aligned
   unsigned long long* sortA = reinterpret_cast<unsigned long long*>(basis + sort_off);  // n
-  unsigned long long* sortB = sortA + n;                                    // n
-  uint32_t* freecomb = reinterpret_cast<uint32_t*>(sortB + n);              // per warp (kFreeRows+1) * CW
-  const int CW = a.CW;
+  unsigned long long* sortB = sortA + nB;                                    // n
+  uint32_t* freecomb = reinterpret_cast<uint32_t*>(sortB + nB);             // per warp (kFreeRows+1) * CW
   const unsigned int total = *a.lsd_count;
 
   for (;;) {
@@ -221,8 +228,12 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     const unsigned int q = (unsigned int)S.flags[0];
     if (q >= total) break;
     const uint32_t shot = a.lsd_shots[q];
-    const float* vsoft = a.lsd_soft + (size_t)q * n;
-    const uint32_t* syn = a.syn + (size_t)shot * t.mw;
+    const int di = a.dem_of_shot ? __ldg(a.dem_of_shot + shot) : 0;
+    if ((unsigned)di >= (unsigned)a.ndem) continue;   // the BP kernel queues valid problems only
+    const Tables& t = sdem[di];
+    const int n = t.n, m = t.m, W = t.W, nw = t.nw, CW = (t.n + 31) / 32;
+    const float* vsoft = a.lsd_soft + (size_t)q * nB;
+    const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
 
     for (int j = tid; j < n; j += kLsdThreads) {
       S.key[j] = reliability_key(vsoft[j]);
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
         // that reduces to zero is free; its record (itself plus the pivots that sum to it) is kept for
         // the first `order` free columns.
         uint32_t x[WP], comb[WP];
-        uint32_t* fc = freecomb + (size_t)warp * (kFreeRows + 1) * CW;
+        uint32_t* fc = freecomb + (size_t)warp * (kFreeRows + 1) * CWB;
         int nfree = 0;
         for (int tp = 0; tp < kap; ++tp) {
           const int j = (int)(Bv[tp] & 0xffffffffull);
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
             const int p = lowest_bit<WP>(x, lane);
             append_row<WP, true>(x, comb, p, r, S, basis, combrow, W, CW, &S.b_head[r], &S.b_tail[r], lane);
           } else {
-            if (nfree < a.order) {
+            if (nfree < t.lsd_order) {
 #pragma unroll
               for (int qq = 0; qq < WP; ++qq) {
                 const int w = lane + 32 * qq;
@@ -426,7 +437,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
           comb[qq] = 0u;
         }
         reduce<WP, true>(x, comb, S.b_head[r], S, basis, combrow, W, CW, lane);
-        const int q = min(a.order, nfree);
+        const int q = min(t.lsd_order, nfree);
         if (q == 0) {
 #pragma unroll
           for (int qq = 0; qq < WP; ++qq) {
@@ -492,9 +503,9 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     __syncthreads();
     // outputs
     const bool solved = status == 1;
-    for (int w = tid; w < nw; w += kLsdThreads) a.corr[(size_t)shot * nw + w] = solved ? S.ebits[w] : 0u;
+    for (int w = tid; w < nw; w += kLsdThreads) a.corr[(size_t)shot * a.corr_stride + w] = solved ? S.ebits[w] : 0u;
     if (a.want_soft)
-      for (int j = tid; j < n; j += kLsdThreads) a.soft[(size_t)shot * n + j] = vsoft[j];
+      for (int j = tid; j < n; j += kLsdThreads) a.soft[(size_t)shot * a.soft_stride + j] = vsoft[j];
     if (warp == 0) {
       uint32_t fail = 0;
       for (int rb = 0; rb < t.kw; ++rb) {
@@ -506,15 +517,15 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
             par ^= (S.ebits[j >> 5] >> (j & 31)) & 1u;
           }
         const uint32_t word = __ballot_sync(kFull, par != 0);
-        if (a.logical && lane == 0) a.logical[(size_t)shot * t.kw + rb] = word;
-        if (a.obs) fail |= word ^ __ldg(a.obs + (size_t)shot * t.kw + rb);
+        if (a.logical && lane == 0) a.logical[(size_t)shot * a.log_stride + rb] = word;
+        if (a.obs) fail |= word ^ __ldg(a.obs + (size_t)shot * a.log_stride + rb);
       }
       if (lane == 0) {
         if (a.stats) {
           vibe_shot_stats st;
           st.status = solved ? VIBE_STATUS_OK : VIBE_STATUS_UNSOLVABLE;
           st.lsd_invoked = 1; st.n_converged = 0; st.chosen_member = 255;
-          st.iters = (uint16_t)a.T;
+          st.iters = (uint16_t)t.T;
           st.largest_cluster = (uint16_t)min(S.flags[4], 65535);
           st.n_clusters = (uint32_t)nr;
           a.stats[shot] = st;
@@ -531,66 +542,64 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-int lsd_wp(const Tables& t) {
-  const int need = max((t.W + 31) / 32, ((t.n + 31) / 32 + 31) / 32);
+int lsd_wp(const Bounds& b) {
+  const int need = max((b.W + 31) / 32, ((b.n + 31) / 32 + 31) / 32);
   int wp = 1;
   while (wp < need) wp <<= 1;
   return wp;
 }
 
-}  // namespace
-
-size_t lsd_smem_bytes(const Tables& t) {
-  const size_t m = t.m, n = t.n;
-  return a16(8 * m) + 4 * a16(4 * n) + 11 * a16(4 * m) + a16(4 * (size_t)t.W) + a16(4 * (size_t)t.nw) +
-         a16(32) + 2 * a16(m);
+template <int P>
+cudaError_t lsd_launch_one(const LsdArgs& a, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t err = ensure_dyn_smem<k_lsd<P>>(smem);
+  if (err != cudaSuccess) return err;
+  k_lsd<P><<<grid, kLsdThreads, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
-long long lsd_scratch_words(const Tables& t) {
-  const long long CW = (t.n + 31) / 32;
-  const long long head = ((long long)t.m * t.W + (long long)t.m * CW + 1) & ~1LL;
+template <int P>
+cudaError_t lsd_occupancy_one(size_t smem, int* out) {
+  cudaError_t err = ensure_dyn_smem<k_lsd<P>>(smem);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_lsd<P>, kLsdThreads, smem);
+}
+
+}  // namespace
+
+size_t lsd_smem_bytes(const Bounds& b, int ndem) {
+  const size_t m = b.m, n = b.n;
+  return a16(8 * m) + 4 * a16(4 * n) + 11 * a16(4 * m) + a16(4 * (size_t)b.W) + a16(4 * (size_t)b.nw) + a16(32) +
+         2 * a16(m) + a16((size_t)ndem * sizeof(Tables));
+}
+
+long long lsd_scratch_words(const Bounds& b) {
+  const long long CW = (b.n + 31) / 32;
+  const long long head = ((long long)b.m * b.W + (long long)b.m * CW + 1) & ~1LL;
   const long long free_rows = (long long)(kLsdThreads / 32) * (kFreeRows + 1) * CW;
-  return (head + 4LL * t.n + free_rows + 2 + 1) & ~1LL;   // even: every CTA's slice stays 8-byte aligned
+  return (head + 4LL * b.n + free_rows + 2 + 1) & ~1LL;   // even: every CTA's slice stays 8-byte aligned
 }
 
 cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = lsd_smem_bytes(a.t);
-  cudaError_t err;
-  switch (lsd_wp(a.t)) {
-#define VIBE_LSD_CASE(P)                                                                           \
-  case P:                                                                                          \
-    err = cudaFuncSetAttribute(k_lsd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    if (err != cudaSuccess) return err;                                                            \
-    k_lsd<P><<<grid, kLsdThreads, smem, s>>>(a);                                                   \
-    return cudaGetLastError();
-    VIBE_LSD_CASE(1)
-    VIBE_LSD_CASE(2)
-    VIBE_LSD_CASE(4)
-    VIBE_LSD_CASE(8)
-    VIBE_LSD_CASE(16)
-#undef VIBE_LSD_CASE
-    default:
-      return cudaErrorInvalidValue;
+  const size_t smem = lsd_smem_bytes(a.bnd, a.ndem);
+  switch (lsd_wp(a.bnd)) {
+    case 1: return lsd_launch_one<1>(a, grid, smem, s);
+    case 2: return lsd_launch_one<2>(a, grid, smem, s);
+    case 4: return lsd_launch_one<4>(a, grid, smem, s);
+    case 8: return lsd_launch_one<8>(a, grid, smem, s);
+    case 16: return lsd_launch_one<16>(a, grid, smem, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t lsd_occupancy(const Tables& t, int* blocks_per_sm) {
-  const size_t smem = lsd_smem_bytes(t);
-  cudaError_t err;
-  switch (lsd_wp(t)) {
-#define VIBE_LSD_OCC(P)                                                                            \
-  case P:                                                                                          \
-    err = cudaFuncSetAttribute(k_lsd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    if (err != cudaSuccess) return err;                                                            \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_lsd<P>, kLsdThreads, smem);
-    VIBE_LSD_OCC(1)
-    VIBE_LSD_OCC(2)
-    VIBE_LSD_OCC(4)
-    VIBE_LSD_OCC(8)
-    VIBE_LSD_OCC(16)
-#undef VIBE_LSD_OCC
-    default:
-      return cudaErrorInvalidValue;
+cudaError_t lsd_occupancy(const Bounds& b, int ndem, int* blocks_per_sm) {
+  const size_t smem = lsd_smem_bytes(b, ndem);
+  switch (lsd_wp(b)) {
+    case 1: return lsd_occupancy_one<1>(smem, blocks_per_sm);
+    case 2: return lsd_occupancy_one<2>(smem, blocks_per_sm);
+    case 4: return lsd_occupancy_one<4>(smem, blocks_per_sm);
+    case 8: return lsd_occupancy_one<8>(smem, blocks_per_sm);
+    case 16: return lsd_occupancy_one<16>(smem, blocks_per_sm);
+    default: return cudaErrorInvalidValue;
   }
 }
 

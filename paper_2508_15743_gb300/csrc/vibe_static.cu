@@ -57,13 +57,13 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   if (!d_syndromes || !d_corrections) return vibe::set_error(VIBE_ERR_INVALID, "NULL syndromes or corrections");
   const vibe::Tables& t = v.t;
   // Fixed part: counters, two n-float rows per BP warp (LLR accumulator, posterior), one row set per
-  // LSD CTA. The LSD CTAs
-  // are capped at one per SM so the fixed part stays small; the rest holds the LSD hand-off queue.
+  // LSD CTA. The LSD CTAs are capped at one per SM so the fixed part stays small; the rest holds the
+  // LSD hand-off queue.
   const int bp_grid = v.bp_grid;
   const int lsd_grid = v.lsd_grid < v.num_sms ? v.lsd_grid : v.num_sms;
   const size_t ctrl_b = 256;
   const size_t bp_b = up256((size_t)bp_grid * vibe::kBpWarpsPerCta * 2 * (size_t)t.n * sizeof(float));
-  const size_t lsd_b = up256((size_t)lsd_grid * (size_t)vibe::lsd_scratch_words(t) * sizeof(uint32_t));
+  const size_t lsd_b = up256((size_t)lsd_grid * (size_t)vibe::lsd_scratch_words(v.bnd) * sizeof(uint32_t));
   const size_t fixed = ctrl_b + bp_b + lsd_b;
   const size_t per_shot = (size_t)t.n * sizeof(float) + sizeof(uint32_t);
   const long long max_b = fixed + 512 < kStaticBytes ? (long long)((kStaticBytes - fixed - 512) / per_shot) : 0;
@@ -89,12 +89,11 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   cudaError_t e = cudaMemsetAsync(ctrl, 0, ctrl_b, s);
   if (e != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
   vibe::BpArgs a{};
-  a.t = t;
-  a.T = v.T; a.M = v.M; a.alpha = v.alpha; a.want_soft = 0;
-  a.warp_smem = v.L.warp_smem; a.off_msg = v.L.off_msg; a.off_dec = v.L.off_dec;
-  a.off_s = v.L.off_s; a.off_par = v.L.off_par; a.off_cand = v.L.off_cand;
-  a.syn = d_syndromes; a.nshots = (uint32_t)B; a.corr = d_corrections; a.logical = d_logical; a.stats = d_stats;
-  a.soft = nullptr; a.obs = nullptr; a.counters = nullptr;
+  a.one = t;
+  a.dems = v.d_desc; a.ndem = 1; a.dem_of_shot = nullptr; a.bnd = v.bnd; a.want_soft = 0;
+  a.syn = d_syndromes; a.syn_stride = t.mw; a.nshots = (uint32_t)B;
+  a.corr = d_corrections; a.corr_stride = t.nw; a.logical = d_logical; a.log_stride = t.kw; a.stats = d_stats;
+  a.soft = nullptr; a.soft_stride = t.n; a.obs = nullptr; a.counters = nullptr;
   a.next_shot = ctrl; a.lsd_count = ctrl + 1; a.lsd_shots = lsd_shots; a.lsd_soft = lsd_soft;
   a.scratch = bp_scratch;
   a.scratch_pitch = 2LL * t.n;
@@ -102,14 +101,13 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   const int grid = (int)(need_ctas < bp_grid ? need_ctas : bp_grid);
   if ((e = vibe::launch_bp(a, v.msg_fp16, grid, s)) != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
   vibe::LsdArgs l{};
-  l.t = t;
-  l.T = v.T; l.order = v.lsd_order; l.want_soft = 0;
-  l.CW = (t.n + 31) / 32;
-  l.syn = d_syndromes; l.corr = d_corrections; l.logical = d_logical; l.stats = d_stats; l.soft = nullptr;
+  l.dems = v.d_desc; l.ndem = 1; l.dem_of_shot = nullptr; l.bnd = v.bnd; l.want_soft = 0;
+  l.syn = d_syndromes; l.syn_stride = t.mw; l.corr = d_corrections; l.corr_stride = t.nw;
+  l.logical = d_logical; l.log_stride = t.kw; l.stats = d_stats; l.soft = nullptr; l.soft_stride = t.n;
   l.obs = nullptr; l.counters = nullptr;
   l.lsd_count = ctrl + 1; l.lsd_shots = lsd_shots; l.lsd_soft = lsd_soft; l.lsd_next = ctrl + 2;
   l.scratch = lsd_scratch;
-  l.scratch_pitch = vibe::lsd_scratch_words(t);
+  l.scratch_pitch = vibe::lsd_scratch_words(v.bnd);
   if ((e = vibe::launch_lsd(l, lsd_grid, s)) != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
   return VIBE_OK;
 }

@@ -20,7 +20,8 @@ VIBE_ERR_NOMEM = -2
 VIBE_ERR_CUDA = -3
 VIBE_ERR_UNSUPPORTED = -4
 VIBE_NUM_COUNTERS = 8
-CNT_SHOTS, CNT_FAILURES, CNT_LSD, CNT_PAIR_ITERS, CNT_UNSOLVABLE = 0, 1, 2, 3, 4
+CNT_SHOTS, CNT_FAILURES, CNT_LSD, CNT_PAIR_ITERS, CNT_UNSOLVABLE, CNT_BAD_PROBLEM = 0, 1, 2, 3, 4, 5
+VIBE_STATUS_OK, VIBE_STATUS_UNSOLVABLE, VIBE_STATUS_BAD_PROBLEM = 0, 1, 2
 
 STATS_DTYPE = np.dtype([("status", "u1"), ("lsd_invoked", "u1"), ("n_converged", "u1"),
                         ("chosen_member", "u1"), ("iters", "<u2"), ("largest_cluster", "<u2"),
@@ -64,6 +65,14 @@ def _load():
     lib.vibe_profile.restype = ctypes.c_int
     lib.vibe_profile_read.argtypes = [vp, vp, vp, vp, vp]
     lib.vibe_profile_read.restype = ctypes.c_int
+    lib.vibe_autotune.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.vibe_autotune.restype = ctypes.c_int
+    lib.vibe_batch_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+    lib.vibe_batch_create.restype = ctypes.c_int
+    lib.vibe_batch_decode.argtypes = [vp, vp, vp, i32, i64, vp, i32, vp, i32, vp, vp, vp, vp]
+    lib.vibe_batch_decode.restype = ctypes.c_int
+    lib.vibe_batch_destroy.argtypes = [vp]
+    lib.vibe_batch_destroy.restype = ctypes.c_int
     lib.vibe_destroy.argtypes = [vp]
     lib.vibe_destroy.restype = ctypes.c_int
     lib.vibe_last_error.argtypes = []
@@ -167,9 +176,36 @@ def vibe_profile_read(h):
     return dict(bp_ms=bp.value, lsd_ms=lsd.value, bp_launches=nb.value, lsd_launches=nl.value)
 
 
+def vibe_autotune(h, d_syndromes, B, stream=None):
+    """Returns the (BP, LSD) CTAs per SM the tuner kept for this handle."""
+    bp, lsd = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(_lib.vibe_autotune(h, _ptr(d_syndromes), int(B), _stream_ptr(stream), ctypes.addressof(bp),
+                              ctypes.addressof(lsd)))
+    return bp.value, lsd.value
+
+
 def vibe_destroy(h):
     if h:
         _check(_lib.vibe_destroy(h))
+
+
+def vibe_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    out = ctypes.c_void_p()
+    _check(_lib.vibe_batch_create(arr, len(handles), ctypes.byref(out)))
+    return out.value
+
+
+def vibe_batch_decode(b, d_problem, d_syndromes, syn_stride, B, d_corrections, corr_stride, d_logical=None,
+                      log_stride=0, d_stats=None, d_observables=None, d_counters=None, stream=None):
+    _check(_lib.vibe_batch_decode(b, _ptr(d_problem), _ptr(d_syndromes), int(syn_stride), int(B),
+                                  _ptr(d_corrections), int(corr_stride), _ptr(d_logical), int(log_stride),
+                                  _ptr(d_stats), _ptr(d_observables), _ptr(d_counters), _stream_ptr(stream)))
+
+
+def vibe_batch_destroy(b):
+    if b:
+        _check(_lib.vibe_batch_destroy(b))
 
 
 # ---------------------------------------------------------------------------------------------
@@ -234,6 +270,45 @@ class Decoder:
 
     def profile_read(self):
         return vibe_profile_read(self.handle)
+
+    def autotune(self, syndromes, stream=None):
+        return vibe_autotune(self.handle, syndromes, int(syndromes.shape[0]), stream)
+
+
+class MixedBatch:
+    """Several Decoders decoded by one launch pair (vibe_batch_*); shot b uses decoders[problem[b]]."""
+
+    def __init__(self, decoders):
+        self.decoders = list(decoders)
+        self.mw = max(d.mw for d in self.decoders)
+        self.nw = max(d.nw for d in self.decoders)
+        self.kw = max(d.kw for d in self.decoders)
+        self.handle = vibe_batch_create([d.handle for d in self.decoders])
+
+    def close(self):
+        if self.handle:
+            vibe_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, problem, syndromes, observables=None, counters=None, stream=None, out=None):
+        """problem: int32 CUDA tensor [B]; syndromes: int32 CUDA tensor [B, >= max ceil(m/32)]."""
+        import torch
+        B = int(syndromes.shape[0])
+        dev = syndromes.device
+        if out is None:
+            out = dict(corrections=torch.zeros((B, self.nw), dtype=torch.int32, device=dev),
+                       logical=torch.zeros((B, self.kw), dtype=torch.int32, device=dev),
+                       stats=torch.empty((B, 12), dtype=torch.uint8, device=dev))
+        vibe_batch_decode(self.handle, problem, syndromes, syndromes.shape[1], B, out["corrections"],
+                          out["corrections"].shape[1], out["logical"], out["logical"].shape[1], out["stats"],
+                          observables, counters, stream)
+        return out
 
 
 def stats_to_numpy(stats_tensor):
