@@ -36,6 +36,8 @@ extern "C" {
 
 #define VIBE_STATUS_OK 0
 #define VIBE_STATUS_UNSOLVABLE 1 /* syndrome outside the column span of H; correction is zero */
+#define VIBE_STATUS_CLUSTER_LIMIT 3 /* LSD met a cluster of more columns than its combination records hold
+                                       (32 x 32 x words-per-lane: at least 4096, or all n); correction zero */
 #define VIBE_STATUS_BAD_PROBLEM 2 /* vibe_batch_decode: problem index outside 0..count-1; nothing decoded,
                                      correction and logical words zero */
 
@@ -57,7 +59,17 @@ typedef struct {
                         cluster for the lowest prior weight (q <= 10) */
   int32_t msg_fp16;  /* 0: FP32 messages; 1: FP16 storage of variable-to-check messages, FP32 arithmetic */
   uint64_t seed;     /* seeds the schedules when vibe_create gets schedules == NULL */
+  int32_t bp_engine; /* BP kernel: VIBE_ENGINE_AUTO, VIBE_ENGINE_WARP or VIBE_ENGINE_CTA (same results) */
 } vibe_params;
+
+/* BP engines. WARP: one warp per shot with the member's whole message image in shared memory; fast for
+ * problems whose image is small (code capacity, phenomenological). CTA: one thread block per shot, a
+ * 16-byte min/second-min/sign summary per check in shared memory and the messages in global memory;
+ * for circuit-level problems whose image does not fit. AUTO takes WARP when at least 8 warps per SM
+ * fit, else CTA. Both give the same bits. */
+#define VIBE_ENGINE_AUTO 0
+#define VIBE_ENGINE_WARP 1
+#define VIBE_ENGINE_CTA 2
 
 /* Per-shot record, 12 bytes. */
 typedef struct {

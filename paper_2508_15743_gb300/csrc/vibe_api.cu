@@ -78,42 +78,56 @@ struct Launch {
   Bounds bnd{};
   int msg_fp16 = 0;
   int device = 0, num_sms = 0;
-  int bp_blocks_per_sm = 0, lsd_blocks_per_sm = 0;
-  int bp_grid() const { return std::max(1, bp_blocks_per_sm * num_sms); }
+  int bp_blocks_per_sm = 0, bpx_blocks_per_sm = 0, lsd_blocks_per_sm = 0;
+  bool warp_engine() const { return (bnd.engines & 1) != 0; }
+  bool cta_engine() const { return (bnd.engines & 2) != 0; }
+  int bp_grid() const { return warp_engine() ? std::max(1, bp_blocks_per_sm * num_sms) : 0; }
+  int bpx_grid() const { return cta_engine() ? std::max(1, bpx_blocks_per_sm * num_sms) : 0; }
   int lsd_grid() const { return std::max(1, lsd_blocks_per_sm * num_sms); }
+  // per-CTA global scratch of the CTA engine, bytes; the candidate posteriors only with soft output
+  long long bpx_pitch(bool soft) const {
+    return (bnd.cta_scratch + (soft ? 4LL * bnd.M * bnd.n : 0LL) + 15) & ~15LL;
+  }
 };
 
 // Device memory a decode uses besides its inputs and outputs; grown on demand, reused afterwards.
 struct Workspace {
   long long chunk = 0, chunk_max = 0;
-  int bp_warps = 0, lsd_ctas = 0, pitch_m = 0;
-  unsigned int* ctrl = nullptr;   // [0] next shot, [1] LSD count, [2] next LSD shot
+  int bp_warps = 0, lsd_ctas = 0;
+  long long bpx_bytes = 0;
+  unsigned int* ctrl = nullptr;   // [0] next shot (warp engine), [1] LSD count, [2] next LSD shot, [3] next shot (CTA engine)
   uint32_t* lsd_shots = nullptr;
   float* lsd_soft = nullptr;
   float* bp_scratch = nullptr;
+  unsigned char* bpx_scratch = nullptr;
   uint32_t* lsd_scratch = nullptr;
 
   void release() {
-    cudaFree(ctrl); cudaFree(lsd_shots); cudaFree(lsd_soft); cudaFree(bp_scratch); cudaFree(lsd_scratch);
-    ctrl = nullptr; lsd_shots = nullptr; lsd_soft = nullptr; bp_scratch = nullptr; lsd_scratch = nullptr;
-    chunk = 0;
+    cudaFree(ctrl); cudaFree(lsd_shots); cudaFree(lsd_soft); cudaFree(bp_scratch); cudaFree(bpx_scratch);
+    cudaFree(lsd_scratch);
+    ctrl = nullptr; lsd_shots = nullptr; lsd_soft = nullptr; bp_scratch = nullptr; bpx_scratch = nullptr;
+    lsd_scratch = nullptr;
+    chunk = 0; bp_warps = 0; lsd_ctas = 0; bpx_bytes = 0;
   }
-  int ensure(const Launch& L, long long need) {
+  int ensure(const Launch& L, long long need, bool soft) {
     const long long want = std::min(need, chunk_max);
-    if (ctrl && want <= chunk && L.bp_grid() * vibe::kBpWarpsPerCta <= bp_warps && L.lsd_grid() <= lsd_ctas)
-      return VIBE_OK;
+    const int warps = L.bp_grid() * vibe::kBpWarpsPerCta;
+    const long long xb = (long long)L.bpx_grid() * L.bpx_pitch(soft);
+    if (ctrl && want <= chunk && warps <= bp_warps && L.lsd_grid() <= lsd_ctas && xb <= bpx_bytes) return VIBE_OK;
     const long long c = std::max(want, chunk);
+    const long long xkeep = std::max(xb, bpx_bytes);
     release();
     const Bounds& b = L.bnd;
-    const int warps = L.bp_grid() * vibe::kBpWarpsPerCta;
     VIBE_CUDA(dalloc(&ctrl, 4), "workspace");
     VIBE_CUDA(dalloc(&lsd_shots, (size_t)c), "workspace");
     VIBE_CUDA(dalloc(&lsd_soft, (size_t)c * b.n), "workspace");
     VIBE_CUDA(dalloc(&bp_scratch, (size_t)warps * (size_t)(2 + b.M) * b.n), "workspace");
+    VIBE_CUDA(dalloc(&bpx_scratch, (size_t)xkeep), "workspace");
     VIBE_CUDA(dalloc(&lsd_scratch, (size_t)L.lsd_grid() * (size_t)vibe::lsd_scratch_words(b)), "workspace");
     chunk = c;
     bp_warps = warps;
     lsd_ctas = L.lsd_grid();
+    bpx_bytes = xkeep;
     return VIBE_OK;
   }
   ~Workspace() { release(); }
@@ -155,7 +169,7 @@ struct Batch {
 };
 
 int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, cudaStream_t s) {
-  int rc = ws.ensure(L, q.B);
+  int rc = ws.ensure(L, q.B, q.soft != nullptr);
   if (rc != VIBE_OK) return rc;
   for (long long b0 = 0; b0 < q.B; b0 += ws.chunk) {
     const long long nb = std::min(ws.chunk, q.B - b0);
@@ -176,11 +190,22 @@ int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, c
     a.next_shot = ws.ctrl; a.lsd_count = ws.ctrl + 1; a.lsd_shots = ws.lsd_shots; a.lsd_soft = ws.lsd_soft;
     a.scratch = ws.bp_scratch;
     a.scratch_pitch = (long long)(2 + L.bnd.M) * L.bnd.n;
-    const int bp_grid = (int)std::min<long long>(L.bp_grid(), (nb + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
+    a.xscratch = ws.bpx_scratch;
+    a.xscratch_pitch = L.bpx_pitch(a.want_soft != 0);
+    a.next_shot_x = ws.ctrl + 3;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (prof.on) { e0 = prof.next(); e1 = prof.next(); e2 = prof.next(); }
     if (e0) cudaEventRecord(e0, s);
-    VIBE_CUDA(vibe::launch_bp(a, L.msg_fp16, bp_grid, s), "BP kernel launch");
+    if (L.warp_engine()) {
+      const int grid = (int)std::min<long long>(L.bp_grid(), (nb + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
+      a.flag_bad = 1;
+      VIBE_CUDA(vibe::launch_bp(a, L.msg_fp16, grid, s), "BP kernel launch");
+    }
+    if (L.cta_engine()) {
+      const int grid = (int)std::min<long long>(L.bpx_grid(), nb);
+      a.flag_bad = L.warp_engine() ? 0 : 1;
+      VIBE_CUDA(vibe::launch_bpx(a, L.msg_fp16, grid, s), "BP kernel launch");
+    }
     if (e1) cudaEventRecord(e1, s);
     vibe::LsdArgs l{};
     l.dems = L.d_desc; l.ndem = L.ndem; l.dem_of_shot = a.dem_of_shot; l.bnd = L.bnd;
@@ -205,31 +230,49 @@ int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, c
 int size_launch(Launch& L) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, L.device);
-  const size_t bp_smem = vibe::bp_cta_smem_bytes(L.bnd, L.mixed ? L.ndem : 0);
-  if (bp_smem > (size_t)optin)
-    return fail(VIBE_ERR_UNSUPPORTED, "BP state of one shot (%d bytes per warp) does not fit in shared memory",
-                L.bnd.warp_smem);
+  const int nd = L.mixed ? L.ndem : 0;
+  if (L.warp_engine()) {
+    if (vibe::bp_cta_smem_bytes(L.bnd, nd) > (size_t)optin)
+      return fail(VIBE_ERR_UNSUPPORTED, "BP state of one shot (%d bytes per warp) does not fit in shared memory",
+                  L.bnd.warp_smem);
+    VIBE_CUDA(vibe::bp_occupancy(L.bnd, nd, L.msg_fp16, &L.bp_blocks_per_sm), "BP occupancy");
+    if (L.bp_blocks_per_sm < 1) return fail(VIBE_ERR_UNSUPPORTED, "the BP kernel cannot be resident");
+  }
+  if (L.cta_engine()) {
+    if (vibe::bpx_cta_smem_bytes(L.bnd, nd) > (size_t)optin)
+      return fail(VIBE_ERR_UNSUPPORTED, "check summaries of one shot (%d bytes) do not fit in shared memory",
+                  L.bnd.cta_smem);
+    VIBE_CUDA(vibe::bpx_occupancy(L.bnd, nd, L.msg_fp16, &L.bpx_blocks_per_sm), "BP occupancy");
+    if (L.bpx_blocks_per_sm < 1) return fail(VIBE_ERR_UNSUPPORTED, "the BP kernel cannot be resident");
+  }
   if (vibe::lsd_smem_bytes(L.bnd, L.ndem) > (size_t)optin)
     return fail(VIBE_ERR_UNSUPPORTED, "LSD state of one shot does not fit in shared memory");
-  VIBE_CUDA(vibe::bp_occupancy(L.bnd, L.mixed ? L.ndem : 0, L.msg_fp16, &L.bp_blocks_per_sm), "BP occupancy");
   VIBE_CUDA(vibe::lsd_occupancy(L.bnd, L.ndem, &L.lsd_blocks_per_sm), "LSD occupancy");
-  if (L.bp_blocks_per_sm < 1 || L.lsd_blocks_per_sm < 1)
-    return fail(VIBE_ERR_UNSUPPORTED, "kernels cannot be resident with this problem size");
+  if (L.lsd_blocks_per_sm < 1) return fail(VIBE_ERR_UNSUPPORTED, "the LSD kernel cannot be resident");
   return VIBE_OK;
 }
 
-Bounds bounds_of(const Tables& t) {
+// Sizes bounding every problem of a launch; the engine-specific ones over that engine's problems only.
+Bounds bounds_over(const Tables* ts, int count) {
   Bounds b{};
-  b.m = t.m; b.n = t.n; b.W = t.W; b.nw = t.nw; b.kw = t.kw; b.M = t.M; b.DP = t.DP; b.RP = t.RP;
-  b.warp_smem = t.warp_smem; b.lsd_order = t.lsd_order;
+  bool first_warp = true;
+  for (int i = 0; i < count; ++i) {
+    const Tables& t = ts[i];
+    b.m = std::max(b.m, t.m); b.n = std::max(b.n, t.n); b.W = std::max(b.W, t.W); b.nw = std::max(b.nw, t.nw);
+    b.kw = std::max(b.kw, t.kw); b.M = std::max(b.M, t.M); b.DP = std::max(b.DP, t.DP);
+    b.lsd_order = std::max(b.lsd_order, t.lsd_order);
+    if (t.engine == VIBE_ENGINE_WARP) {
+      b.engines |= 1;
+      b.RP = first_warp ? t.RP : (b.RP == t.RP ? b.RP : 0);
+      first_warp = false;
+      b.warp_smem = std::max(b.warp_smem, t.warp_smem);
+    } else {
+      b.engines |= 2;
+      b.cta_smem = std::max(b.cta_smem, t.cta_smem);
+      b.cta_scratch = std::max(b.cta_scratch, t.cta_scratch);
+    }
+  }
   return b;
-}
-
-void widen(Bounds& b, const Tables& t) {
-  b.m = std::max(b.m, t.m); b.n = std::max(b.n, t.n); b.W = std::max(b.W, t.W); b.nw = std::max(b.nw, t.nw);
-  b.kw = std::max(b.kw, t.kw); b.M = std::max(b.M, t.M); b.DP = std::max(b.DP, t.DP);
-  b.RP = b.RP == t.RP ? b.RP : 0;
-  b.warp_smem = std::max(b.warp_smem, t.warp_smem); b.lsd_order = std::max(b.lsd_order, t.lsd_order);
 }
 
 }  // namespace
@@ -247,6 +290,9 @@ struct vibe_handle {
   uint32_t *csc_ent = nullptr, *sched = nullptr, *lvl_off = nullptr, *perm = nullptr;
   float* lam = nullptr;
   void* msg_init = nullptr;
+  uint32_t* row_edge = nullptr;
+  void* msg_csc = nullptr;
+  float4* sum_init = nullptr;
   unsigned long long* tmp_counters = nullptr;
   // host-buffer staging
   long long stage_cap = 0;
@@ -266,7 +312,7 @@ struct vibe_handle {
     cudaFree(tmp_counters);
     cudaFree(rowptr); cudaFree(colidx); cudaFree(colptr); cudaFree(rowidx); cudaFree(lrowptr); cudaFree(lcolidx);
     cudaFree(nlev); cudaFree(csc_ent); cudaFree(sched); cudaFree(lvl_off); cudaFree(perm); cudaFree(lam);
-    cudaFree(msg_init); cudaFree(d_desc);
+    cudaFree(msg_init); cudaFree(row_edge); cudaFree(msg_csc); cudaFree(sum_init); cudaFree(d_desc);
     cudaSetDevice(prev);
   }
 };
@@ -329,9 +375,12 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   if (p->M < 1 || p->M > K || p->M > 32) return fail(VIBE_ERR_INVALID, "M must be in 1..min(K, 32)");
   if (p->lsd_order < 0 || p->lsd_order > 10) return fail(VIBE_ERR_INVALID, "lsd_order must be in 0..10");
   if (p->msg_fp16 != 0 && p->msg_fp16 != 1) return fail(VIBE_ERR_INVALID, "msg_fp16 must be 0 or 1");
+  if (p->bp_engine < VIBE_ENGINE_AUTO || p->bp_engine > VIBE_ENGINE_CTA)
+    return fail(VIBE_ERR_INVALID, "bp_engine must be VIBE_ENGINE_AUTO, _WARP or _CTA");
   for (int j = 0; j < n; ++j)
     if (!(priors[j] > 0.0 && priors[j] < 0.5)) return fail(VIBE_ERR_INVALID, "prior %d = %g outside (0, 0.5)", j, priors[j]);
-  if (n >= (1 << 23) || m >= (1 << 23)) return fail(VIBE_ERR_UNSUPPORTED, "n and m must be below 2^23");
+  if (n >= (1 << 23)) return fail(VIBE_ERR_UNSUPPORTED, "n must be below 2^23");
+  if (m > 16384) return fail(VIBE_ERR_UNSUPPORTED, "m must be at most 16384");
   const int E = H->rowptr[m];
   int maxrow = 0;
   for (int r = 0; r < m; ++r) maxrow = std::max(maxrow, H->rowptr[r + 1] - H->rowptr[r]);
@@ -370,6 +419,19 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   t.mw = (m + 31) / 32; t.nw = (n + 31) / 32; t.kw = (k + 31) / 32; t.W = t.mw;
   t.T = p->max_iter; t.M = p->M; t.lsd_order = p->lsd_order; t.alpha = p->alpha;
   vibe::bp_warp_smem_bytes(&t, p->msg_fp16);
+  vibe::bpx_layout(&t, p->msg_fp16);
+  t.engine = p->bp_engine;
+  if (t.engine == VIBE_ENGINE_AUTO) {
+    // the warp engine when its per-warp image leaves at least 8 warps per SM, else the CTA engine
+    int optin = 0, blocks = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    t.engine = VIBE_ENGINE_WARP;
+    const Bounds bw = bounds_over(&t, 1);
+    t.engine = VIBE_ENGINE_CTA;
+    if (vibe::bp_cta_smem_bytes(bw, 0) <= (size_t)optin &&
+        vibe::bp_occupancy(bw, 0, p->msg_fp16, &blocks) == cudaSuccess && blocks * vibe::kBpWarpsPerCta >= 8)
+      t.engine = VIBE_ENGINE_WARP;
+  }
   const int Lnnz = L->rowptr[k];
   const size_t msg_bytes = (size_t)m * t.RP * (p->msg_fp16 ? 2 : 4);
   const size_t lev_scratch = std::max<size_t>(2 * (size_t)n + E, (size_t)K * ((size_t)m + 3 * (size_t)n + 1));
@@ -391,6 +453,9 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   VIBE_TRY(dalloc(&h->perm, (size_t)K * n), "tables");
   VIBE_TRY(dalloc(&h->lam, n), "tables");
   VIBE_TRY(cudaMalloc(&h->msg_init, std::max<size_t>(msg_bytes, 16)), "tables");
+  VIBE_TRY(dalloc(&h->row_edge, E), "tables");
+  VIBE_TRY(cudaMalloc(&h->msg_csc, ((size_t)E * (p->msg_fp16 ? 2 : 4) + 15) / 16 * 16 + 16), "tables");
+  VIBE_TRY(dalloc(&h->sum_init, m), "tables");
   VIBE_TRY(dalloc(&h->d_desc, 1), "tables");
   VIBE_TRY(dalloc(&scratch, lev_scratch), "tables");
   VIBE_TRY(dalloc(&h->tmp_counters, VIBE_NUM_COUNTERS), "tables");
@@ -406,11 +471,13 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
     VIBE_TRY(vibe::seeded_schedules(h->perm, n, K, p->seed, s), "schedule kernel");
   }
   VIBE_TRY(vibe::build_tables(h->rowptr, h->colidx, m, n, K, h->perm, t.RP, t.DP, p->msg_fp16, h->lam, h->colptr,
-                              h->rowidx, h->csc_ent, h->msg_init, h->sched, h->lvl_off, h->nlev, scratch, s),
+                              h->rowidx, h->csc_ent, h->msg_init, h->sched, h->lvl_off, h->nlev, h->row_edge,
+                              h->msg_csc, h->sum_init, scratch, s),
            "graph builder");
   t.rowptr = h->rowptr; t.colidx = h->colidx; t.colptr = h->colptr; t.rowidx = h->rowidx;
   t.csc_ent = h->csc_ent; t.lam = h->lam; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
   t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
+  t.row_edge = h->row_edge; t.msg_csc = h->msg_csc; t.sum_init = h->sum_init;
   VIBE_TRY(cudaMemcpyAsync(h->d_desc, &t, sizeof(Tables), cudaMemcpyHostToDevice, s), "upload");
   VIBE_TRY(cudaStreamSynchronize(s), "graph builder");
   cudaFree(scratch);
@@ -421,7 +488,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   h->L.one = t;
   h->L.d_desc = h->d_desc;
   h->L.ndem = 1;
-  h->L.bnd = bounds_of(t);
+  h->L.bnd = bounds_over(&t, 1);
   if ((rc = size_launch(h->L)) != VIBE_OK) return bail(rc);
   h->ws.chunk_max = std::max<long long>(1, (long long)(kWorkspaceBytes / ((size_t)n * 4 + 8)));
   *out = h;
@@ -541,7 +608,8 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
   const Tables& t = h->t;
   uint32_t* corr = nullptr;
   VIBE_CUDA(dalloc(&corr, (size_t)B * t.nw), "autotune");
-  const int bp_max = h->L.bp_blocks_per_sm, lsd_max = h->L.lsd_blocks_per_sm;
+  int& bp_cfg = h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm;
+  const int bp_max = bp_cfg, lsd_max = h->L.lsd_blocks_per_sm;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -552,7 +620,7 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
   const int lsd_try[] = {lsd_max, std::max(1, lsd_max / 2)};
   for (int bi = 0; bi < 3 && rc == VIBE_OK; ++bi)
     for (int li = 0; li < 2 && rc == VIBE_OK; ++li) {
-      h->L.bp_blocks_per_sm = std::max(1, bp_try[bi]);
+      bp_cfg = std::max(1, bp_try[bi]);
       h->L.lsd_blocks_per_sm = std::max(1, lsd_try[li]);
       Batch q{nullptr, d_syndromes, t.mw, B, corr, t.nw, nullptr, t.kw, nullptr, nullptr, t.n, nullptr, nullptr};
       if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;   // warm-up (and workspace)
@@ -562,9 +630,9 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_bp = h->L.bp_blocks_per_sm; best_lsd = h->L.lsd_blocks_per_sm; }
+      if (ms < best) { best = ms; best_bp = bp_cfg; best_lsd = h->L.lsd_blocks_per_sm; }
     }
-  h->L.bp_blocks_per_sm = best_bp;
+  bp_cfg = best_bp;
   h->L.lsd_blocks_per_sm = best_lsd;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -589,14 +657,13 @@ int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** o
     if (!handles[i]) return fail(VIBE_ERR_INVALID, "handle %d is NULL", i);
   const vibe_handle* h0 = handles[0];
   std::vector<Tables> desc(count);
-  Bounds b = bounds_of(h0->t);
   for (int i = 0; i < count; ++i) {
     const vibe_handle* h = handles[i];
     if (h->device != h0->device) return fail(VIBE_ERR_INVALID, "handles live on different devices");
     if (h->L.msg_fp16 != h0->L.msg_fp16) return fail(VIBE_ERR_INVALID, "handles mix FP16 and FP32 messages");
     desc[i] = h->t;
-    widen(b, h->t);
   }
+  const Bounds b = bounds_over(desc.data(), count);
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != h0->device)
     return fail(VIBE_ERR_INVALID, "the handles' device must be current");

@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_b
     if (MIXED) {
       const int di = __ldg(a.dem_of_shot + shot);
       if ((unsigned)di >= (unsigned)a.ndem) {
+        if (!a.flag_bad) continue;
         // problem index outside the launch's table: zero outputs, status BAD_PROBLEM, no decoding
         for (int w = lane; w < a.corr_stride; w += 32) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
         if (a.logical)
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_b
         if (a.counters && lane == 0) atomicAdd(a.counters + VIBE_CNT_BAD_PROBLEM, 1ull);
         continue;
       }
+      if (sdem[di].engine != VIBE_ENGINE_WARP) continue;   // left to the CTA engine
       decode_shot<MT, DP, RPC, true>(a, sdem[di], shot, base, acc, lpost, cand_post, lane, my_iters, my_shots,
                                      my_fail);
     } else {

@@ -54,10 +54,12 @@ __global__ void k_csc_fill(const int32_t* __restrict__ rowptr, const int32_t* __
   }
 }
 
-// Sort each column's entries by check (insertion sort, degree <= 32) and emit rowidx and csc_ent.
-__global__ void k_csc_finish(int n, int DP, int RP, int spc, const int32_t* __restrict__ colptr,
-                             uint32_t* __restrict__ packed, int32_t* __restrict__ rowidx,
-                             uint32_t* __restrict__ csc_ent) {
+// Sort each column's entries by check (insertion sort, degree <= 32) and emit rowidx, csc_ent and,
+// for every CSR entry, the CSC edge id of the same (check, column) pair.
+__global__ void k_csc_finish(int n, int DP, int RP, int spc, const int32_t* __restrict__ rowptr,
+                             const int32_t* __restrict__ colptr, uint32_t* __restrict__ packed,
+                             int32_t* __restrict__ rowidx, uint32_t* __restrict__ csc_ent,
+                             uint32_t* __restrict__ row_edge) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     int b = colptr[v], d = colptr[v + 1] - b;
     for (int i = 1; i < d; ++i) {
@@ -69,7 +71,10 @@ __global__ void k_csc_finish(int n, int DP, int RP, int spc, const int32_t* __re
     for (int k = 0; k < DP; ++k) {
       uint32_t x = k < d ? packed[b + k] : 0u;
       csc_ent[(size_t)v * DP + k] = k < d ? csc_entry(x >> 8, x & 0xffu, RP, spc) : 0u;
-      if (k < d) rowidx[b + k] = (int32_t)(x >> 8);
+      if (k < d) {
+        rowidx[b + k] = (int32_t)(x >> 8);
+        row_edge[rowptr[x >> 8] + (x & 0xffu)] = (uint32_t)(b + k);
+      }
     }
   }
 }
@@ -93,6 +98,43 @@ __global__ void k_msg_init(const int32_t* __restrict__ rowptr, const int32_t* __
     const int deg = rowptr[c + 1] - rowptr[c];
     float x = slot < deg ? lam[colidx[rowptr[c] + slot]] : __int_as_float(0x7f800000);
     out[t] = to_msg<MT>(x);
+  }
+}
+
+template <typename MT>
+__device__ __forceinline__ float msg_magnitude(MT x);
+template <>
+__device__ __forceinline__ float msg_magnitude<float>(float x) { return fabsf(x); }
+template <>
+__device__ __forceinline__ float msg_magnitude<__half>(__half x) { return fabsf(__half2float(x)); }
+
+// CTA engine: prior messages in CSC edge order.
+template <typename MT>
+__global__ void k_msg_csc(const int32_t* __restrict__ colptr, int n, const float* __restrict__ lam,
+                          MT* __restrict__ out) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const MT x = to_msg<MT>(lam[v]);
+    for (int e = colptr[v]; e < colptr[v + 1]; ++e) out[e] = x;
+  }
+}
+
+// CTA engine: per check, the smallest and second smallest prior-message magnitude over its row (with
+// multiplicity), the CSC edge id of the first smallest in row order, and the parity of the signs.
+template <typename MT>
+__global__ void k_sum_init(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int m,
+                           const uint32_t* __restrict__ row_edge, const float* __restrict__ lam,
+                           float4* __restrict__ out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    float m1 = __int_as_float(0x7f800000), m2 = m1;
+    uint32_t i1 = 0xffffffffu, sg = 0u;
+    for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
+      const MT x = to_msg<MT>(lam[colidx[q]]);
+      const float a = msg_magnitude<MT>(x);
+      sg ^= (float)x < 0.0f ? 1u : 0u;
+      if (a < m1) { m2 = m1; m1 = a; i1 = row_edge[q]; }
+      else if (a < m2) m2 = a;
+    }
+    out[c] = make_float4(m1, m2, __uint_as_float(i1), __uint_as_float(sg));
   }
 }
 
@@ -180,7 +222,8 @@ cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cuda
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K, const uint32_t* d_perm,
                          int RP, int DP, int msg_fp16, const float* d_lam, int32_t* d_colptr, int32_t* d_rowidx,
                          uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint32_t* d_lvl_off,
-                         int32_t* d_nlev, int32_t* d_scratch, cudaStream_t s) {
+                         int32_t* d_nlev, uint32_t* d_row_edge, void* d_msg_csc, float4* d_sum_init,
+                         int32_t* d_scratch, cudaStream_t s) {
   // scratch layout: cnt[n] | fill[n] | packed[E] ; later reused by k_levels (K*(m+3n+1))
   int E = 0;
   cudaError_t err = cudaMemcpyAsync(&E, d_rowptr + m, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -193,7 +236,15 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
   k_col_count<<<grid_for(E, 256), 256, 0, s>>>(d_colidx, E, cnt);
   k_scan_single<<<1, 1024, 0, s>>>(cnt, n, d_colptr);
   k_csc_fill<<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_colptr, fill, packed);
-  k_csc_finish<<<grid_for(n, 128), 128, 0, s>>>(n, DP, RP, msg_fp16 ? 8 : 4, d_colptr, packed, d_rowidx, d_csc_ent);
+  k_csc_finish<<<grid_for(n, 128), 128, 0, s>>>(n, DP, RP, msg_fp16 ? 8 : 4, d_rowptr, d_colptr, packed, d_rowidx,
+                                                 d_csc_ent, d_row_edge);
+  if (msg_fp16) {
+    k_msg_csc<__half><<<grid_for(n, 128), 128, 0, s>>>(d_colptr, n, d_lam, static_cast<__half*>(d_msg_csc));
+    k_sum_init<__half><<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_row_edge, d_lam, d_sum_init);
+  } else {
+    k_msg_csc<float><<<grid_for(n, 128), 128, 0, s>>>(d_colptr, n, d_lam, static_cast<float*>(d_msg_csc));
+    k_sum_init<float><<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_row_edge, d_lam, d_sum_init);
+  }
   if (msg_fp16)
     k_msg_init<__half><<<grid_for((long long)m * RP, 256), 256, 0, s>>>(d_rowptr, d_colidx, m, RP, d_lam,
                                                                        static_cast<__half*>(d_msg_init));

@@ -11,7 +11,8 @@
 
 namespace vibe {
 
-constexpr int kBpWarpsPerCta = 2;   // persistent BP kernel: warps per CTA, one shot per warp
+constexpr int kBpWarpsPerCta = 2;   // warp engine: warps per CTA, one shot per warp
+constexpr int kBpxThreads = 256;    // CTA engine: threads per CTA, one shot per CTA
 constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
 constexpr int kMaxRowDeg = 255;     // position of an edge inside its check row fits in 8 bits
 constexpr int kMaxColDeg = 32;
@@ -45,7 +46,12 @@ struct Tables {
   int W;         // words of a bit vector over the checks: ceil(m/32)
   int T, M, lsd_order;
   float alpha;
-  int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // BP per-warp shared memory, bytes
+  int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // warp engine: per-warp shared memory, bytes
+  int engine;    // VIBE_ENGINE_WARP or VIBE_ENGINE_CTA
+  // CTA engine: shared memory of one CTA (bytes) and global scratch of one CTA (bytes, 16-aligned parts)
+  int xo_summ, xo_s, xo_par, xo_dec, xo_rl, cta_smem;
+  // xg_cpost = cta_scratch: the M*n candidate posteriors (soft output only) follow the fixed part
+  long long xg_msg, xg_lpost, xg_acc, xg_cand, xg_cpost, cta_scratch;
   const int32_t* rowptr;   // H CSR
   const int32_t* colidx;
   const int32_t* colptr;   // H CSC, checks ascending in each column
@@ -58,6 +64,10 @@ struct Tables {
   const int32_t* nlev;     // K level counts
   const int32_t* lrowptr;  // L CSR
   const int32_t* lcolidx;
+  // CTA engine
+  const uint32_t* row_edge; // E: for each CSR entry of H, the CSC edge id of the same (check, column)
+  const void* msg_csc;      // E messages (float or half) in CSC edge order: lambda of the edge's column
+  const float4* sum_init;   // m: (min1, min2, edge id of min1, sign parity) of the prior messages per row
 };
 
 // Sizes that bound every problem of a launch (shared-memory layouts, strides, scratch pitches).
@@ -66,6 +76,9 @@ struct Bounds {
   int RP;          // common row pitch if all problems share it, else 0
   int warp_smem;   // largest BP per-warp layout
   int lsd_order;   // largest LSD order
+  int cta_smem;    // largest CTA-engine shared-memory layout (0 if no problem uses that engine)
+  long long cta_scratch;   // largest CTA-engine global scratch per CTA, bytes
+  int engines;     // bit 0: some problem uses the warp engine, bit 1: the CTA engine
 };
 
 struct BpArgs {
@@ -75,6 +88,7 @@ struct BpArgs {
   const int32_t* dem_of_shot;  // problem of each shot (mixed launch), or NULL
   Bounds bnd;
   int want_soft;
+  int flag_bad;                // this kernel reports shots whose problem index is out of range
   // batch (one chunk); strides in 32-bit words, soft stride in floats
   const uint32_t* syn;
   int syn_stride;
@@ -93,10 +107,14 @@ struct BpArgs {
   unsigned int* lsd_count;
   uint32_t* lsd_shots;
   float* lsd_soft;             // pitch bnd.n floats per queued shot
-  // per-warp global scratch: n floats (LLR accumulator), n floats (posterior), M*n floats (candidate
-  // posteriors, only with want_soft); pitch in floats
+  // warp engine, per-warp global scratch: n floats (LLR accumulator), n floats (posterior), M*n floats
+  // (candidate posteriors, only with want_soft); pitch in floats
   float* scratch;
   long long scratch_pitch;
+  // CTA engine, per-CTA global scratch (Tables::xg_* offsets); pitch in bytes
+  unsigned char* xscratch;
+  long long xscratch_pitch;
+  unsigned int* next_shot_x;   // the CTA engine's own shot counter
 };
 
 struct LsdArgs {
@@ -158,8 +176,8 @@ int set_error(int code, const char* msg);
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K,
                          const uint32_t* d_perm, int RP, int DP, int msg_fp16, const float* d_lam,
                          int32_t* d_colptr, int32_t* d_rowidx, uint32_t* d_csc_ent, void* d_msg_init,
-                         uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev, int32_t* d_scratch,
-                         cudaStream_t s);
+                         uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev, uint32_t* d_row_edge,
+                         void* d_msg_csc, float4* d_sum_init, int32_t* d_scratch, cudaStream_t s);
 cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
 
 // K1: persistent BP + ensemble selection (vibe_bp.cu)
@@ -169,7 +187,15 @@ size_t bp_cta_smem_bytes(const Bounds& b, int ndem);
 cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
 cudaError_t bp_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_per_sm);
 
-// K3: LSD (vibe_lsd.cu)
+// K1': CTA-engine BP + ensemble selection (vibe_bpx.cu)
+void bpx_layout(Tables* t, int msg_fp16);   // fills t's xo_*/xg_* fields
+size_t bpx_cta_smem_bytes(const Bounds& b, int ndem);
+cudaError_t launch_bpx(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
+cudaError_t bpx_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_per_sm);
+
+// K3: LSD (vibe_lsd.cu). The per-column arrays (4 words per column) stay in shared memory up to 6144
+// columns and move to the CTA's global scratch above that.
+__host__ __device__ inline bool lsd_cols_in_smem(const Bounds& b) { return b.n <= 6144; }
 size_t lsd_smem_bytes(const Bounds& b, int ndem);
 long long lsd_scratch_words(const Bounds& b);
 cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s);

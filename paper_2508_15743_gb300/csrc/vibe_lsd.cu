@@ -16,6 +16,8 @@
 // Warps work on different clusters in parallel; the merge bookkeeping of each round is serial (one
 // thread) because it is short (one pick per invalid cluster). Every loop is bounded: at most n + 1
 // rounds (each adds a column), list walks bounded by list lengths.
+#include <algorithm>
+
 #include "vibe_internal.cuh"
 
 namespace vibe {
@@ -178,17 +180,22 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kLsdThreads / 32;
   // arrays sized by the launch's bounds; each shot uses the first m / n entries of its problem
-  const int mB = a.bnd.m, nB = a.bnd.n, WB = a.bnd.W, nwB = a.bnd.nw, CWB = (a.bnd.n + 31) / 32;
+  // combination records cover the first 32 * CW columns of a cluster in reliability order
+  const int mB = a.bnd.m, nB = a.bnd.n, WB = a.bnd.W, nwB = a.bnd.nw, CWB = min((a.bnd.n + 31) / 32, 32 * WP);
+  const bool cols_smem = lsd_cols_in_smem(a.bnd);
+  uint32_t* basis = a.scratch + (long long)blockIdx.x * a.scratch_pitch;   // m * W
   LsdShared S;
   Tables* sdem;
   {
     unsigned char* p = smem;
     auto take = [&](size_t bytes) { unsigned char* r = p; p += (bytes + 15) & ~(size_t)15; return r; };
     S.best = reinterpret_cast<unsigned long long*>(take(8 * (size_t)mB));
-    S.key = reinterpret_cast<uint32_t*>(take(4 * (size_t)nB));
-    S.col_root = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
-    S.col_next = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
-    S.pend_next = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
+    if (cols_smem) {
+      S.key = reinterpret_cast<uint32_t*>(take(4 * (size_t)nB));
+      S.col_root = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
+      S.col_next = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
+      S.pend_next = reinterpret_cast<int32_t*>(take(4 * (size_t)nB));
+    }
     S.ck_par = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
     S.rank = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
     S.b_head = reinterpret_cast<int32_t*>(take(4 * (size_t)mB));
@@ -213,12 +220,18 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     const int words = a.ndem * (int)(sizeof(Tables) / 4);
     for (int q = tid; q < words; q += kLsdThreads) dst[q] = __ldg(src + q);
   }
-  uint32_t* basis = a.scratch + (long long)blockIdx.x * a.scratch_pitch;   // m * W
   uint32_t* combrow = basis + (size_t)mB * WB;                              // m * CW
   const size_t sort_off = ((size_t)mB * WB + (size_t)mB * CWB + 1) & ~(size_t)1;   // 8-byte aligned
   unsigned long long* sortA = reinterpret_cast<unsigned long long*>(basis + sort_off);  // n
   unsigned long long* sortB = sortA + nB;                                    // n
   uint32_t* freecomb = reinterpret_cast<uint32_t*>(sortB + nB);             // per warp (kFreeRows+1) * CW
+  if (!cols_smem) {                                                          // 4 * n, after the free rows
+    uint32_t* cols = freecomb + (size_t)nwarps * (kFreeRows + 1) * CWB;
+    S.key = cols;
+    S.col_root = reinterpret_cast<int32_t*>(cols + nB);
+    S.col_next = reinterpret_cast<int32_t*>(cols + 2 * (size_t)nB);
+    S.pend_next = reinterpret_cast<int32_t*>(cols + 3 * (size_t)nB);
+  }
   const unsigned int total = *a.lsd_count;
 
   for (;;) {
@@ -231,7 +244,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     const int di = a.dem_of_shot ? __ldg(a.dem_of_shot + shot) : 0;
     if ((unsigned)di >= (unsigned)a.ndem) continue;   // the BP kernel queues valid problems only
     const Tables& t = sdem[di];
-    const int n = t.n, m = t.m, W = t.W, nw = t.nw, CW = (t.n + 31) / 32;
+    const int n = t.n, m = t.m, W = t.W, nw = t.nw, CW = min((t.n + 31) / 32, 32 * WP);
     const float* vsoft = a.lsd_soft + (size_t)q * nB;
     const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
 
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
       S.c_head[c] = -1; S.c_tail[c] = -1; S.c_cnt[c] = 0;
       S.p_head[c] = -1; S.p_tail[c] = -1;
     }
-    if (tid == 0) { S.flags[1] = 0; S.flags[2] = 0; }
+    if (tid == 0) { S.flags[1] = 0; S.flags[2] = 0; S.flags[5] = 0; }
     __syncthreads();
 
     for (int round = 0; round <= n + 1; ++round) {
@@ -380,6 +393,10 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
       for (int k = warp; k < nr; k += nwarps) {
         const int r = S.dlist[k];
         const int kap = S.c_cnt[r];
+        if (kap > 32 * CW) {   // more columns than the combination records hold
+          if (lane == 0) S.flags[5] = 1;
+          continue;
+        }
         unsigned long long* A = sortA + S.rank[r];
         unsigned long long* Bv = sortB + S.rank[r];
         if (lane == 0) {
@@ -502,7 +519,8 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     }
     __syncthreads();
     // outputs
-    const bool solved = status == 1;
+    const bool limit = status == 1 && S.flags[5] != 0;
+    const bool solved = status == 1 && !limit;
     for (int w = tid; w < nw; w += kLsdThreads) a.corr[(size_t)shot * a.corr_stride + w] = solved ? S.ebits[w] : 0u;
     if (a.want_soft)
       for (int j = tid; j < n; j += kLsdThreads) a.soft[(size_t)shot * a.soft_stride + j] = vsoft[j];
@@ -523,7 +541,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
       if (lane == 0) {
         if (a.stats) {
           vibe_shot_stats st;
-          st.status = solved ? VIBE_STATUS_OK : VIBE_STATUS_UNSOLVABLE;
+          st.status = solved ? VIBE_STATUS_OK : limit ? VIBE_STATUS_CLUSTER_LIMIT : VIBE_STATUS_UNSOLVABLE;
           st.lsd_invoked = 1; st.n_converged = 0; st.chosen_member = 255;
           st.iters = (uint16_t)t.T;
           st.largest_cluster = (uint16_t)min(S.flags[4], 65535);
@@ -532,7 +550,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
         }
         if (a.counters) {
           atomicAdd(a.counters + VIBE_CNT_LSD, 1ull);
-          if (!solved) atomicAdd(a.counters + VIBE_CNT_UNSOLVABLE, 1ull);
+          if (!solved && !limit) atomicAdd(a.counters + VIBE_CNT_UNSOLVABLE, 1ull);
           if (fail) atomicAdd(a.counters + VIBE_CNT_FAILURES, 1ull);
         }
       }
@@ -542,8 +560,10 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Words per lane of the kernel's bit vectors: enough for the check vectors, and for combination
+// records of all n columns up to n = 4096 (larger problems record clusters of up to 32 * 32 * WP).
 int lsd_wp(const Bounds& b) {
-  const int need = max((b.W + 31) / 32, ((b.n + 31) / 32 + 31) / 32);
+  const int need = max(max((b.W + 31) / 32, min(((b.n + 31) / 32 + 31) / 32, 4)), 1);
   int wp = 1;
   while (wp < need) wp <<= 1;
   return wp;
@@ -568,15 +588,16 @@ cudaError_t lsd_occupancy_one(size_t smem, int* out) {
 
 size_t lsd_smem_bytes(const Bounds& b, int ndem) {
   const size_t m = b.m, n = b.n;
-  return a16(8 * m) + 4 * a16(4 * n) + 11 * a16(4 * m) + a16(4 * (size_t)b.W) + a16(4 * (size_t)b.nw) + a16(32) +
-         2 * a16(m) + a16((size_t)ndem * sizeof(Tables));
+  return a16(8 * m) + (lsd_cols_in_smem(b) ? 4 * a16(4 * n) : 0) + 11 * a16(4 * m) + a16(4 * (size_t)b.W) +
+         a16(4 * (size_t)b.nw) + a16(32) + 2 * a16(m) + a16((size_t)ndem * sizeof(Tables));
 }
 
 long long lsd_scratch_words(const Bounds& b) {
-  const long long CW = (b.n + 31) / 32;
+  const long long CW = std::min<long long>((b.n + 31) / 32, 32LL * lsd_wp(b));
   const long long head = ((long long)b.m * b.W + (long long)b.m * CW + 1) & ~1LL;
   const long long free_rows = (long long)(kLsdThreads / 32) * (kFreeRows + 1) * CW;
-  return (head + 4LL * b.n + free_rows + 2 + 1) & ~1LL;   // even: every CTA's slice stays 8-byte aligned
+  const long long cols = lsd_cols_in_smem(b) ? 0 : 4LL * b.n;
+  return (head + 4LL * b.n + free_rows + cols + 2 + 1) & ~1LL;   // even: every CTA's slice stays 8-byte aligned
 }
 
 cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s) {

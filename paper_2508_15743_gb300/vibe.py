@@ -21,7 +21,7 @@ VIBE_ERR_CUDA = -3
 VIBE_ERR_UNSUPPORTED = -4
 VIBE_NUM_COUNTERS = 8
 CNT_SHOTS, CNT_FAILURES, CNT_LSD, CNT_PAIR_ITERS, CNT_UNSOLVABLE, CNT_BAD_PROBLEM = 0, 1, 2, 3, 4, 5
-VIBE_STATUS_OK, VIBE_STATUS_UNSOLVABLE, VIBE_STATUS_BAD_PROBLEM = 0, 1, 2
+VIBE_STATUS_OK, VIBE_STATUS_UNSOLVABLE, VIBE_STATUS_BAD_PROBLEM, VIBE_STATUS_CLUSTER_LIMIT = 0, 1, 2, 3
 
 STATS_DTYPE = np.dtype([("status", "u1"), ("lsd_invoked", "u1"), ("n_converged", "u1"),
                         ("chosen_member", "u1"), ("iters", "<u2"), ("largest_cluster", "<u2"),
@@ -42,7 +42,11 @@ class vibe_csr(ctypes.Structure):
 
 class vibe_params(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("M", ctypes.c_int32),
-                ("lsd_order", ctypes.c_int32), ("msg_fp16", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("lsd_order", ctypes.c_int32), ("msg_fp16", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("bp_engine", ctypes.c_int32)]
+
+
+ENGINE_AUTO, ENGINE_WARP, ENGINE_CTA = 0, 1, 2
 
 
 def _load():
@@ -215,14 +219,16 @@ def vibe_batch_destroy(b):
 class Decoder:
     """One resident decoding problem: vibe_create at construction, vibe_destroy on close()."""
 
-    def __init__(self, dem, K, schedules=None, T=30, alpha=0.625, M=None, lsd_order=0, msg_fp16=False, seed=0):
+    def __init__(self, dem, K, schedules=None, T=30, alpha=0.625, M=None, lsd_order=0, msg_fp16=False, seed=0,
+                 engine=ENGINE_AUTO):
         if M is None:
             M = 1 if K == 1 else min(5, K)
         self.dem = dem
         self.m, self.n, self.k = dem.m, dem.n, dem.k
         self.mw, self.nw, self.kw = (self.m + 31) // 32, (self.n + 31) // 32, (self.k + 31) // 32
         self.K, self.T, self.M = K, T, M
-        self.params = vibe_params(int(T), float(alpha), int(M), int(lsd_order), int(bool(msg_fp16)), int(seed))
+        self.params = vibe_params(int(T), float(alpha), int(M), int(lsd_order), int(bool(msg_fp16)), int(seed),
+                                  int(engine))
         self.handle = vibe_create(dem.H, dem.L, dem.priors, K, schedules, self.params)
 
     def close(self):
