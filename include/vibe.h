@@ -59,17 +59,17 @@ typedef struct {
                         cluster for the lowest prior weight (q <= 10) */
   int32_t msg_fp16;  /* 0: FP32 messages; 1: FP16 storage of variable-to-check messages, FP32 arithmetic */
   uint64_t seed;     /* seeds the schedules when vibe_create gets schedules == NULL */
-  int32_t bp_engine; /* BP kernel: VIBE_ENGINE_AUTO, VIBE_ENGINE_WARP or VIBE_ENGINE_CTA (same results) */
+  int32_t bp_engine; /* BP kernel: VIBE_ENGINE_AUTO, _IMAGE or _SUMMARY (same results) */
 } vibe_params;
 
-/* BP engines. WARP: one warp per shot with the member's whole message image in shared memory; fast for
- * problems whose image is small (code capacity, phenomenological). CTA: one thread block per shot, a
- * 16-byte min/second-min/sign summary per check in shared memory and the messages in global memory;
- * for circuit-level problems whose image does not fit. AUTO takes WARP when at least 8 warps per SM
- * fit, else CTA. Both give the same bits. */
+/* BP engines; both run one warp per shot and give the same bits. IMAGE: the member's whole message
+ * image in shared memory; fast for problems whose image is small (code capacity, phenomenological).
+ * SUMMARY: an exact 16-byte smallest/second-smallest/holders/sign summary per check in shared memory
+ * and the messages in global memory; for circuit-level problems whose image does not fit. AUTO takes
+ * IMAGE when at least 8 warps per SM fit, else SUMMARY. */
 #define VIBE_ENGINE_AUTO 0
-#define VIBE_ENGINE_WARP 1
-#define VIBE_ENGINE_CTA 2
+#define VIBE_ENGINE_IMAGE 1
+#define VIBE_ENGINE_SUMMARY 2
 
 /* Per-shot record, 12 bytes. */
 typedef struct {
@@ -89,6 +89,7 @@ typedef struct {
 #define VIBE_CNT_PAIR_ITERS 3  /* BP sweeps executed, summed over (shot, member) pairs */
 #define VIBE_CNT_UNSOLVABLE 4
 #define VIBE_CNT_BAD_PROBLEM 5 /* vibe_batch_decode shots with an out-of-range problem index */
+#define VIBE_CNT_RESCANS 6     /* summary engine: check rows rescanned (a min holder's message grew) */
 #define VIBE_NUM_COUNTERS 8
 
 typedef struct vibe_handle vibe_handle;

@@ -84,9 +84,9 @@ struct Launch {
   int bp_grid() const { return warp_engine() ? std::max(1, bp_blocks_per_sm * num_sms) : 0; }
   int bpx_grid() const { return cta_engine() ? std::max(1, bpx_blocks_per_sm * num_sms) : 0; }
   int lsd_grid() const { return std::max(1, lsd_blocks_per_sm * num_sms); }
-  // per-CTA global scratch of the CTA engine, bytes; the candidate posteriors only with soft output
+  // per-warp global scratch of the summary engine, bytes; the candidate posteriors only with soft output
   long long bpx_pitch(bool soft) const {
-    return (bnd.cta_scratch + (soft ? 4LL * bnd.M * bnd.n : 0LL) + 15) & ~15LL;
+    return (bnd.x_warp_scratch + (soft ? 4LL * bnd.M * bnd.n : 0LL) + 15) & ~15LL;
   }
 };
 
@@ -95,7 +95,8 @@ struct Workspace {
   long long chunk = 0, chunk_max = 0;
   int bp_warps = 0, lsd_ctas = 0;
   long long bpx_bytes = 0;
-  unsigned int* ctrl = nullptr;   // [0] next shot (warp engine), [1] LSD count, [2] next LSD shot, [3] next shot (CTA engine)
+  unsigned int* ctrl = nullptr;   // [0] next shot (image engine), [1] LSD count, [2] next LSD shot,
+                                  // [3] next shot (summary engine)
   uint32_t* lsd_shots = nullptr;
   float* lsd_soft = nullptr;
   float* bp_scratch = nullptr;
@@ -112,7 +113,7 @@ struct Workspace {
   int ensure(const Launch& L, long long need, bool soft) {
     const long long want = std::min(need, chunk_max);
     const int warps = L.bp_grid() * vibe::kBpWarpsPerCta;
-    const long long xb = (long long)L.bpx_grid() * L.bpx_pitch(soft);
+    const long long xb = (long long)L.bpx_grid() * vibe::kBpxWarpsPerCta * L.bpx_pitch(soft);
     if (ctrl && want <= chunk && warps <= bp_warps && L.lsd_grid() <= lsd_ctas && xb <= bpx_bytes) return VIBE_OK;
     const long long c = std::max(want, chunk);
     const long long xkeep = std::max(xb, bpx_bytes);
@@ -202,7 +203,7 @@ int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, c
       VIBE_CUDA(vibe::launch_bp(a, L.msg_fp16, grid, s), "BP kernel launch");
     }
     if (L.cta_engine()) {
-      const int grid = (int)std::min<long long>(L.bpx_grid(), nb);
+      const int grid = (int)std::min<long long>(L.bpx_grid(), (nb + vibe::kBpxWarpsPerCta - 1) / vibe::kBpxWarpsPerCta);
       a.flag_bad = L.warp_engine() ? 0 : 1;
       VIBE_CUDA(vibe::launch_bpx(a, L.msg_fp16, grid, s), "BP kernel launch");
     }
@@ -240,8 +241,8 @@ int size_launch(Launch& L) {
   }
   if (L.cta_engine()) {
     if (vibe::bpx_cta_smem_bytes(L.bnd, nd) > (size_t)optin)
-      return fail(VIBE_ERR_UNSUPPORTED, "check summaries of one shot (%d bytes) do not fit in shared memory",
-                  L.bnd.cta_smem);
+      return fail(VIBE_ERR_UNSUPPORTED, "check summaries of one shot (%d bytes per warp) do not fit in shared memory",
+                  L.bnd.x_warp_smem);
     VIBE_CUDA(vibe::bpx_occupancy(L.bnd, nd, L.msg_fp16, &L.bpx_blocks_per_sm), "BP occupancy");
     if (L.bpx_blocks_per_sm < 1) return fail(VIBE_ERR_UNSUPPORTED, "the BP kernel cannot be resident");
   }
@@ -261,15 +262,15 @@ Bounds bounds_over(const Tables* ts, int count) {
     b.m = std::max(b.m, t.m); b.n = std::max(b.n, t.n); b.W = std::max(b.W, t.W); b.nw = std::max(b.nw, t.nw);
     b.kw = std::max(b.kw, t.kw); b.M = std::max(b.M, t.M); b.DP = std::max(b.DP, t.DP);
     b.lsd_order = std::max(b.lsd_order, t.lsd_order);
-    if (t.engine == VIBE_ENGINE_WARP) {
+    if (t.engine == VIBE_ENGINE_IMAGE) {
       b.engines |= 1;
       b.RP = first_warp ? t.RP : (b.RP == t.RP ? b.RP : 0);
       first_warp = false;
       b.warp_smem = std::max(b.warp_smem, t.warp_smem);
     } else {
       b.engines |= 2;
-      b.cta_smem = std::max(b.cta_smem, t.cta_smem);
-      b.cta_scratch = std::max(b.cta_scratch, t.cta_scratch);
+      b.x_warp_smem = std::max(b.x_warp_smem, t.x_warp_smem);
+      b.x_warp_scratch = std::max(b.x_warp_scratch, t.x_warp_scratch);
     }
   }
   return b;
@@ -288,6 +289,7 @@ struct vibe_handle {
   int32_t *rowptr = nullptr, *colidx = nullptr, *colptr = nullptr, *rowidx = nullptr;
   int32_t *lrowptr = nullptr, *lcolidx = nullptr, *nlev = nullptr;
   uint32_t *csc_ent = nullptr, *sched = nullptr, *lvl_off = nullptr, *perm = nullptr;
+  uint2* sched_rec = nullptr;
   float* lam = nullptr;
   void* msg_init = nullptr;
   uint32_t* row_edge = nullptr;
@@ -312,7 +314,7 @@ struct vibe_handle {
     cudaFree(tmp_counters);
     cudaFree(rowptr); cudaFree(colidx); cudaFree(colptr); cudaFree(rowidx); cudaFree(lrowptr); cudaFree(lcolidx);
     cudaFree(nlev); cudaFree(csc_ent); cudaFree(sched); cudaFree(lvl_off); cudaFree(perm); cudaFree(lam);
-    cudaFree(msg_init); cudaFree(row_edge); cudaFree(msg_csc); cudaFree(sum_init); cudaFree(d_desc);
+    cudaFree(msg_init); cudaFree(sched_rec); cudaFree(row_edge); cudaFree(msg_csc); cudaFree(sum_init); cudaFree(d_desc);
     cudaSetDevice(prev);
   }
 };
@@ -375,7 +377,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   if (p->M < 1 || p->M > K || p->M > 32) return fail(VIBE_ERR_INVALID, "M must be in 1..min(K, 32)");
   if (p->lsd_order < 0 || p->lsd_order > 10) return fail(VIBE_ERR_INVALID, "lsd_order must be in 0..10");
   if (p->msg_fp16 != 0 && p->msg_fp16 != 1) return fail(VIBE_ERR_INVALID, "msg_fp16 must be 0 or 1");
-  if (p->bp_engine < VIBE_ENGINE_AUTO || p->bp_engine > VIBE_ENGINE_CTA)
+  if (p->bp_engine < VIBE_ENGINE_AUTO || p->bp_engine > VIBE_ENGINE_SUMMARY)
     return fail(VIBE_ERR_INVALID, "bp_engine must be VIBE_ENGINE_AUTO, _WARP or _CTA");
   for (int j = 0; j < n; ++j)
     if (!(priors[j] > 0.0 && priors[j] < 0.5)) return fail(VIBE_ERR_INVALID, "prior %d = %g outside (0, 0.5)", j, priors[j]);
@@ -422,15 +424,15 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   vibe::bpx_layout(&t, p->msg_fp16);
   t.engine = p->bp_engine;
   if (t.engine == VIBE_ENGINE_AUTO) {
-    // the warp engine when its per-warp image leaves at least 8 warps per SM, else the CTA engine
+    // the image engine when its per-warp image leaves at least 8 warps per SM, else the summary engine
     int optin = 0, blocks = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    t.engine = VIBE_ENGINE_WARP;
+    t.engine = VIBE_ENGINE_IMAGE;
     const Bounds bw = bounds_over(&t, 1);
-    t.engine = VIBE_ENGINE_CTA;
+    t.engine = VIBE_ENGINE_SUMMARY;
     if (vibe::bp_cta_smem_bytes(bw, 0) <= (size_t)optin &&
         vibe::bp_occupancy(bw, 0, p->msg_fp16, &blocks) == cudaSuccess && blocks * vibe::kBpWarpsPerCta >= 8)
-      t.engine = VIBE_ENGINE_WARP;
+      t.engine = VIBE_ENGINE_IMAGE;
   }
   const int Lnnz = L->rowptr[k];
   const size_t msg_bytes = (size_t)m * t.RP * (p->msg_fp16 ? 2 : 4);
@@ -449,6 +451,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   VIBE_TRY(dalloc(&h->nlev, K), "tables");
   VIBE_TRY(dalloc(&h->csc_ent, (size_t)n * t.DP), "tables");
   VIBE_TRY(dalloc(&h->sched, (size_t)K * n), "tables");
+  VIBE_TRY(dalloc(&h->sched_rec, (size_t)K * n), "tables");
   VIBE_TRY(dalloc(&h->lvl_off, (size_t)K * (n + 1)), "tables");
   VIBE_TRY(dalloc(&h->perm, (size_t)K * n), "tables");
   VIBE_TRY(dalloc(&h->lam, n), "tables");
@@ -471,13 +474,13 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
     VIBE_TRY(vibe::seeded_schedules(h->perm, n, K, p->seed, s), "schedule kernel");
   }
   VIBE_TRY(vibe::build_tables(h->rowptr, h->colidx, m, n, K, h->perm, t.RP, t.DP, p->msg_fp16, h->lam, h->colptr,
-                              h->rowidx, h->csc_ent, h->msg_init, h->sched, h->lvl_off, h->nlev, h->row_edge,
+                              h->rowidx, h->csc_ent, h->msg_init, h->sched, h->sched_rec, h->lvl_off, h->nlev, h->row_edge,
                               h->msg_csc, h->sum_init, scratch, s),
            "graph builder");
   t.rowptr = h->rowptr; t.colidx = h->colidx; t.colptr = h->colptr; t.rowidx = h->rowidx;
   t.csc_ent = h->csc_ent; t.lam = h->lam; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
   t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
-  t.row_edge = h->row_edge; t.msg_csc = h->msg_csc; t.sum_init = h->sum_init;
+  t.row_edge = h->row_edge; t.msg_csc = h->msg_csc; t.sum_init = h->sum_init; t.sched_rec = h->sched_rec;
   VIBE_TRY(cudaMemcpyAsync(h->d_desc, &t, sizeof(Tables), cudaMemcpyHostToDevice, s), "upload");
   VIBE_TRY(cudaStreamSynchronize(s), "graph builder");
   cudaFree(scratch);

@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_b
         if (a.counters && lane == 0) atomicAdd(a.counters + VIBE_CNT_BAD_PROBLEM, 1ull);
         continue;
       }
-      if (sdem[di].engine != VIBE_ENGINE_WARP) continue;   // left to the CTA engine
+      if (sdem[di].engine != VIBE_ENGINE_IMAGE) continue;   // left to the summary engine
       decode_shot<MT, DP, RPC, true>(a, sdem[di], shot, base, acc, lpost, cand_post, lane, my_iters, my_shots,
                                      my_fail);
     } else {

@@ -1,29 +1,37 @@
 // K1' -- the BP ensemble for problems whose message image does not fit in shared memory (circuit-level
-// detector error models: rows of 100-200 entries, E up to ~4e5). Same method, same results as the warp
-// engine (vibe_bp.cu); a different layout.
+// detector error models: rows of 100-200 entries, E up to ~4e5): the summary engine. Same method, same
+// results as the image engine (vibe_bp.cu), which keeps a member's whole message image in shared
+// memory; a different layout.
 //
-// One CTA decodes one shot at a time (persistent, shots from a global counter), running the members
-// one after another with the iteration budget of the correction limit (Sec. III.D.2). A member sweeps
-// the dependency wavefronts of its schedule; the threads of the CTA take the columns of one level, then
-// the CTA synchronises.
+// Why a warp per shot. The wavefront levels of a random serial order on these graphs are short: a
+// column conflicts with every column of its ~4 checks (~600 others), so a sweep of the d=11 problem
+// has ~1000 levels of ~32 columns. One warp matches that width and synchronises with __syncwarp.
 //
-// Check-node state. For every check c the CTA keeps in shared memory a 16-byte summary of the current
+// Each warp decodes one shot at a time (persistent, shots from a global counter), running the members
+// one after another with the iteration budget of the correction limit (Sec. III.D.2).
+//
+// Check-node state. For every check c the warp keeps in shared memory a 16-byte summary of the current
 // variable-to-check messages of its row: the smallest magnitude, the second smallest (with
-// multiplicity, +inf for a one-entry row), the edge holding the smallest, and the parity of the sign
-// bits. The magnitude minimum over the row without edge e is then (e == holder ? second : smallest),
-// and the sign parity without e is parity XOR sign(m_e): exactly the minimum and sign product that
-// Algorithm 1's check update takes over N(c) \ v, with no row scan. The messages themselves (E floats or
-// halves per CTA, in CSC edge order so that a column's are contiguous) stay in global memory, where the
-// column update reads its old values and writes the new ones.
+// multiplicity, +inf for a one-entry row), the edges holding them, and the parity of the sign bits
+// (bit 31 of the second holder word). The magnitude minimum over the row without edge e is then
+// (e == first holder ? second : smallest), and the sign parity without e is parity XOR sign(m_e):
+// exactly the minimum and sign product that Algorithm 1's check update takes over N(c) \ v, with no
+// row scan. The messages themselves (E floats or halves per warp, in CSC edge order so that a column's
+// are contiguous) stay in global memory, where the column update reads its old values and writes the
+// new ones.
 //
-// Keeping the summary exact after column v replaces its message on c (old magnitude o, new x):
+// Keeping the summary exact after column v replaces its message on c with magnitude x:
 //   v holds the smallest:  x <= second -> smallest = x;  else the row is rescanned;
-//   o == second (v may hold it): x > second -> rescan; x < smallest -> v becomes the holder and the old
-//                          smallest the second; else second = x;
-//   otherwise:             x < smallest -> shift; x < second -> second = x.
+//   v holds the second:    x > second -> rescan; x < smallest -> v and the first holder swap places;
+//                          else second = x;
+//   otherwise:             x < smallest -> v holds the smallest, the old one the second;
+//                          x < second -> v holds the second.
+// Holding both holders keeps rescans rare even when many messages tie (equal priors at the start).
 // Every check is touched by one column per level, so the updates of a level never collide. Rescans
-// are queued and done after the level by one warp per check (a minimum/second-minimum reduction over
-// the row's messages), before any later level reads the summary.
+// are queued and done after the level by the whole warp (a minimum/second-minimum reduction over the
+// row's messages), before any later level reads the summary. A column's global reads (checks, old
+// messages, prior) do not depend on the level before it, so each lane fetches its next column while
+// the current level finishes.
 //
 // Arithmetic equals the oracle's bit for bit: same per-node operation order (__fadd_rn/__fmul_rn), min
 // and sign exact, FP16 storage with -0 stored as +0.
@@ -68,33 +76,57 @@ __device__ __forceinline__ bool is_finite_bits(float x) {
   return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
 }
 
-// Shared state of the CTA for its current shot.
+// Shared state of one warp for its current shot.
 struct XShared {
-  float4* summ;     // m check summaries (smallest, second, holder edge bits, sign parity bits)
+  float4* summ;     // m check summaries (smallest, second, holder edges, sign parity)
   uint8_t* s8;      // m syndrome bits
   uint8_t* par8;    // m: (H e)_c XOR s_c
   uint32_t* dec;    // nw: the member's decisions e, bit-packed
-  int32_t* rlist;   // m: checks to rescan after the current level
-  int* ctl;         // control words (see k_bpx)
+  int32_t* rlist;   // 32 * DP: checks to rescan after the current chunk of 32 columns
 };
+
+// Blocks per SM the register budget targets (16 warps per SM).
+template <typename MT>
+struct MinBlocksX { static constexpr int value = 16 / kBpxWarpsPerCta; };
+
+// What a column update reads from global memory: its checks, its current messages and its prior.
+// None of it changes before the column's own update (a column's messages are written only by that
+// column), so it can be fetched a level early.
+template <int DP>
+struct ColData {
+  uint32_t v, e0;
+  int deg;
+  float lam;
+  int c[DP];
+  float o[DP];
+};
+
+template <typename MT, int DP>
+__device__ __forceinline__ void fetch_column(uint2 rec, const Tables& t, const MT* msg, ColData<DP>& d) {
+  d.v = rec.x & 0xffffffu;
+  d.deg = (int)(rec.x >> 24);
+  d.e0 = rec.y;
+  d.lam = __ldg(t.lam + d.v);
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    d.c[k] = 0;
+    d.o[k] = 0.0f;
+    if (k < d.deg) {
+      d.c[k] = __ldg(t.rowidx + d.e0 + k);
+      d.o[k] = XMsg<MT>::value(XMsg<MT>::load(msg + d.e0 + k));
+    }
+  }
+}
 
 // Serial-V update of column v (deg checks, edges e0 .. e0 + deg - 1 in ascending check order).
 template <typename MT, int DP>
-__device__ __forceinline__ void update_column_x(uint32_t v, int deg, const Tables& t, MT* msg, const XShared& X,
+__device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tables& t, MT* msg, const XShared& X,
                                                 int* rcount, float* lpost) {
-  const uint32_t e0 = (uint32_t)__ldg(t.colptr + v);
-  int c[DP];
-  float o[DP];
-#pragma unroll
-  for (int k = 0; k < DP; ++k) {
-    c[k] = 0;
-    o[k] = 0.0f;
-    if (k < deg) {
-      c[k] = __ldg(t.rowidx + e0 + k);
-      o[k] = XMsg<MT>::value(XMsg<MT>::load(msg + e0 + k));
-    }
-  }
-  const float lamv = __ldg(t.lam + v);
+  const uint32_t v = d.v, e0 = d.e0;
+  const int deg = d.deg;
+  const int* c = d.c;
+  const float* o = d.o;
+  const float lamv = d.lam;
   const float alpha = t.alpha;
   float mcv[DP];
 #pragma unroll
@@ -104,7 +136,7 @@ __device__ __forceinline__ void update_column_x(uint32_t v, int deg, const Table
       const float4 sm = X.summ[c[k]];
       const bool holder = __float_as_uint(sm.z) == e0 + k;
       const float mn = holder ? sm.y : sm.x;
-      const uint32_t neg = (__float_as_uint(sm.w) ^ sign_bit(o[k]) ^ (uint32_t)X.s8[c[k]]) & 1u;
+      const uint32_t neg = ((__float_as_uint(sm.w) >> 31) ^ sign_bit(o[k]) ^ (uint32_t)X.s8[c[k]]) & 1u;
       const float mag = __fmul_rn(alpha, mn);
       mcv[k] = neg ? -mag : mag;
     }
@@ -124,20 +156,26 @@ __device__ __forceinline__ void update_column_x(uint32_t v, int deg, const Table
       const float x = XMsg<MT>::store(msg + e0 + k, a);
       pre = __fadd_rn(pre, mcv[k]);
       // summary maintenance
-      const float om = fabsf(o[k]), nm = fabsf(x);
+      const float nm = fabsf(x);
+      const uint32_t e = e0 + k;
       float4 s = X.summ[c[k]];   // this level's only reader and writer of check c
-      s.w = __uint_as_float(__float_as_uint(s.w) ^ sign_bit(o[k]) ^ sign_bit(x));
+      uint32_t i1 = __float_as_uint(s.z), i2 = __float_as_uint(s.w) & 0x7fffffffu;
+      const uint32_t sg = (__float_as_uint(s.w) >> 31) ^ sign_bit(o[k]) ^ sign_bit(x);
       bool rescan = false;
-      if (__float_as_uint(s.z) == e0 + k) {
+      if (e == i1) {
         if (nm <= s.y) s.x = nm;
         else rescan = true;
-      } else if (om == s.y && nm > s.y) {
-        rescan = true;
+      } else if (e == i2) {
+        if (nm > s.y) rescan = true;
+        else if (nm < s.x) { s.y = s.x; i2 = i1; s.x = nm; i1 = e; }
+        else s.y = nm;
       } else if (nm < s.x) {
-        s.y = s.x; s.x = nm; s.z = __uint_as_float(e0 + k);
+        s.y = s.x; i2 = i1; s.x = nm; i1 = e;
       } else if (nm < s.y) {
-        s.y = nm;
+        s.y = nm; i2 = e;
       }
+      s.z = __uint_as_float(i1);
+      s.w = __uint_as_float(i2 | (sg << 31));
       X.summ[c[k]] = s;
       if (rescan) X.rlist[atomicAdd(rcount, 1)] = c[k];
     }
@@ -154,64 +192,60 @@ __device__ __forceinline__ void update_column_x(uint32_t v, int deg, const Table
   if (lpost) lpost[v] = L;
 }
 
+// (value, edge) pairs ordered by value, then edge
+__device__ __forceinline__ bool before(float a, uint32_t ia, float b, uint32_t ib) {
+  return a < b || (a == b && ia < ib);
+}
+
 // Warp-cooperative rescan of check c: smallest and second smallest magnitude (with multiplicity) and
-// the edge of the smallest over the row's current messages; the sign parity is kept as it is.
+// their edges over the row's current messages; the sign parity is kept as it is.
 template <typename MT>
 __device__ __forceinline__ void rescan_row(int c, const Tables& t, const MT* msg, float4* summ, int lane) {
   float m1 = __int_as_float(0x7f800000), m2 = m1;
-  uint32_t i1 = 0xffffffffu;
+  uint32_t i1 = 0x7fffffffu, i2 = 0x7fffffffu;
   const int b = __ldg(t.rowptr + c), e = __ldg(t.rowptr + c + 1);
   for (int q = b + lane; q < e; q += 32) {
     const uint32_t ed = __ldg(t.row_edge + q);
     const float a = fabsf(XMsg<MT>::value(XMsg<MT>::load(msg + ed)));
-    if (a < m1 || (a == m1 && ed < i1)) { m2 = m1; m1 = a; i1 = ed; }
-    else if (a < m2) m2 = a;
+    if (before(a, ed, m1, i1)) { m2 = m1; i2 = i1; m1 = a; i1 = ed; }
+    else if (before(a, ed, m2, i2)) { m2 = a; i2 = ed; }
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
     const float n1 = __shfl_xor_sync(kFull, m1, off), n2 = __shfl_xor_sync(kFull, m2, off);
-    const uint32_t j1 = __shfl_xor_sync(kFull, i1, off);
-    if (n1 < m1 || (n1 == m1 && j1 < i1)) {
-      m2 = fminf(n2, m1);
-      m1 = n1;
-      i1 = j1;
-    } else {
-      m2 = fminf(m2, n1);
+    const uint32_t j1 = __shfl_xor_sync(kFull, i1, off), j2 = __shfl_xor_sync(kFull, i2, off);
+    if (before(n1, j1, m1, i1)) {   // the other's first wins; second = better of my first, its second
+      if (before(m1, i1, n2, j2)) { m2 = m1; i2 = i1; } else { m2 = n2; i2 = j2; }
+      m1 = n1; i1 = j1;
+    } else if (before(n1, j1, m2, i2)) {
+      m2 = n1; i2 = j1;
     }
   }
   if (lane == 0) {
     float4 s = summ[c];
     s.x = m1; s.y = m2; s.z = __uint_as_float(i1);
+    s.w = __uint_as_float((__float_as_uint(s.w) & 0x80000000u) | i2);
     summ[c] = s;
   }
 }
 
-// control words in static shared memory
-enum : int { C_SHOT = 0, C_RC = 1 /* 3 rescan counters */, C_SLOT = 4, C_Q = 5, C_BEST = 6, C_ITERS = 7, C_NCTL = 8 };
 
-struct XCand {
-  int t[32], i[32], slot[32];
-  float W[32];
-  float nrm;
-};
-
-// Decodes shot `shot` of problem t with the whole CTA.
+// Decodes shot `shot` of problem t with one warp. base: the warp's shared memory; gs: its global
+// scratch (messages, posterior, LLR accumulator, candidate records).
 template <typename MT, int DP>
-__device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, uint32_t shot, unsigned char* smem,
-                                              unsigned char* gs, int* ctl, XCand& cl, uint32_t& gl,
-                                              unsigned long long& my_iters, unsigned long long& my_shots,
-                                              unsigned long long& my_fail) {
-  constexpr int NT = kBpxThreads, NWARP = kBpxThreads / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, uint32_t shot, unsigned char* base,
+                                              unsigned char* gs, int lane, unsigned long long& my_iters,
+                                              unsigned long long& my_shots, unsigned long long& my_fail,
+                                              unsigned long long& my_rescans) {
   const int n = t.n, m = t.m, K = t.K, M = t.M, T = t.T, nw = t.nw, kw = t.kw;
   const int m4 = (m + 3) >> 2;
   XShared X;
-  X.summ = reinterpret_cast<float4*>(smem + t.xo_summ);
-  X.s8 = smem + t.xo_s;
-  X.par8 = smem + t.xo_par;
-  X.dec = reinterpret_cast<uint32_t*>(smem + t.xo_dec);
-  X.rlist = reinterpret_cast<int32_t*>(smem + t.xo_rl);
-  X.ctl = ctl;
+  X.summ = reinterpret_cast<float4*>(base + t.xo_summ);
+  X.s8 = base + t.xo_s;
+  X.par8 = base + t.xo_par;
+  X.dec = reinterpret_cast<uint32_t*>(base + t.xo_dec);
+  X.rlist = reinterpret_cast<int32_t*>(base + t.xo_rl);
+  volatile int* rcount = reinterpret_cast<volatile int*>(base + t.xo_rc);
   MT* msg = reinterpret_cast<MT*>(gs + t.xg_msg);
   float* lpost = reinterpret_cast<float*>(gs + t.xg_lpost);
   float* acc = reinterpret_cast<float*>(gs + t.xg_acc);
@@ -220,226 +254,238 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
 
   const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
   uint32_t any = 0;
-  for (int c = tid; c < 4 * m4; c += NT) {
+  for (int c = lane; c < 4 * m4; c += 32) {
     const uint32_t b = c < m ? (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u : 0u;
     X.s8[c] = (uint8_t)b;
     any |= b;
   }
-  const int anyS = __syncthreads_or(any != 0);
-  if (tid == 0) ++my_shots;
+  any = __any_sync(kFull, any);
+  __syncwarp();
+  ++my_shots;
   uint32_t* out_corr = a.corr + (size_t)shot * a.corr_stride;
 
-  if (!anyS && !a.want_soft) {
+  if (!any && !a.want_soft) {
     // s = 0: every member converges in iteration 1 to e = 0; member 0 is chosen
-    for (int w = tid; w < nw; w += NT) out_corr[w] = 0u;
+    for (int w = lane; w < nw; w += 32) out_corr[w] = 0u;
     if (a.logical)
-      for (int w = tid; w < kw; w += NT) a.logical[(size_t)shot * a.log_stride + w] = 0u;
-    if (warp == 0 && a.obs) {
+      for (int w = lane; w < kw; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+    if (a.obs) {
       uint32_t f = 0;
       for (int w = lane; w < kw; w += 32) f |= a.obs[(size_t)shot * a.log_stride + w];
       if (__any_sync(kFull, f) && lane == 0) ++my_fail;
     }
-    if (a.stats && tid == 0) {
+    if (a.stats && lane == 0) {
       vibe_shot_stats st;
       st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)M; st.chosen_member = 0;
       st.iters = 1; st.largest_cluster = 0; st.n_clusters = 0;
       a.stats[shot] = st;
     }
-    __syncthreads();
     return;
   }
 
-  int ncand = 0;   // the same in every thread
+  // candidate list, lane j holds entry j (sorted by iteration, then member)
+  int ncand = 0;
+  int c_t = 0, c_i = 0, c_slot = 0;
+  float c_W = 0.0f;
+
   for (int i = 0; i < K; ++i) {
-    const int budget = ncand < M ? T : cl.t[M - 1] - 1;
+    const int budget = ncand < M ? T : __shfl_sync(kFull, c_t, M - 1) - 1;
     if (budget <= 0) break;
     // member init: prior messages and summaries, decisions 0, parity = s
     {
-      for (int c = tid; c < m; c += NT) X.summ[c] = __ldg(t.sum_init + c);
+      for (int c = lane; c < m; c += 32) X.summ[c] = __ldg(t.sum_init + c);
       const uint4* src = reinterpret_cast<const uint4*>(t.msg_csc);
       uint4* dst = reinterpret_cast<uint4*>(msg);
       const int nv = (int)(((size_t)t.E * sizeof(MT) + 15) / 16);
-      for (int q = tid; q < nv; q += NT) __stcg(dst + q, __ldg(src + q));
-      for (int w = tid; w < nw; w += NT) X.dec[w] = 0u;
+      for (int q = lane; q < nv; q += 32) __stcg(dst + q, __ldg(src + q));
+      for (int w = lane; w < nw; w += 32) X.dec[w] = 0u;
       const uint32_t* s32 = reinterpret_cast<const uint32_t*>(X.s8);
       uint32_t* p32 = reinterpret_cast<uint32_t*>(X.par8);
-      for (int q = tid; q < m4; q += NT) p32[q] = s32[q];
+      for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
+      if (lane == 0) *rcount = 0;
     }
-    __syncthreads();
-    const uint32_t* sch = t.sched + (size_t)i * n;
+    __syncwarp();
+    const uint2* rec = t.sched_rec + (size_t)i * n;
     const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
     const int nl = __ldg(t.nlev + i);
     int conv = 0;
+    ColData<DP> cd;
     for (int it = 1; it <= budget; ++it) {
+      // the posterior is needed after the last possible sweep of a member that may end without
+      // converging (LLR average) and, for soft output, after every sweep
       float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
-      for (int l = 0; l < nl; ++l, ++gl) {
-        // rescan counters rotate over three words: the one zeroed here was last read two levels ago
-        if (tid == 0) ctl[C_RC + (gl + 1) % 3] = 0;
-        int* rc = ctl + C_RC + gl % 3;
-        const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
-        for (uint32_t idx = b + tid; idx < e; idx += NT) {
-          const uint32_t ent = __ldg(sch + idx);
-          update_column_x<MT, DP>(ent & 0xffffffu, (int)(ent >> 24), t, msg, X, rc, lp);
+      // the sweep in chunks of up to 32 columns of one level, one column per lane; rescans after each
+      // chunk (later chunks of the same level touch other checks)
+      bool have = false;
+      int l = 0;
+      uint32_t cs = __ldg(lo), e = __ldg(lo + 1);
+      while (l < nl) {
+        if (cs + lane < e) {
+          if (!have) fetch_column<MT, DP>(__ldg(rec + cs + lane), t, msg, cd);
+          update_column_x<MT, DP>(cd, t, msg, X, const_cast<int*>(rcount), lp);
         }
-        __syncthreads();
-        const int nres = *rc;
+        // fetch this lane's column of the next chunk
+        uint32_t ncs = cs + 32, ne = e;
+        int nlv = l;
+        if (ncs >= e) {
+          nlv = l + 1;
+          ncs = e;
+          ne = nlv < nl ? __ldg(lo + nlv + 1) : e;
+        }
+        have = false;
+        if (nlv < nl && ncs + lane < ne) { fetch_column<MT, DP>(__ldg(rec + ncs + lane), t, msg, cd); have = true; }
+        __syncwarp();
+        const int nres = *rcount;
         if (nres > 0) {
-          for (int q = warp; q < nres; q += NWARP) rescan_row<MT>(X.rlist[q], t, msg, X.summ, lane);
-          __syncthreads();
+          for (int q = 0; q < nres; ++q) rescan_row<MT>(X.rlist[q], t, msg, X.summ, lane);
+          my_rescans += (unsigned long long)nres;
+          __syncwarp();
+          if (lane == 0) *rcount = 0;
+          __syncwarp();
         }
+        cs = ncs; e = ne; l = nlv;
       }
-      if (tid == 0) ++my_iters;
+      ++my_iters;
       uint32_t bad = 0;
       const uint32_t* p32 = reinterpret_cast<const uint32_t*>(X.par8);
-      for (int q = tid; q < m4; q += NT) bad |= p32[q];
-      if (!__syncthreads_or(bad != 0)) { conv = it; break; }
+      for (int q = lane; q < m4; q += 32) bad |= p32[q];
+      if (!__any_sync(kFull, bad)) { conv = it; break; }
     }
     if (conv) {
-      if (tid == 0) {
-        // W(e) = sum of lambda_j over e_j = 1, ascending j
-        float W = 0.0f;
-        for (int w = 0; w < nw; ++w) {
-          uint32_t x = X.dec[w];
-          while (x) {
-            const int bpos = __ffs(x) - 1;
-            W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
-            x &= x - 1;
-          }
+      // insert (conv, i); i exceeds every member already listed, so it goes after equal iterations
+      const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
+      const int slot = ncand < M ? ncand : __shfl_sync(kFull, c_slot, M - 1);
+      uint32_t* bits = cand + (size_t)slot * nw;
+      for (int w = lane; w < nw; w += 32) bits[w] = X.dec[w];
+      // W(e) = sum of lambda_j over e_j = 1, ascending j (every lane folds the same sequence)
+      float W = 0.0f;
+      for (int w = 0; w < nw; ++w) {
+        uint32_t x = X.dec[w];
+        while (x) {
+          const int bpos = __ffs(x) - 1;
+          W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
+          x &= x - 1;
         }
-        // insert (conv, i) after the entries with t <= conv; a full list drops its last entry
-        int p = 0;
-        while (p < ncand && cl.t[p] <= conv) ++p;
-        const int slot = ncand < M ? ncand : cl.slot[M - 1];
-        const int last = min(ncand, M - 1);
-        for (int j = last; j > p; --j) {
-          cl.t[j] = cl.t[j - 1]; cl.i[j] = cl.i[j - 1]; cl.slot[j] = cl.slot[j - 1]; cl.W[j] = cl.W[j - 1];
-        }
-        if (p <= last) { cl.t[p] = conv; cl.i[p] = i; cl.slot[p] = slot; cl.W[p] = W; }
-        ctl[C_SLOT] = slot;
       }
-      __syncthreads();
-      const int slot = ctl[C_SLOT];
-      for (int w = tid; w < nw; w += NT) cand[(size_t)slot * nw + w] = X.dec[w];
-      if (a.want_soft)
-        for (int v = tid; v < n; v += NT) cpost[(size_t)slot * n + v] = lpost[v];
+      if (a.want_soft) {
+        float* dst = cpost + (size_t)slot * n;
+        for (int v = lane; v < n; v += 32) dst[v] = lpost[v];
+      }
+      const float uW = __shfl_up_sync(kFull, c_W, 1);
+      const int ut = __shfl_up_sync(kFull, c_t, 1), ui = __shfl_up_sync(kFull, c_i, 1);
+      const int us = __shfl_up_sync(kFull, c_slot, 1);
+      const int last = min(ncand, M - 1);
+      if (lane > p && lane <= last) { c_W = uW; c_t = ut; c_i = ui; c_slot = us; }
+      if (lane == p) { c_W = W; c_t = conv; c_i = i; c_slot = slot; }
       ncand = min(ncand + 1, M);
     } else if (ncand == 0) {
-      // not converged after T sweeps and no candidate yet: add LLR^i / ||LLR^i|| (finite entries);
-      // the norm is the canonical 32-partial sum with an XOR-butterfly combine
-      if (warp == 0) {
-        float part = 0.0f;
-        for (int v = lane; v < n; v += 32) {
-          const float x = lpost[v];
-          part = __fadd_rn(part, is_finite_bits(x) ? __fmul_rn(x, x) : 0.0f);
-        }
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) part = __fadd_rn(part, __shfl_xor_sync(kFull, part, off));
-        if (lane == 0) cl.nrm = __fsqrt_rn(part);
+      // not converged after T sweeps and no candidate yet: add LLR^i / ||LLR^i|| (finite entries)
+      float part = 0.0f;
+      for (int v = lane; v < n; v += 32) {
+        const float x = lpost[v];
+        part = __fadd_rn(part, is_finite_bits(x) ? __fmul_rn(x, x) : 0.0f);
       }
-      __syncthreads();
-      const float nrm = cl.nrm;
-      for (int v = tid; v < n; v += NT) {
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) part = __fadd_rn(part, __shfl_xor_sync(kFull, part, off));
+      const float nrm = __fsqrt_rn(part);
+      for (int v = lane; v < n; v += 32) {
         const float x = lpost[v];
         const float term = is_finite_bits(x) ? (nrm == 0.0f ? 0.0f : __fdiv_rn(x, nrm)) : x;
         acc[v] = __fadd_rn(i == 0 ? 0.0f : acc[v], term);
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 
   if (ncand > 0) {
-    if (tid == 0) {
-      int best = 0;   // first minimum of W over the list
-      for (int j = 1; j < ncand; ++j)
-        if (cl.W[j] < cl.W[best]) best = j;
-      ctl[C_BEST] = best;
-      ctl[C_ITERS] = ncand == M ? cl.t[M - 1] : T;
+    // first minimum of W over the candidate list
+    float bw = lane < ncand ? c_W : __int_as_float(0x7f800000);
+    int bi = lane;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const float ow = __shfl_xor_sync(kFull, bw, off);
+      const int oi = __shfl_xor_sync(kFull, bi, off);
+      if (ow < bw || (ow == bw && oi < bi)) { bw = ow; bi = oi; }
     }
-    __syncthreads();
-    const int best = ctl[C_BEST];
-    const int slot = cl.slot[best];
+    const int slot = __shfl_sync(kFull, c_slot, bi);
+    const int member = __shfl_sync(kFull, c_i, bi);
+    const int iters = ncand == M ? __shfl_sync(kFull, c_t, M - 1) : T;
     const uint32_t* bits = cand + (size_t)slot * nw;
-    for (int w = tid; w < nw; w += NT) out_corr[w] = bits[w];
+    for (int w = lane; w < nw; w += 32) out_corr[w] = bits[w];
     if (a.want_soft) {
       const float* src = cpost + (size_t)slot * n;
       float* dst = a.soft + (size_t)shot * a.soft_stride;
-      for (int v = tid; v < n; v += NT) dst[v] = src[v];
+      for (int v = lane; v < n; v += 32) dst[v] = src[v];
     }
-    if (warp == 0) {
-      uint32_t fail = 0;
-      for (int rb = 0; rb < kw; ++rb) {
-        const int r = 32 * rb + lane;
-        uint32_t par = 0;
-        if (r < t.k)
-          for (int e = __ldg(t.lrowptr + r); e < __ldg(t.lrowptr + r + 1); ++e) {
-            const int j = __ldg(t.lcolidx + e);
-            par ^= (bits[j >> 5] >> (j & 31)) & 1u;
-          }
-        const uint32_t word = __ballot_sync(kFull, par != 0);
-        if (a.logical && lane == 0) a.logical[(size_t)shot * a.log_stride + rb] = word;
-        if (a.obs) fail |= word ^ a.obs[(size_t)shot * a.log_stride + rb];
-      }
-      if (fail && lane == 0) ++my_fail;
-      if (a.stats && lane == 0) {
-        vibe_shot_stats st;
-        st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)ncand;
-        st.chosen_member = (uint8_t)cl.i[best]; st.iters = (uint16_t)ctl[C_ITERS];
-        st.largest_cluster = 0; st.n_clusters = 0;
-        a.stats[shot] = st;
-      }
+    uint32_t fail = 0;
+    for (int rb = 0; rb < kw; ++rb) {
+      const int r = 32 * rb + lane;
+      uint32_t par = 0;
+      if (r < t.k)
+        for (int e = __ldg(t.lrowptr + r); e < __ldg(t.lrowptr + r + 1); ++e) {
+          const int j = __ldg(t.lcolidx + e);
+          par ^= (bits[j >> 5] >> (j & 31)) & 1u;
+        }
+      const uint32_t word = __ballot_sync(kFull, par != 0);
+      if (a.logical && lane == 0) a.logical[(size_t)shot * a.log_stride + rb] = word;
+      if (a.obs) fail |= word ^ a.obs[(size_t)shot * a.log_stride + rb];
+    }
+    if (fail && lane == 0) ++my_fail;
+    if (a.stats && lane == 0) {
+      vibe_shot_stats st;
+      st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)ncand;
+      st.chosen_member = (uint8_t)member; st.iters = (uint16_t)iters; st.largest_cluster = 0; st.n_clusters = 0;
+      a.stats[shot] = st;
     }
   } else {
     // hand the averaged soft vector to the LSD kernel
-    if (tid == 0) {
-      const unsigned int q = atomicAdd(a.lsd_count, 1u);
-      a.lsd_shots[q] = shot;
-      ctl[C_Q] = (int)q;
-    }
-    __syncthreads();
-    float* dst = a.lsd_soft + (size_t)(unsigned)ctl[C_Q] * a.bnd.n;
+    uint32_t q = 0;
+    if (lane == 0) q = atomicAdd(a.lsd_count, 1u);
+    q = __shfl_sync(kFull, q, 0);
+    if (lane == 0) a.lsd_shots[q] = shot;
+    float* dst = a.lsd_soft + (size_t)q * a.bnd.n;
     const float kf = (float)K;
-    for (int v = tid; v < n; v += NT) dst[v] = __fdiv_rn(acc[v], kf);
+    for (int v = lane; v < n; v += 32) dst[v] = __fdiv_rn(acc[v], kf);
   }
-  __syncthreads();
+  __syncwarp();
 }
 
 // MIXED: shots name their problems (dem_of_shot); the descriptors are copied to shared memory after
-// the CTA's layout and shots of warp-engine problems are left to that kernel. Otherwise every shot
+// the warps' regions and shots of image-engine problems are left to that kernel. Otherwise every shot
 // decodes a.one from the parameter space.
 template <typename MT, int DP, bool MIXED>
-__global__ void __launch_bounds__(kBpxThreads, 2) k_bpx(const BpArgs a) {
+__global__ void __launch_bounds__(kBpxWarpsPerCta * 32, MinBlocksX<MT>::value) k_bpx(const BpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int ctl[C_NCTL];
-  __shared__ XCand cl;
-  const int tid = threadIdx.x;
-  Tables* sdem = reinterpret_cast<Tables*>(smem + a.bnd.cta_smem);
+  const int lane = threadIdx.x & 31;
+  const int wcta = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kBpxWarpsPerCta + wcta;
+  Tables* sdem = reinterpret_cast<Tables*>(smem + (size_t)kBpxWarpsPerCta * a.bnd.x_warp_smem);
   if (MIXED) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(a.dems);
     uint32_t* dst = reinterpret_cast<uint32_t*>(sdem);
     const int words = a.ndem * (int)(sizeof(Tables) / 4);
-    for (int q = tid; q < words; q += kBpxThreads) dst[q] = __ldg(src + q);
+    for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = __ldg(src + q);
+    __syncthreads();
   }
-  if (tid < C_NCTL) ctl[tid] = 0;
-  unsigned char* gs = a.xscratch + (long long)blockIdx.x * a.xscratch_pitch;
-  unsigned long long my_iters = 0, my_shots = 0, my_fail = 0;
-  uint32_t gl = 0;   // levels swept by this CTA (rotates the rescan counters)
+  unsigned char* base = smem + (size_t)wcta * a.bnd.x_warp_smem;
+  unsigned char* gs = a.xscratch + gw * a.xscratch_pitch;
+  unsigned long long my_iters = 0, my_shots = 0, my_fail = 0, my_rescans = 0;
 
   for (;;) {
-    __syncthreads();
-    if (tid == 0) ctl[C_SHOT] = (int)atomicAdd(a.next_shot_x, 1u);
-    __syncthreads();
-    const uint32_t shot = (uint32_t)ctl[C_SHOT];
+    uint32_t shot = 0;
+    if (lane == 0) shot = atomicAdd(a.next_shot_x, 1u);
+    shot = __shfl_sync(kFull, shot, 0);
     if (shot >= a.nshots) break;
     if (MIXED) {
       const int di = __ldg(a.dem_of_shot + shot);
       if ((unsigned)di >= (unsigned)a.ndem) {
         if (!a.flag_bad) continue;
-        for (int w = tid; w < a.corr_stride; w += kBpxThreads) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
+        for (int w = lane; w < a.corr_stride; w += 32) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
         if (a.logical)
-          for (int w = tid; w < a.log_stride; w += kBpxThreads) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+          for (int w = lane; w < a.log_stride; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
         if (a.soft)
-          for (int j = tid; j < a.soft_stride; j += kBpxThreads) a.soft[(size_t)shot * a.soft_stride + j] = 0.0f;
-        if (tid == 0) {
+          for (int j = lane; j < a.soft_stride; j += 32) a.soft[(size_t)shot * a.soft_stride + j] = 0.0f;
+        if (lane == 0) {
           if (a.stats) {
             vibe_shot_stats st;
             st.status = VIBE_STATUS_BAD_PROBLEM; st.lsd_invoked = 0; st.n_converged = 0; st.chosen_member = 0;
@@ -450,17 +496,18 @@ __global__ void __launch_bounds__(kBpxThreads, 2) k_bpx(const BpArgs a) {
         }
         continue;
       }
-      if (sdem[di].engine != VIBE_ENGINE_CTA) continue;
-      decode_shot_x<MT, DP>(a, sdem[di], shot, smem, gs, ctl, cl, gl, my_iters, my_shots, my_fail);
+      if (sdem[di].engine != VIBE_ENGINE_SUMMARY) continue;   // left to the image engine
+      decode_shot_x<MT, DP>(a, sdem[di], shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
     } else {
-      decode_shot_x<MT, DP>(a, a.one, shot, smem, gs, ctl, cl, gl, my_iters, my_shots, my_fail);
+      decode_shot_x<MT, DP>(a, a.one, shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
     }
   }
-  if (tid == 0 && a.counters) {
+  if (lane == 0 && a.counters) {
     atomicAdd(a.counters + VIBE_CNT_SHOTS, my_shots);
     atomicAdd(a.counters + VIBE_CNT_PAIR_ITERS, my_iters);
+    if (my_fail) atomicAdd(a.counters + VIBE_CNT_FAILURES, my_fail);
+    if (my_rescans) atomicAdd(a.counters + VIBE_CNT_RESCANS, my_rescans);
   }
-  if ((tid & 31) == 0 && a.counters && my_fail) atomicAdd(a.counters + VIBE_CNT_FAILURES, my_fail);
 }
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -469,7 +516,7 @@ template <typename MT, int DP, bool MIXED>
 cudaError_t launch_x(const BpArgs& a, int grid, size_t smem, cudaStream_t s) {
   cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
   if (err != cudaSuccess) return err;
-  k_bpx<MT, DP, MIXED><<<grid, kBpxThreads, smem, s>>>(a);
+  k_bpx<MT, DP, MIXED><<<grid, kBpxWarpsPerCta * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -477,7 +524,7 @@ template <typename MT, int DP, bool MIXED>
 cudaError_t occupancy_x(size_t smem, int* out) {
   cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bpx<MT, DP, MIXED>, kBpxThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bpx<MT, DP, MIXED>, kBpxWarpsPerCta * 32, smem);
 }
 
 template <typename Fn>
@@ -519,19 +566,20 @@ void bpx_layout(Tables* t, int msg_fp16) {
   t->xo_s = (int)o;     o = a16(o + m4);
   t->xo_par = (int)o;   o = a16(o + m4);
   t->xo_dec = (int)o;   o = a16(o + 4 * (size_t)t->nw);
-  t->xo_rl = (int)o;    o = a16(o + 4 * (size_t)t->m);
-  t->cta_smem = (int)o;
+  t->xo_rl = (int)o;    o = a16(o + 4 * 32 * (size_t)t->DP);
+  t->xo_rc = (int)o;    o = a16(o + 4);
+  t->x_warp_smem = (int)o;
   long long g = 0;
   t->xg_msg = g;   g += (long long)a16((size_t)t->E * (msg_fp16 ? 2 : 4));
   t->xg_lpost = g; g += (long long)a16(4 * (size_t)t->n);
   t->xg_acc = g;   g += (long long)a16(4 * (size_t)t->n);
   t->xg_cand = g;  g += (long long)a16(4 * (size_t)t->M * t->nw);
   t->xg_cpost = g;
-  t->cta_scratch = g;
+  t->x_warp_scratch = g;
 }
 
 size_t bpx_cta_smem_bytes(const Bounds& b, int ndem) {
-  return (size_t)b.cta_smem + a16((size_t)ndem * sizeof(Tables));
+  return (size_t)kBpxWarpsPerCta * b.x_warp_smem + a16((size_t)ndem * sizeof(Tables));
 }
 
 cudaError_t launch_bpx(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s) {

@@ -108,7 +108,7 @@ __device__ __forceinline__ float msg_magnitude<float>(float x) { return fabsf(x)
 template <>
 __device__ __forceinline__ float msg_magnitude<__half>(__half x) { return fabsf(__half2float(x)); }
 
-// CTA engine: prior messages in CSC edge order.
+// Summary engine: prior messages in CSC edge order.
 template <typename MT>
 __global__ void k_msg_csc(const int32_t* __restrict__ colptr, int n, const float* __restrict__ lam,
                           MT* __restrict__ out) {
@@ -118,23 +118,24 @@ __global__ void k_msg_csc(const int32_t* __restrict__ colptr, int n, const float
   }
 }
 
-// CTA engine: per check, the smallest and second smallest prior-message magnitude over its row (with
-// multiplicity), the CSC edge id of the first smallest in row order, and the parity of the signs.
+// Summary engine: per check, the smallest and second smallest prior-message magnitude over its row (with
+// multiplicity), the CSC edge ids holding them (first ones in row order; 0x7fffffff for none), and the
+// parity of the signs in bit 31 of the second holder word.
 template <typename MT>
 __global__ void k_sum_init(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int m,
                            const uint32_t* __restrict__ row_edge, const float* __restrict__ lam,
                            float4* __restrict__ out) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
     float m1 = __int_as_float(0x7f800000), m2 = m1;
-    uint32_t i1 = 0xffffffffu, sg = 0u;
+    uint32_t i1 = 0x7fffffffu, i2 = 0x7fffffffu, sg = 0u;
     for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
       const MT x = to_msg<MT>(lam[colidx[q]]);
       const float a = msg_magnitude<MT>(x);
       sg ^= (float)x < 0.0f ? 1u : 0u;
-      if (a < m1) { m2 = m1; m1 = a; i1 = row_edge[q]; }
-      else if (a < m2) m2 = a;
+      if (a < m1) { m2 = m1; i2 = i1; m1 = a; i1 = row_edge[q]; }
+      else if (a < m2) { m2 = a; i2 = row_edge[q]; }
     }
-    out[c] = make_float4(m1, m2, __uint_as_float(i1), __uint_as_float(sg));
+    out[c] = make_float4(m1, m2, __uint_as_float(i1), __uint_as_float(i2 | (sg << 31)));
   }
 }
 
@@ -185,6 +186,17 @@ __global__ void k_levels(const uint32_t* __restrict__ perm, int n, int m, int K,
   nlev[i] = nl;
 }
 
+// Summary engine: each schedule entry with its column's first CSC edge, so that a column update needs
+// one dependent load less.
+__global__ void k_sched_rec(const uint32_t* __restrict__ sched, long long total, const int32_t* __restrict__ colptr,
+                            uint2* __restrict__ rec) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const uint32_t ent = sched[q];
+    rec[q] = make_uint2(ent, (uint32_t)colptr[ent & 0xffffffu]);
+  }
+}
+
 __device__ __forceinline__ uint64_t splitmix64_next(uint64_t& st) {
   uint64_t z = (st += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -221,7 +233,7 @@ cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cuda
 
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K, const uint32_t* d_perm,
                          int RP, int DP, int msg_fp16, const float* d_lam, int32_t* d_colptr, int32_t* d_rowidx,
-                         uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint32_t* d_lvl_off,
+                         uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint2* d_sched_rec, uint32_t* d_lvl_off,
                          int32_t* d_nlev, uint32_t* d_row_edge, void* d_msg_csc, float4* d_sum_init,
                          int32_t* d_scratch, cudaStream_t s) {
   // scratch layout: cnt[n] | fill[n] | packed[E] ; later reused by k_levels (K*(m+3n+1))
@@ -252,6 +264,7 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
     k_msg_init<float><<<grid_for((long long)m * RP, 256), 256, 0, s>>>(d_rowptr, d_colidx, m, RP, d_lam,
                                                                       static_cast<float*>(d_msg_init));
   k_levels<<<(K + 31) / 32, 32, 0, s>>>(d_perm, n, m, K, d_colptr, d_rowidx, d_sched, d_lvl_off, d_nlev, d_scratch);
+  k_sched_rec<<<grid_for((long long)K * n, 256), 256, 0, s>>>(d_sched, (long long)K * n, d_colptr, d_sched_rec);
   return cudaGetLastError();
 }
 

@@ -11,8 +11,8 @@
 
 namespace vibe {
 
-constexpr int kBpWarpsPerCta = 2;   // warp engine: warps per CTA, one shot per warp
-constexpr int kBpxThreads = 256;    // CTA engine: threads per CTA, one shot per CTA
+constexpr int kBpWarpsPerCta = 2;   // image engine: warps per CTA, one shot per warp
+constexpr int kBpxWarpsPerCta = 2;  // summary engine: warps per CTA, one shot per warp
 constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
 constexpr int kMaxRowDeg = 255;     // position of an edge inside its check row fits in 8 bits
 constexpr int kMaxColDeg = 32;
@@ -46,12 +46,12 @@ struct Tables {
   int W;         // words of a bit vector over the checks: ceil(m/32)
   int T, M, lsd_order;
   float alpha;
-  int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // warp engine: per-warp shared memory, bytes
-  int engine;    // VIBE_ENGINE_WARP or VIBE_ENGINE_CTA
-  // CTA engine: shared memory of one CTA (bytes) and global scratch of one CTA (bytes, 16-aligned parts)
-  int xo_summ, xo_s, xo_par, xo_dec, xo_rl, cta_smem;
-  // xg_cpost = cta_scratch: the M*n candidate posteriors (soft output only) follow the fixed part
-  long long xg_msg, xg_lpost, xg_acc, xg_cand, xg_cpost, cta_scratch;
+  int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // image engine: per-warp shared memory, bytes
+  int engine;    // VIBE_ENGINE_IMAGE or VIBE_ENGINE_SUMMARY
+  // summary engine: shared memory of one warp (bytes) and global scratch of one warp (bytes, 16-aligned parts)
+  int xo_summ, xo_s, xo_par, xo_dec, xo_rl, xo_rc, x_warp_smem;
+  // xg_cpost = x_warp_scratch: the M*n candidate posteriors (soft output only) follow the fixed part
+  long long xg_msg, xg_lpost, xg_acc, xg_cand, xg_cpost, x_warp_scratch;
   const int32_t* rowptr;   // H CSR
   const int32_t* colidx;
   const int32_t* colptr;   // H CSC, checks ascending in each column
@@ -60,11 +60,12 @@ struct Tables {
   const float* lam;        // n prior LLRs
   const void* msg_init;    // m*RP messages (float or half): lambda of the edge's column, +inf padding
   const uint32_t* sched;   // K*n: column | (degree << 24), grouped by wavefront level
+  const uint2* sched_rec;  // K*n: (sched entry, first CSC edge of the column), same order
   const uint32_t* lvl_off; // K*(n+1): level offsets into sched
   const int32_t* nlev;     // K level counts
   const int32_t* lrowptr;  // L CSR
   const int32_t* lcolidx;
-  // CTA engine
+  // summary engine
   const uint32_t* row_edge; // E: for each CSR entry of H, the CSC edge id of the same (check, column)
   const void* msg_csc;      // E messages (float or half) in CSC edge order: lambda of the edge's column
   const float4* sum_init;   // m: (min1, min2, edge id of min1, sign parity) of the prior messages per row
@@ -76,9 +77,9 @@ struct Bounds {
   int RP;          // common row pitch if all problems share it, else 0
   int warp_smem;   // largest BP per-warp layout
   int lsd_order;   // largest LSD order
-  int cta_smem;    // largest CTA-engine shared-memory layout (0 if no problem uses that engine)
-  long long cta_scratch;   // largest CTA-engine global scratch per CTA, bytes
-  int engines;     // bit 0: some problem uses the warp engine, bit 1: the CTA engine
+  int x_warp_smem;    // largest summary-engine shared memory per warp (0 if no problem uses that engine)
+  long long x_warp_scratch;   // largest summary-engine global scratch per warp, bytes
+  int engines;     // bit 0: some problem uses the image engine, bit 1: the summary engine
 };
 
 struct BpArgs {
@@ -107,14 +108,14 @@ struct BpArgs {
   unsigned int* lsd_count;
   uint32_t* lsd_shots;
   float* lsd_soft;             // pitch bnd.n floats per queued shot
-  // warp engine, per-warp global scratch: n floats (LLR accumulator), n floats (posterior), M*n floats
+  // image engine, per-warp global scratch: n floats (LLR accumulator), n floats (posterior), M*n floats
   // (candidate posteriors, only with want_soft); pitch in floats
   float* scratch;
   long long scratch_pitch;
-  // CTA engine, per-CTA global scratch (Tables::xg_* offsets); pitch in bytes
+  // summary engine, per-warp global scratch (Tables::xg_* offsets); pitch in bytes
   unsigned char* xscratch;
   long long xscratch_pitch;
-  unsigned int* next_shot_x;   // the CTA engine's own shot counter
+  unsigned int* next_shot_x;   // the summary engine's own shot counter
 };
 
 struct LsdArgs {
@@ -176,7 +177,7 @@ int set_error(int code, const char* msg);
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K,
                          const uint32_t* d_perm, int RP, int DP, int msg_fp16, const float* d_lam,
                          int32_t* d_colptr, int32_t* d_rowidx, uint32_t* d_csc_ent, void* d_msg_init,
-                         uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev, uint32_t* d_row_edge,
+                         uint32_t* d_sched, uint2* d_sched_rec, uint32_t* d_lvl_off, int32_t* d_nlev, uint32_t* d_row_edge,
                          void* d_msg_csc, float4* d_sum_init, int32_t* d_scratch, cudaStream_t s);
 cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
 
@@ -187,7 +188,7 @@ size_t bp_cta_smem_bytes(const Bounds& b, int ndem);
 cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
 cudaError_t bp_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_per_sm);
 
-// K1': CTA-engine BP + ensemble selection (vibe_bpx.cu)
+// K1': summary-engine BP + ensemble selection (vibe_bpx.cu)
 void bpx_layout(Tables* t, int msg_fp16);   // fills t's xo_*/xg_* fields
 size_t bpx_cta_smem_bytes(const Bounds& b, int ndem);
 cudaError_t launch_bpx(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);

@@ -56,7 +56,7 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   if (B == 0) return VIBE_OK;
   if (!d_syndromes || !d_corrections) return vibe::set_error(VIBE_ERR_INVALID, "NULL syndromes or corrections");
   const vibe::Tables& t = v.t;
-  if (t.engine != VIBE_ENGINE_WARP)
+  if (t.engine != VIBE_ENGINE_IMAGE)
     return vibe::set_error(VIBE_ERR_UNSUPPORTED, "the static workspace serves warp-engine handles only");
   // Fixed part: counters, two n-float rows per BP warp (LLR accumulator, posterior), one row set per
   // LSD CTA. The LSD CTAs are capped at one per SM so the fixed part stays small; the rest holds the

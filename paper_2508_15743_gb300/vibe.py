@@ -20,7 +20,7 @@ VIBE_ERR_NOMEM = -2
 VIBE_ERR_CUDA = -3
 VIBE_ERR_UNSUPPORTED = -4
 VIBE_NUM_COUNTERS = 8
-CNT_SHOTS, CNT_FAILURES, CNT_LSD, CNT_PAIR_ITERS, CNT_UNSOLVABLE, CNT_BAD_PROBLEM = 0, 1, 2, 3, 4, 5
+CNT_SHOTS, CNT_FAILURES, CNT_LSD, CNT_PAIR_ITERS, CNT_UNSOLVABLE, CNT_BAD_PROBLEM, CNT_RESCANS = 0, 1, 2, 3, 4, 5, 6
 VIBE_STATUS_OK, VIBE_STATUS_UNSOLVABLE, VIBE_STATUS_BAD_PROBLEM, VIBE_STATUS_CLUSTER_LIMIT = 0, 1, 2, 3
 
 STATS_DTYPE = np.dtype([("status", "u1"), ("lsd_invoked", "u1"), ("n_converged", "u1"),
@@ -46,7 +46,7 @@ class vibe_params(ctypes.Structure):
                 ("bp_engine", ctypes.c_int32)]
 
 
-ENGINE_AUTO, ENGINE_WARP, ENGINE_CTA = 0, 1, 2
+ENGINE_AUTO, ENGINE_IMAGE, ENGINE_SUMMARY = 0, 1, 2
 
 
 def _load():

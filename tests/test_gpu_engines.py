@@ -1,9 +1,9 @@
-"""GPU parity of the CTA engine (check summaries in shared memory, messages in global memory).
+"""GPU parity of the summary engine (check summaries in shared memory, messages in global memory).
 
-The CTA engine decodes the same problems as the warp engine with a different data layout; both must
-match the oracle bit for bit (corrections, logical flips, per-shot records, FP32 posteriors). It is
-the only engine for circuit-level detector error models of distance 7 and more, whose rows of 100-200
-entries do not fit the warp engine's shared-memory image.
+The summary engine decodes the same problems as the image engine with a different data layout; both
+must match the oracle bit for bit (corrections, logical flips, per-shot records, FP32 posteriors). It
+is the only engine for circuit-level detector error models of distance 7 and more, whose rows of
+100-200 entries do not fit the image engine's shared-memory message image.
 """
 import numpy as np
 import pytest
@@ -57,15 +57,15 @@ def assert_same(g, r, soft=True, what=""):
 
 
 @pytest.mark.parametrize("fp16", [False, True])
-def test_cta_engine_pheno_d9_matches_oracle(V, fp16):
+def test_summary_engine_pheno_d9_matches_oracle(V, fp16):
     w = D.WORKLOADS["cc666_d9_pheno"]
     dm = D.build_workload("cc666_d9_pheno")
     syn, obs = D.sample(dm, 1200, 21)
     perms = D.schedules(dm.n, w["K"], w["seed"])
-    g = run(V, dm, perms, syn, w["T"], w["M"], V.ENGINE_CTA, fp16=fp16, obs=obs)
+    g = run(V, dm, perms, syn, w["T"], w["M"], V.ENGINE_SUMMARY, fp16=fp16, obs=obs)
     mode = oracle.FP16MSG if fp16 else oracle.FP32
     r = oracle.decode(dm, perms, syn, w["T"], w["alpha"], w["M"], mode=mode, nthreads=8)
-    assert_same(g, r, what=f"CTA engine, d9 pheno, fp16={fp16}")
+    assert_same(g, r, what=f"summary engine, d9 pheno, fp16={fp16}")
     assert r["stats"]["lsd_invoked"].sum() > 50
     fails = (r["logical"] != obs).any(axis=1).sum()
     assert g["counters"][V.CNT_SHOTS] == len(syn) and g["counters"][V.CNT_FAILURES] == fails
@@ -75,39 +75,39 @@ def test_engines_agree_on_circuit_d5(V):
     dm = C.circuit_dem(5, 5, 0.003, noise="si1000", basis="X")
     syn, _ = D.sample(dm, 600, 8)
     perms = D.schedules(dm.n, 8, 8)
-    a = run(V, dm, perms, syn, 20, 3, V.ENGINE_WARP)
-    b = run(V, dm, perms, syn, 20, 3, V.ENGINE_CTA)
-    assert_same(a, b, what="warp vs CTA engine")
+    a = run(V, dm, perms, syn, 20, 3, V.ENGINE_IMAGE)
+    b = run(V, dm, perms, syn, 20, 3, V.ENGINE_SUMMARY)
+    assert_same(a, b, what="image vs summary engine")
 
 
 @pytest.mark.parametrize("d,basis,noise,fp16", [(3, "X", "si1000", False), (5, "Z", "uniform", False),
                                                 (7, "X", "si1000", False), (7, "X", "si1000", True)])
-def test_cta_engine_circuit_matches_oracle(V, d, basis, noise, fp16):
+def test_summary_engine_circuit_matches_oracle(V, d, basis, noise, fp16):
     dm = C.circuit_dem(d, d, 0.004, noise=noise, basis=basis)
     syn, obs = D.sample(dm, 300, 30 + d)
     K, T, M = 6, 12, 3
     perms = D.schedules(dm.n, K, d)
-    g = run(V, dm, perms, syn, T, M, V.ENGINE_CTA, fp16=fp16, obs=obs)
+    g = run(V, dm, perms, syn, T, M, V.ENGINE_SUMMARY, fp16=fp16, obs=obs)
     mode = oracle.FP16MSG if fp16 else oracle.FP32
     r = oracle.decode(dm, perms, syn, T, 0.625, M, mode=mode, nthreads=16)
     assert_same(g, r, what=f"circuit d={d} {basis} {noise} fp16={fp16}")
     assert not np.any(g["stats"]["status"] == V.VIBE_STATUS_CLUSTER_LIMIT)
 
 
-def test_auto_engine_picks_cta_for_large_circuit(V):
+def test_auto_engine_picks_summary_for_large_circuit(V):
     dm = C.circuit_dem(7, 7, 0.001, noise="si1000", basis="X")
     dec = V.Decoder(dm, 4, D.schedules(dm.n, 4, 1), T=5, M=2)
-    # decoding works and gives the same as an explicit CTA-engine handle
+    # decoding works and gives the same as an explicit summary-engine handle
     syn, _ = D.sample(dm, 64, 2)
     syn_t = torch.from_numpy(syn.view(np.int32)).cuda()
     a = dec.decode(syn_t)["corrections"].cpu().numpy()
     dec.close()
-    dec2 = V.Decoder(dm, 4, D.schedules(dm.n, 4, 1), T=5, M=2, engine=V.ENGINE_CTA)
+    dec2 = V.Decoder(dm, 4, D.schedules(dm.n, 4, 1), T=5, M=2, engine=V.ENGINE_SUMMARY)
     b = dec2.decode(syn_t)["corrections"].cpu().numpy()
     dec2.close()
     assert np.array_equal(a, b)
     with pytest.raises(V.VibeError) as e:
-        V.Decoder(dm, 4, D.schedules(dm.n, 4, 1), T=5, M=2, engine=V.ENGINE_WARP, msg_fp16=False)
+        V.Decoder(dm, 4, D.schedules(dm.n, 4, 1), T=5, M=2, engine=V.ENGINE_IMAGE, msg_fp16=False)
     assert e.value.code == V.VIBE_ERR_UNSUPPORTED
 
 
