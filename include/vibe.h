@@ -191,15 +191,17 @@ int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, 
                         uint32_t* d_logical, vibe_shot_stats* d_stats, void* stream);
 
 /*
- * vibe_autotune -- times the decode of a sample batch (d_syndromes: B >= 1 shots, device) with a few
- * persistent-grid sizes for the BP and LSD kernels (occupancy maximum, 3/4 and 1/2 of it for BP;
- * maximum and half for LSD) and keeps the fastest for this handle. Decoding results do not depend
- * on the grid sizes (shots are independent; each shot's arithmetic is fixed), only the time does.
- * Synchronous; allocates a B-shot output buffer for the duration of the call and the workspace.
- * The chosen sizes (CTAs per SM) are returned when the pointers are not NULL.
+ * vibe_autotune -- times the decode of a sample batch (d_syndromes: B >= 1 shots, device) on each BP
+ * engine the problem fits (VIBE_ENGINE_IMAGE, VIBE_ENGINE_SUMMARY) with a few persistent-grid sizes
+ * (occupancy maximum, 3/4 and 1/2 of it for BP; maximum and half for LSD) and keeps the fastest
+ * engine and sizes for this handle. Decoding results do not depend on the engine or the grid sizes
+ * (shots are independent; each shot's arithmetic is fixed), only the time does. Synchronous;
+ * allocates a B-shot output buffer for the duration of the call and grows the workspace. Tune a
+ * handle before adding it to a vibe_batch: a batch copies the descriptor it sees at creation. The
+ * chosen engine and sizes (CTAs per SM) are returned when the pointers are not NULL.
  *   Errors: VIBE_ERR_INVALID, VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
  */
-int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream,
+int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream, int32_t* engine,
                   int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm);
 
 /*

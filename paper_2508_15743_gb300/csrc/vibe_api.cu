@@ -604,43 +604,68 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
   return profile_read(h->prof, bp_ms, lsd_ms, bp_launches, lsd_launches);
 }
 
-int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream, int32_t* bp_blocks_per_sm,
-                  int32_t* lsd_blocks_per_sm) {
+// Moves handle h to BP engine `engine` (descriptor on the device, bounds, launch sizes); the handle is
+// unchanged if the engine cannot run this problem.
+static int set_engine(vibe_handle* h, int engine) {
+  Tables t = h->t;
+  t.engine = engine;
+  Launch L = h->L;
+  L.one = t;
+  L.bnd = bounds_over(&t, 1);
+  int rc = size_launch(L);
+  if (rc != VIBE_OK) return rc;
+  VIBE_CUDA(cudaMemcpy(h->d_desc, &t, sizeof(Tables), cudaMemcpyHostToDevice), "engine switch");
+  h->t = t;
+  h->L = L;
+  return VIBE_OK;
+}
+
+int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream, int32_t* engine_out,
+                  int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm) {
   if (!h || !d_syndromes || B < 1) return fail(VIBE_ERR_INVALID, "NULL handle/syndromes or empty sample");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const Tables& t = h->t;
+  const int start_engine = h->t.engine;
   uint32_t* corr = nullptr;
-  VIBE_CUDA(dalloc(&corr, (size_t)B * t.nw), "autotune");
-  int& bp_cfg = h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm;
-  const int bp_max = bp_cfg, lsd_max = h->L.lsd_blocks_per_sm;
+  VIBE_CUDA(dalloc(&corr, (size_t)B * h->t.nw), "autotune");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_bp = bp_max, best_lsd = lsd_max;
+  int best_engine = start_engine, best_bp = 0, best_lsd = 0;
   int rc = VIBE_OK;
-  const int bp_try[] = {bp_max, (bp_max * 3 + 3) / 4, (bp_max + 1) / 2};
-  const int lsd_try[] = {lsd_max, std::max(1, lsd_max / 2)};
-  for (int bi = 0; bi < 3 && rc == VIBE_OK; ++bi)
-    for (int li = 0; li < 2 && rc == VIBE_OK; ++li) {
-      bp_cfg = std::max(1, bp_try[bi]);
-      h->L.lsd_blocks_per_sm = std::max(1, lsd_try[li]);
-      Batch q{nullptr, d_syndromes, t.mw, B, corr, t.nw, nullptr, t.kw, nullptr, nullptr, t.n, nullptr, nullptr};
-      if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;   // warm-up (and workspace)
-      cudaEventRecord(e0, s);
-      if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_bp = bp_cfg; best_lsd = h->L.lsd_blocks_per_sm; }
-    }
-  bp_cfg = best_bp;
-  h->L.lsd_blocks_per_sm = best_lsd;
+  for (int engine = VIBE_ENGINE_IMAGE; engine <= VIBE_ENGINE_SUMMARY && rc == VIBE_OK; ++engine) {
+    if (set_engine(h, engine) != VIBE_OK) continue;   // the problem does not fit this engine
+    int& bp_cfg = h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm;
+    const int bp_max = bp_cfg, lsd_max = h->L.lsd_blocks_per_sm;
+    const int bp_try[] = {bp_max, (bp_max * 3 + 3) / 4, (bp_max + 1) / 2};
+    const int lsd_try[] = {lsd_max, std::max(1, lsd_max / 2)};
+    for (int bi = 0; bi < 3 && rc == VIBE_OK; ++bi)
+      for (int li = 0; li < 2 && rc == VIBE_OK; ++li) {
+        bp_cfg = std::max(1, bp_try[bi]);
+        h->L.lsd_blocks_per_sm = std::max(1, lsd_try[li]);
+        const Tables& t = h->t;
+        Batch q{nullptr, d_syndromes, t.mw, B, corr, t.nw, nullptr, t.kw, nullptr, nullptr, t.n, nullptr, nullptr};
+        if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;   // warm-up (and workspace)
+        cudaEventRecord(e0, s);
+        if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_engine = engine; best_bp = bp_cfg; best_lsd = h->L.lsd_blocks_per_sm; }
+      }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(corr);
-  if (rc != VIBE_OK) return rc;
+  if (rc != VIBE_OK) {
+    set_engine(h, start_engine);
+    return rc;
+  }
+  if ((rc = set_engine(h, best_engine)) != VIBE_OK) return rc;
+  (h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm) = best_bp;
+  h->L.lsd_blocks_per_sm = best_lsd;
+  if (engine_out) *engine_out = best_engine;
   if (bp_blocks_per_sm) *bp_blocks_per_sm = best_bp;
   if (lsd_blocks_per_sm) *lsd_blocks_per_sm = best_lsd;
   return VIBE_OK;

@@ -230,6 +230,25 @@ __device__ __forceinline__ void rescan_row(int c, const Tables& t, const MT* msg
 }
 
 
+// A chunk of a sweep: up to 32 consecutive schedule entries [cs, min(cs + 32, e)) of level l, whose
+// entries end at e. l == nl marks the end of the sweep.
+struct Chunk {
+  int l;
+  uint32_t cs, e;
+};
+
+__device__ __forceinline__ Chunk first_chunk(const uint32_t* lo) { return Chunk{0, __ldg(lo), __ldg(lo + 1)}; }
+
+__device__ __forceinline__ Chunk next_chunk(const Chunk& c, const uint32_t* lo, int nl) {
+  if (c.l >= nl) return c;
+  if (c.cs + 32 < c.e) return Chunk{c.l, c.cs + 32, c.e};
+  return Chunk{c.l + 1, c.e, c.l + 1 < nl ? __ldg(lo + c.l + 2) : c.e};
+}
+
+__device__ __forceinline__ bool in_chunk(const Chunk& c, int nl, int lane) {
+  return c.l < nl && c.cs + (uint32_t)lane < c.e;
+}
+
 // Decodes shot `shot` of problem t with one warp. base: the warp's shared memory; gs: its global
 // scratch (messages, posterior, LLR accumulator, candidate records).
 template <typename MT, int DP>
@@ -315,25 +334,20 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       // converging (LLR average) and, for soft output, after every sweep
       float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
       // the sweep in chunks of up to 32 columns of one level, one column per lane; rescans after each
-      // chunk (later chunks of the same level touch other checks)
-      bool have = false;
-      int l = 0;
-      uint32_t cs = __ldg(lo), e = __ldg(lo + 1);
-      while (l < nl) {
-        if (cs + lane < e) {
-          if (!have) fetch_column<MT, DP>(__ldg(rec + cs + lane), t, msg, cd);
-          update_column_x<MT, DP>(cd, t, msg, X, const_cast<int*>(rcount), lp);
-        }
-        // fetch this lane's column of the next chunk
-        uint32_t ncs = cs + 32, ne = e;
-        int nlv = l;
-        if (ncs >= e) {
-          nlv = l + 1;
-          ncs = e;
-          ne = nlv < nl ? __ldg(lo + nlv + 1) : e;
-        }
-        have = false;
-        if (nlv < nl && ncs + lane < ne) { fetch_column<MT, DP>(__ldg(rec + ncs + lane), t, msg, cd); have = true; }
+      // chunk (later chunks of the same level touch other checks). Software pipeline: chunk j+1's
+      // column data (checks, old messages, prior) is fetched before chunk j is updated -- a column's
+      // messages are written only by that column, so the early read sees the same values -- and the
+      // schedule records two chunks ahead.
+      Chunk c = first_chunk(lo);
+      Chunk c1 = next_chunk(c, lo, nl);
+      Chunk c2 = next_chunk(c1, lo, nl);
+      if (in_chunk(c, nl, lane)) fetch_column<MT, DP>(__ldg(rec + c.cs + lane), t, msg, cd);
+      uint2 r1 = in_chunk(c1, nl, lane) ? __ldg(rec + c1.cs + lane) : make_uint2(0u, 0u);
+      while (c.l < nl) {
+        ColData<DP> cdn;
+        if (in_chunk(c1, nl, lane)) fetch_column<MT, DP>(r1, t, msg, cdn);
+        const uint2 r2 = in_chunk(c2, nl, lane) ? __ldg(rec + c2.cs + lane) : make_uint2(0u, 0u);
+        if (in_chunk(c, nl, lane)) update_column_x<MT, DP>(cd, t, msg, X, const_cast<int*>(rcount), lp);
         __syncwarp();
         const int nres = *rcount;
         if (nres > 0) {
@@ -343,7 +357,11 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
           if (lane == 0) *rcount = 0;
           __syncwarp();
         }
-        cs = ncs; e = ne; l = nlv;
+        cd = cdn;
+        r1 = r2;
+        c = c1;
+        c1 = c2;
+        c2 = next_chunk(c2, lo, nl);
       }
       ++my_iters;
       uint32_t bad = 0;

@@ -69,7 +69,7 @@ def _load():
     lib.vibe_profile.restype = ctypes.c_int
     lib.vibe_profile_read.argtypes = [vp, vp, vp, vp, vp]
     lib.vibe_profile_read.restype = ctypes.c_int
-    lib.vibe_autotune.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.vibe_autotune.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     lib.vibe_autotune.restype = ctypes.c_int
     lib.vibe_batch_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
     lib.vibe_batch_create.restype = ctypes.c_int
@@ -181,11 +181,11 @@ def vibe_profile_read(h):
 
 
 def vibe_autotune(h, d_syndromes, B, stream=None):
-    """Returns the (BP, LSD) CTAs per SM the tuner kept for this handle."""
-    bp, lsd = ctypes.c_int32(0), ctypes.c_int32(0)
-    _check(_lib.vibe_autotune(h, _ptr(d_syndromes), int(B), _stream_ptr(stream), ctypes.addressof(bp),
-                              ctypes.addressof(lsd)))
-    return bp.value, lsd.value
+    """Returns the (engine, BP CTAs per SM, LSD CTAs per SM) the tuner kept for this handle."""
+    eng, bp, lsd = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(_lib.vibe_autotune(h, _ptr(d_syndromes), int(B), _stream_ptr(stream), ctypes.addressof(eng),
+                              ctypes.addressof(bp), ctypes.addressof(lsd)))
+    return eng.value, bp.value, lsd.value
 
 
 def vibe_destroy(h):

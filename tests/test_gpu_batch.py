@@ -186,8 +186,70 @@ def test_autotune_keeps_results(V):
     s, _ = D.sample(dm, 4000, 9)
     syn_t = torch.from_numpy(s.view(np.int32)).cuda()
     before = dec.decode(syn_t)["corrections"].cpu().numpy()
-    bp, lsd = dec.autotune(syn_t)
-    assert bp >= 1 and lsd >= 1
+    eng, bp, lsd = dec.autotune(syn_t)
+    assert eng in (V.ENGINE_IMAGE, V.ENGINE_SUMMARY) and bp >= 1 and lsd >= 1
     after = dec.decode(syn_t)["corrections"].cpu().numpy()
     assert np.array_equal(before, after)
     dec.close()
+
+
+def test_autotune_may_switch_engine_and_keeps_results(V):
+    dm = C.circuit_dem(5, 5, 0.003, noise="si1000", basis="X")
+    perms = D.schedules(dm.n, 8, 2)
+    dec = V.Decoder(dm, 8, perms, T=15, M=3, msg_fp16=True)
+    s, _ = D.sample(dm, 3000, 6)
+    syn_t = torch.from_numpy(s.view(np.int32)).cuda()
+    before = dec.decode(syn_t)
+    b_corr, b_st = before["corrections"].cpu().numpy(), V.stats_to_numpy(before["stats"])
+    eng, bp, lsd = dec.autotune(syn_t)
+    assert eng in (V.ENGINE_IMAGE, V.ENGINE_SUMMARY)
+    after = dec.decode(syn_t)
+    assert np.array_equal(b_corr, after["corrections"].cpu().numpy())
+    assert np.array_equal(b_st, V.stats_to_numpy(after["stats"]))
+    dec.close()
+
+
+def test_mixed_batch_in_a_cuda_graph(V):
+    """A mixed decode captured once and replayed on new problem ids and syndromes. A shot writes only
+    its own problem's correction words, so the outputs are cleared before each replay to compare
+    whole rows with a fresh decode."""
+    probs = problems()[:3]
+    decs = [V.Decoder(dm, K, D.schedules(dm.n, K, s, natural=(K == 1)), T=T, M=M, lsd_order=o)
+            for (_, dm, K, M, T, o, s) in probs]
+    mb = V.MixedBatch(decs)
+    rng = np.random.default_rng(9)
+    B = 800
+    mw = max(d.mw for d in decs)
+
+    def draw(seed):
+        pid = rng.integers(0, len(probs), B).astype(np.int32)
+        syn = np.zeros((B, mw), np.uint32)
+        for i, (_, dm, *_r) in enumerate(probs):
+            rows = np.nonzero(pid == i)[0]
+            syn[rows] = pad_words(D.sample(dm, len(rows), seed + i)[0], mw)
+        return pid, syn
+
+    pid0, syn0 = draw(10)
+    pid_t = torch.from_numpy(pid0).cuda()
+    syn_t = torch.from_numpy(syn0.view(np.int32)).cuda()
+    out = mb.decode(pid_t, syn_t)          # warm-up: workspace and kernel attributes
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        mb.decode(pid_t, syn_t, out=out)
+    for seed in (20, 30):
+        pid, syn = draw(seed)
+        pid_t.copy_(torch.from_numpy(pid))
+        syn_t.copy_(torch.from_numpy(syn.view(np.int32)))
+        out["corrections"].zero_()
+        out["logical"].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        ref = mb.decode(pid_t, syn_t)
+        assert np.array_equal(out["corrections"].cpu().numpy(), ref["corrections"].cpu().numpy())
+        assert np.array_equal(out["logical"].cpu().numpy(), ref["logical"].cpu().numpy())
+        assert np.array_equal(out["stats"].cpu().numpy(), ref["stats"].cpu().numpy())
+    del g
+    mb.close()
+    for d in decs:
+        d.close()

@@ -113,8 +113,8 @@ def test_config4_mixed_circuit_family(V):
             decs.append(V.Decoder(dm, K, pm, T=T, M=M, msg_fp16=True))
     mb = V.MixedBatch(decs)
     rng = np.random.default_rng(4)
-    B = 24 * 40
-    pid = rng.permutation(np.repeat(np.arange(24, dtype=np.int32), 40))
+    B = 24 * 24
+    pid = rng.permutation(np.repeat(np.arange(24, dtype=np.int32), 24))
     mw = max(dc.mw for dc in decs)
     syn = np.zeros((B, mw), np.uint32)
     for i, dm in enumerate(dems):
