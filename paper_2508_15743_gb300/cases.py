@@ -3,8 +3,13 @@
     python -m paper_2508_15743_gb300.cases <case> [--shots B]
 
 runs one warm-up decode of 64 shots, then one decode of the case's batch, and prints one JSON line
-with the device counters (shots, BP sweeps, LSD shots, rescans) and the kernel times. Inputs are
-seeded and synthetic; nothing here is timed for reporting (bench.py does that).
+with the device counters (shots, BP sweeps, LSD shots, rescans) and the kernel times.
+
+    python -m paper_2508_15743_gb300.cases <case> --precisions [--shots B]
+
+decodes the same shots with FP32 and FP16 message storage and reports both throughputs, logical
+error rates with 2-sigma binomial intervals and the fraction of differing corrections. Inputs are
+seeded and synthetic; the bench workload's numbers come from bench.py.
 """
 from __future__ import annotations
 
@@ -24,6 +29,10 @@ CASES = {
     # circuit-level d=9 colour code on the summary engine, short ensemble
     "summary_circuit_d9": (lambda: C.circuit_dem(9, 9, 0.001, noise="si1000", basis="X"), 8, 10, 3, False, 2,
                            1216, 5),
+    # circuit-level d=9 at p = 3e-3 with the config-4 ensemble (K=32, T=50): enough logical failures
+    # in 2e4 shots to compare precisions
+    "summary_circuit_d9_p3": (lambda: C.circuit_dem(9, 9, 0.003, noise="si1000", basis="X"), 32, 50, 5, False,
+                              2, 20_000, 4),
     # circuit-level d=11, the full ensemble (K=64, T=50)
     "summary_circuit_d11": (lambda: C.circuit_dem(11, 11, 0.001, noise="si1000", basis="X"), 64, 50, 5, False, 2,
                             2432, 3),
@@ -55,12 +64,60 @@ def run_case(name: str, shots: int = 0) -> dict:
                 E=int(len(dm.H.colidx)))
 
 
+def _ler(fails: int, shots: int) -> dict:
+    p = fails / shots
+    half = 2.0 * np.sqrt(max(p * (1.0 - p), 1.0 / shots) / shots)
+    return dict(ler=p, two_sigma=[max(p - half, 0.0), p + half], failures=int(fails), shots=int(shots))
+
+
+def compare_precisions(name: str, shots: int = 0) -> dict:
+    """Decodes the same shots with FP32 and with FP16 message storage: throughput of each, logical
+    error rates with 2-sigma binomial intervals, and the fraction of shots whose correction differs."""
+    import time
+
+    import torch
+
+    from . import vibe as V
+
+    build, K, T, M, _, engine, default_shots, seed = CASES[name]
+    dm = build()
+    B = shots or default_shots
+    syn, obs = D.sample(dm, B, seed)
+    syn_t = torch.from_numpy(syn.view(np.int32)).cuda()
+    obs_t = torch.from_numpy(obs.view(np.int32)).cuda()
+    out, res = {}, {}
+    for fp16 in (False, True):
+        dec = V.Decoder(dm, K, D.schedules(dm.n, K, seed), T=T, M=M, msg_fp16=fp16, engine=engine)
+        dec.decode(syn_t[:64])
+        torch.cuda.synchronize()
+        cnt = torch.zeros(V.VIBE_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+        t0 = time.perf_counter()
+        o = dec.decode(syn_t, observables=obs_t, counters=cnt)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        c = cnt.cpu().numpy()
+        key = "fp16" if fp16 else "fp32"
+        out[key] = o["corrections"].cpu().numpy()
+        res[key] = dict(shots_per_s=B / dt, ler=_ler(int(c[V.CNT_FAILURES]), B), lsd_fraction=float(c[V.CNT_LSD]) / B,
+                        sweeps_per_shot=float(c[V.CNT_PAIR_ITERS]) / B)
+        dec.close()
+    res["corrections_differ"] = float((out["fp32"] != out["fp16"]).any(axis=1).mean())
+    res["fp16_ler_inside_fp32_interval"] = bool(
+        res["fp32"]["ler"]["two_sigma"][0] <= res["fp16"]["ler"]["ler"] <= res["fp32"]["ler"]["two_sigma"][1])
+    res.update(case=name, shots=B, n=dm.n, m=dm.m, K=K, T=T, M=M)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=sorted(CASES))
     ap.add_argument("--shots", type=int, default=0)
+    ap.add_argument("--precisions", action="store_true", help="compare FP32 and FP16 message storage")
     args = ap.parse_args()
-    print(json.dumps(run_case(args.case, args.shots)))
+    if args.precisions:
+        print(json.dumps(compare_precisions(args.case, args.shots)))
+    else:
+        print(json.dumps(run_case(args.case, args.shots)))
 
 
 if __name__ == "__main__":
