@@ -18,7 +18,9 @@
 // exactly the minimum and sign product that Algorithm 1's check update takes over N(c) \ v, with no
 // row scan. The messages themselves (E floats or halves per warp, in CSC edge order so that a column's
 // are contiguous) stay in global memory, where the column update reads its old values and writes the
-// new ones.
+// new ones; so do the member's decision bits (each lane fetches its column's bit with the column's
+// data, and only that column changes it). Syndrome and check-parity bits are packed 32 to a word, so
+// that the shared-memory state is ~16 bytes per check and more warps fit on an SM.
 //
 // Keeping the summary exact after column v replaces its message on c with magnitude x:
 //   v holds the smallest:  x <= second -> smallest = x;  else the row is rescanned;
@@ -79,9 +81,9 @@ __device__ __forceinline__ bool is_finite_bits(float x) {
 // Shared state of one warp for its current shot.
 struct XShared {
   float4* summ;     // m check summaries (smallest, second, holder edges, sign parity)
-  uint8_t* s8;      // m syndrome bits
-  uint8_t* par8;    // m: (H e)_c XOR s_c
-  uint32_t* dec;    // nw: the member's decisions e, bit-packed
+  uint32_t* s32;    // ceil(m/32) syndrome words
+  uint32_t* par32;  // ceil(m/32) words: (H e) XOR s
+  uint32_t* dec;    // nw: the member's decisions e, bit-packed, in the warp's global scratch
   int32_t* rlist;   // 32 * DP: checks to rescan after the current chunk of 32 columns
 };
 
@@ -95,6 +97,7 @@ struct MinBlocksX { static constexpr int value = 16 / kBpxWarpsPerCta; };
 template <int DP>
 struct ColData {
   uint32_t v, e0;
+  uint32_t e_old;   // the column's current decision
   int deg;
   float lam;
   int c[DP];
@@ -102,11 +105,13 @@ struct ColData {
 };
 
 template <typename MT, int DP>
-__device__ __forceinline__ void fetch_column(uint2 rec, const Tables& t, const MT* msg, ColData<DP>& d) {
+__device__ __forceinline__ void fetch_column(uint2 rec, const Tables& t, const MT* msg, const uint32_t* dec,
+                                             ColData<DP>& d) {
   d.v = rec.x & 0xffffffu;
   d.deg = (int)(rec.x >> 24);
   d.e0 = rec.y;
   d.lam = __ldg(t.lam + d.v);
+  d.e_old = (__ldcg(dec + (d.v >> 5)) >> (d.v & 31)) & 1u;   // only column v writes its bit
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
     d.c[k] = 0;
@@ -136,7 +141,8 @@ __device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tabl
       const float4 sm = X.summ[c[k]];
       const bool holder = __float_as_uint(sm.z) == e0 + k;
       const float mn = holder ? sm.y : sm.x;
-      const uint32_t neg = ((__float_as_uint(sm.w) >> 31) ^ sign_bit(o[k]) ^ (uint32_t)X.s8[c[k]]) & 1u;
+      const uint32_t sk = X.s32[c[k] >> 5] >> (c[k] & 31);
+      const uint32_t neg = ((__float_as_uint(sm.w) >> 31) ^ sign_bit(o[k]) ^ sk) & 1u;
       const float mag = __fmul_rn(alpha, mn);
       mcv[k] = neg ? -mag : mag;
     }
@@ -182,12 +188,11 @@ __device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tabl
   }
   const uint32_t e_new = L <= 0.0f ? 1u : 0u;
   const uint32_t bit = 1u << (v & 31);
-  const uint32_t e_old = (X.dec[v >> 5] & bit) ? 1u : 0u;
-  if (e_new != e_old) {
+  if (e_new != d.e_old) {
     atomicXor(&X.dec[v >> 5], bit);
 #pragma unroll
     for (int k = 0; k < DP; ++k)
-      if (k < deg) X.par8[c[k]] ^= 1u;
+      if (k < deg) atomicXor(&X.par32[c[k] >> 5], 1u << (c[k] & 31));
   }
   if (lpost) lpost[v] = L;
 }
@@ -257,12 +262,12 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
                                               unsigned long long& my_shots, unsigned long long& my_fail,
                                               unsigned long long& my_rescans) {
   const int n = t.n, m = t.m, K = t.K, M = t.M, T = t.T, nw = t.nw, kw = t.kw;
-  const int m4 = (m + 3) >> 2;
+  const int mw = t.mw;
   XShared X;
   X.summ = reinterpret_cast<float4*>(base + t.xo_summ);
-  X.s8 = base + t.xo_s;
-  X.par8 = base + t.xo_par;
-  X.dec = reinterpret_cast<uint32_t*>(base + t.xo_dec);
+  X.s32 = reinterpret_cast<uint32_t*>(base + t.xo_s);
+  X.par32 = reinterpret_cast<uint32_t*>(base + t.xo_par);
+  X.dec = reinterpret_cast<uint32_t*>(gs + t.xg_dec);
   X.rlist = reinterpret_cast<int32_t*>(base + t.xo_rl);
   volatile int* rcount = reinterpret_cast<volatile int*>(base + t.xo_rc);
   MT* msg = reinterpret_cast<MT*>(gs + t.xg_msg);
@@ -273,10 +278,11 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
 
   const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
   uint32_t any = 0;
-  for (int c = lane; c < 4 * m4; c += 32) {
-    const uint32_t b = c < m ? (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u : 0u;
-    X.s8[c] = (uint8_t)b;
-    any |= b;
+  for (int w = lane; w < mw; w += 32) {
+    const int rem = m - 32 * w;
+    const uint32_t x = __ldg(syn + w) & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
+    X.s32[w] = x;
+    any |= x;
   }
   any = __any_sync(kFull, any);
   __syncwarp();
@@ -317,10 +323,8 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       uint4* dst = reinterpret_cast<uint4*>(msg);
       const int nv = (int)(((size_t)t.E * sizeof(MT) + 15) / 16);
       for (int q = lane; q < nv; q += 32) __stcg(dst + q, __ldg(src + q));
-      for (int w = lane; w < nw; w += 32) X.dec[w] = 0u;
-      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(X.s8);
-      uint32_t* p32 = reinterpret_cast<uint32_t*>(X.par8);
-      for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
+      for (int w = lane; w < nw; w += 32) __stcg(X.dec + w, 0u);
+      for (int w = lane; w < mw; w += 32) X.par32[w] = X.s32[w];
       if (lane == 0) *rcount = 0;
     }
     __syncwarp();
@@ -341,11 +345,11 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       Chunk c = first_chunk(lo);
       Chunk c1 = next_chunk(c, lo, nl);
       Chunk c2 = next_chunk(c1, lo, nl);
-      if (in_chunk(c, nl, lane)) fetch_column<MT, DP>(__ldg(rec + c.cs + lane), t, msg, cd);
+      if (in_chunk(c, nl, lane)) fetch_column<MT, DP>(__ldg(rec + c.cs + lane), t, msg, X.dec, cd);
       uint2 r1 = in_chunk(c1, nl, lane) ? __ldg(rec + c1.cs + lane) : make_uint2(0u, 0u);
       while (c.l < nl) {
         ColData<DP> cdn;
-        if (in_chunk(c1, nl, lane)) fetch_column<MT, DP>(r1, t, msg, cdn);
+        if (in_chunk(c1, nl, lane)) fetch_column<MT, DP>(r1, t, msg, X.dec, cdn);
         const uint2 r2 = in_chunk(c2, nl, lane) ? __ldg(rec + c2.cs + lane) : make_uint2(0u, 0u);
         if (in_chunk(c, nl, lane)) update_column_x<MT, DP>(cd, t, msg, X, const_cast<int*>(rcount), lp);
         __syncwarp();
@@ -365,8 +369,7 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       }
       ++my_iters;
       uint32_t bad = 0;
-      const uint32_t* p32 = reinterpret_cast<const uint32_t*>(X.par8);
-      for (int q = lane; q < m4; q += 32) bad |= p32[q];
+      for (int w = lane; w < mw; w += 32) bad |= X.par32[w];
       if (!__any_sync(kFull, bad)) { conv = it; break; }
     }
     if (conv) {
@@ -374,11 +377,11 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
       const int slot = ncand < M ? ncand : __shfl_sync(kFull, c_slot, M - 1);
       uint32_t* bits = cand + (size_t)slot * nw;
-      for (int w = lane; w < nw; w += 32) bits[w] = X.dec[w];
+      for (int w = lane; w < nw; w += 32) bits[w] = __ldcg(X.dec + w);
       // W(e) = sum of lambda_j over e_j = 1, ascending j (every lane folds the same sequence)
       float W = 0.0f;
       for (int w = 0; w < nw; ++w) {
-        uint32_t x = X.dec[w];
+        uint32_t x = __ldcg(X.dec + w);
         while (x) {
           const int bpos = __ffs(x) - 1;
           W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
@@ -578,17 +581,16 @@ cudaError_t occupancy_x_mt(const Bounds& b, int ndem, int* out) {
 }  // namespace
 
 void bpx_layout(Tables* t, int msg_fp16) {
-  const size_t m4 = ((size_t)t->m + 3) / 4 * 4;
   size_t o = 0;
   t->xo_summ = (int)o;  o = a16(o + 16 * (size_t)t->m);
-  t->xo_s = (int)o;     o = a16(o + m4);
-  t->xo_par = (int)o;   o = a16(o + m4);
-  t->xo_dec = (int)o;   o = a16(o + 4 * (size_t)t->nw);
+  t->xo_s = (int)o;     o = a16(o + 4 * (size_t)t->mw);
+  t->xo_par = (int)o;   o = a16(o + 4 * (size_t)t->mw);
   t->xo_rl = (int)o;    o = a16(o + 4 * 32 * (size_t)t->DP);
   t->xo_rc = (int)o;    o = a16(o + 4);
   t->x_warp_smem = (int)o;
   long long g = 0;
   t->xg_msg = g;   g += (long long)a16((size_t)t->E * (msg_fp16 ? 2 : 4));
+  t->xg_dec = g;   g += (long long)a16(4 * (size_t)t->nw);
   t->xg_lpost = g; g += (long long)a16(4 * (size_t)t->n);
   t->xg_acc = g;   g += (long long)a16(4 * (size_t)t->n);
   t->xg_cand = g;  g += (long long)a16(4 * (size_t)t->M * t->nw);

@@ -49,9 +49,9 @@ struct Tables {
   int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // image engine: per-warp shared memory, bytes
   int engine;    // VIBE_ENGINE_IMAGE or VIBE_ENGINE_SUMMARY
   // summary engine: shared memory of one warp (bytes) and global scratch of one warp (bytes, 16-aligned parts)
-  int xo_summ, xo_s, xo_par, xo_dec, xo_rl, xo_rc, x_warp_smem;
+  int xo_summ, xo_s, xo_par, xo_rl, xo_rc, x_warp_smem;
   // xg_cpost = x_warp_scratch: the M*n candidate posteriors (soft output only) follow the fixed part
-  long long xg_msg, xg_lpost, xg_acc, xg_cand, xg_cpost, x_warp_scratch;
+  long long xg_msg, xg_dec, xg_lpost, xg_acc, xg_cand, xg_cpost, x_warp_scratch;
   const int32_t* rowptr;   // H CSR
   const int32_t* colidx;
   const int32_t* colptr;   // H CSC, checks ascending in each column
