@@ -9,7 +9,8 @@ and 5.
 
 Config 4 (colour codes d = 5..15 under circuit-level noise at p = 1, 2, 3, 5 per mille, K=32, FP16,
 one mixed launch): every shot equals the decode of its own handle, and shots of the smaller problems
-match the oracle. T is reduced to 10 to bound the run time; the full-T throughput is a bench figure.
+match the oracle. T is reduced to 10 to bound the run time (an LSD-bound d=15 shot at T=50 runs
+32 x 50 sweeps of ~1300 levels each).
 """
 import numpy as np
 import pytest
