@@ -118,3 +118,33 @@ def test_rejects_bad_arguments():
 
 def test_device_bytes_per_shot_counts_io_and_workspace():
     assert S.device_bytes_per_shot(1, 1, 1, 10) == 4 * 3 + 12 + 4 + 4 + 40
+
+
+def test_make_requests_is_seeded_and_mixes_problems():
+    from paper_2508_15743_gb300 import dem as D
+    dems = [D.build_workload("cc666_d5_codecap"), D.phenomenological_dem(3, 2, 0.05, 0.05)]
+    a = S.make_requests(dems, 2000, 5e4, seed=3)
+    b = S.make_requests(dems, 2000, 5e4, seed=3)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    arrivals, problems, syn, obs = a
+    assert np.all(np.diff(arrivals) >= 0)
+    assert set(np.unique(problems)) == {0, 1}
+    assert syn.shape == (2000, max(D.words(d.m) for d in dems))
+    # each row's syndrome uses only its own problem's words and bits
+    for i, dm in enumerate(dems):
+        rows = problems == i
+        assert not syn[rows][:, D.words(dm.m):].any()
+        rem = dm.m % 32
+        if rem:
+            assert not (syn[rows][:, D.words(dm.m) - 1] >> rem).any()
+
+
+def test_case_runner_binomial_interval():
+    from paper_2508_15743_gb300 import cases
+    r = cases._ler(100, 10_000)
+    assert r["ler"] == 0.01 and r["failures"] == 100 and r["shots"] == 10_000
+    half = 2 * np.sqrt(0.01 * 0.99 / 10_000)
+    assert np.isclose(r["two_sigma"][0], 0.01 - half) and np.isclose(r["two_sigma"][1], 0.01 + half)
+    z = cases._ler(0, 1000)           # no failures: the interval still has width
+    assert z["two_sigma"][0] == 0.0 and z["two_sigma"][1] > 0.0
