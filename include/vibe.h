@@ -214,7 +214,7 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
  * vibe_batch_create -- handles[0..count) (1 <= count <= 64, non-NULL, created on the current
  *   device, all with the same msg_fp16) are referenced, not copied: they must outlive the batch and
  *   must not be destroyed first. The batch owns a device copy of their descriptors and its own
- *   workspace. Errors: VIBE_ERR_INVALID (bad count/handles, mixed devices or message precisions,
+ *   workspace (summary-engine problems run the packed state layout in a batch; results are the same). Errors: VIBE_ERR_INVALID (bad count/handles, mixed devices or message precisions,
  *   device not current), VIBE_ERR_UNSUPPORTED (the largest problem's state with the batch's
  *   descriptor table does not fit in shared memory), VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
  */

@@ -44,6 +44,11 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 constexpr size_t kWorkspaceBytes = size_t(4) << 30;   // LSD hand-off buffer budget per workspace
 
+// Summary engine: problems with at least this many checks start with the byte layout of the warp
+// state, the others with the packed layout (measured: packed is faster on the circuit-level colour
+// codes of d = 5 and 9, bytes on d = 11 with 990 checks). vibe_autotune times both.
+constexpr int kBytesLayoutChecks = 900;
+
 int check_csr(const vibe_csr* A, const char* name, bool rows_nonempty) {
   if (!A || !A->rowptr || (!A->colidx && A->nrows > 0)) return fail(VIBE_ERR_INVALID, "%s: NULL matrix", name);
   if (A->nrows < 0 || A->ncols < 1) return fail(VIBE_ERR_INVALID, "%s: bad shape %d x %d", name, A->nrows, A->ncols);
@@ -269,6 +274,7 @@ Bounds bounds_over(const Tables* ts, int count) {
       b.warp_smem = std::max(b.warp_smem, t.warp_smem);
     } else {
       b.engines |= 2;
+      b.x_packed = t.x_packed;   // used by single-problem launches only
       b.x_warp_smem = std::max(b.x_warp_smem, t.x_warp_smem);
       b.x_warp_scratch = std::max(b.x_warp_scratch, t.x_warp_scratch);
     }
@@ -421,6 +427,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   t.mw = (m + 31) / 32; t.nw = (n + 31) / 32; t.kw = (k + 31) / 32; t.W = t.mw;
   t.T = p->max_iter; t.M = p->M; t.lsd_order = p->lsd_order; t.alpha = p->alpha;
   vibe::bp_warp_smem_bytes(&t, p->msg_fp16);
+  t.x_packed = m < kBytesLayoutChecks ? 1 : 0;
   vibe::bpx_layout(&t, p->msg_fp16);
   t.engine = p->bp_engine;
   if (t.engine == VIBE_ENGINE_AUTO) {
@@ -604,11 +611,13 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
   return profile_read(h->prof, bp_ms, lsd_ms, bp_launches, lsd_launches);
 }
 
-// Moves handle h to BP engine `engine` (descriptor on the device, bounds, launch sizes); the handle is
-// unchanged if the engine cannot run this problem.
-static int set_engine(vibe_handle* h, int engine) {
+// Moves handle h to BP engine `engine` and, for the summary engine, state layout `packed` (descriptor
+// on the device, bounds, launch sizes); the handle is unchanged if the engine cannot run this problem.
+static int set_engine(vibe_handle* h, int engine, int packed) {
   Tables t = h->t;
   t.engine = engine;
+  t.x_packed = packed;
+  vibe::bpx_layout(&t, h->L.msg_fp16);
   Launch L = h->L;
   L.one = t;
   L.bnd = bounds_over(&t, 1);
@@ -624,17 +633,21 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
                   int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm) {
   if (!h || !d_syndromes || B < 1) return fail(VIBE_ERR_INVALID, "NULL handle/syndromes or empty sample");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int start_engine = h->t.engine;
+  const int start_engine = h->t.engine, start_packed = h->t.x_packed;
   uint32_t* corr = nullptr;
   VIBE_CUDA(dalloc(&corr, (size_t)B * h->t.nw), "autotune");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_engine = start_engine, best_bp = 0, best_lsd = 0;
+  int best_engine = start_engine, best_packed = start_packed, best_bp = 0, best_lsd = 0;
   int rc = VIBE_OK;
-  for (int engine = VIBE_ENGINE_IMAGE; engine <= VIBE_ENGINE_SUMMARY && rc == VIBE_OK; ++engine) {
-    if (set_engine(h, engine) != VIBE_OK) continue;   // the problem does not fit this engine
+  // candidates: the image engine, and the summary engine in both state layouts
+  const int cand_engine[] = {VIBE_ENGINE_IMAGE, VIBE_ENGINE_SUMMARY, VIBE_ENGINE_SUMMARY};
+  const int cand_packed[] = {start_packed, 1, 0};
+  for (int ci = 0; ci < 3 && rc == VIBE_OK; ++ci) {
+    const int engine = cand_engine[ci];
+    if (set_engine(h, engine, cand_packed[ci]) != VIBE_OK) continue;   // the problem does not fit
     int& bp_cfg = h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm;
     const int bp_max = bp_cfg, lsd_max = h->L.lsd_blocks_per_sm;
     const int bp_try[] = {bp_max, (bp_max * 3 + 3) / 4, (bp_max + 1) / 2};
@@ -652,17 +665,20 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; best_engine = engine; best_bp = bp_cfg; best_lsd = h->L.lsd_blocks_per_sm; }
+        if (ms < best) {
+          best = ms; best_engine = engine; best_packed = cand_packed[ci];
+          best_bp = bp_cfg; best_lsd = h->L.lsd_blocks_per_sm;
+        }
       }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(corr);
   if (rc != VIBE_OK) {
-    set_engine(h, start_engine);
+    set_engine(h, start_engine, start_packed);
     return rc;
   }
-  if ((rc = set_engine(h, best_engine)) != VIBE_OK) return rc;
+  if ((rc = set_engine(h, best_engine, best_packed)) != VIBE_OK) return rc;
   (h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm) = best_bp;
   h->L.lsd_blocks_per_sm = best_lsd;
   if (engine_out) *engine_out = best_engine;
@@ -690,6 +706,12 @@ int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** o
     if (h->device != h0->device) return fail(VIBE_ERR_INVALID, "handles live on different devices");
     if (h->L.msg_fp16 != h0->L.msg_fp16) return fail(VIBE_ERR_INVALID, "handles mix FP16 and FP32 messages");
     desc[i] = h->t;
+    if (desc[i].engine == VIBE_ENGINE_SUMMARY && !desc[i].x_packed) {
+      // the mixed summary kernel runs the packed state layout; the batch's own copy of the
+      // descriptor (the batch has its own workspace) is laid out for it
+      desc[i].x_packed = 1;
+      vibe::bpx_layout(&desc[i], h->L.msg_fp16);
+    }
   }
   const Bounds b = bounds_over(desc.data(), count);
   int cur = -1;

@@ -18,9 +18,12 @@
 // exactly the minimum and sign product that Algorithm 1's check update takes over N(c) \ v, with no
 // row scan. The messages themselves (E floats or halves per warp, in CSC edge order so that a column's
 // are contiguous) stay in global memory, where the column update reads its old values and writes the
-// new ones; so do the member's decision bits (each lane fetches its column's bit with the column's
-// data, and only that column changes it). Syndrome and check-parity bits are packed 32 to a word, so
-// that the shared-memory state is ~16 bytes per check and more warps fit on an SM.
+// new ones. Two layouts of the rest of a warp's state (same results): "bytes" keeps the decision
+// bits in shared memory and one byte per check for the syndrome and the check parity; "packed" moves
+// the decision bits to global memory (each lane fetches its column's bit with the column's data, and
+// only that column changes it) and packs syndrome and parity 32 bits to a word, for ~16 bytes of
+// shared memory per check and more resident warps. Measured on circuit-level colour codes, packed is
+// faster at d=5..9 and bytes at d=11 (the host picks by the number of checks; the tuner times both).
 //
 // Keeping the summary exact after column v replaces its message on c with magnitude x:
 //   v holds the smallest:  x <= second -> smallest = x;  else the row is rescanned;
@@ -81,9 +84,11 @@ __device__ __forceinline__ bool is_finite_bits(float x) {
 // Shared state of one warp for its current shot.
 struct XShared {
   float4* summ;     // m check summaries (smallest, second, holder edges, sign parity)
-  uint32_t* s32;    // ceil(m/32) syndrome words
-  uint32_t* par32;  // ceil(m/32) words: (H e) XOR s
-  uint32_t* dec;    // nw: the member's decisions e, bit-packed, in the warp's global scratch
+  uint32_t* s32;    // packed: ceil(m/32) syndrome words
+  uint32_t* par32;  // packed: ceil(m/32) words, (H e) XOR s
+  uint8_t* s8;      // bytes: m syndrome bytes
+  uint8_t* par8;    // bytes: m bytes, (H e)_c XOR s_c
+  uint32_t* dec;    // nw: the member's decisions, bit-packed (packed: in the warp's global scratch)
   int32_t* rlist;   // 32 * DP: checks to rescan after the current chunk of 32 columns
 };
 
@@ -104,14 +109,14 @@ struct ColData {
   float o[DP];
 };
 
-template <typename MT, int DP>
+template <typename MT, int DP, bool PK>
 __device__ __forceinline__ void fetch_column(uint2 rec, const Tables& t, const MT* msg, const uint32_t* dec,
                                              ColData<DP>& d) {
   d.v = rec.x & 0xffffffu;
   d.deg = (int)(rec.x >> 24);
   d.e0 = rec.y;
   d.lam = __ldg(t.lam + d.v);
-  d.e_old = (__ldcg(dec + (d.v >> 5)) >> (d.v & 31)) & 1u;   // only column v writes its bit
+  d.e_old = PK ? (__ldcg(dec + (d.v >> 5)) >> (d.v & 31)) & 1u : 0u;   // only column v writes its bit
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
     d.c[k] = 0;
@@ -124,7 +129,7 @@ __device__ __forceinline__ void fetch_column(uint2 rec, const Tables& t, const M
 }
 
 // Serial-V update of column v (deg checks, edges e0 .. e0 + deg - 1 in ascending check order).
-template <typename MT, int DP>
+template <typename MT, int DP, bool PK>
 __device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tables& t, MT* msg, const XShared& X,
                                                 int* rcount, float* lpost) {
   const uint32_t v = d.v, e0 = d.e0;
@@ -141,7 +146,7 @@ __device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tabl
       const float4 sm = X.summ[c[k]];
       const bool holder = __float_as_uint(sm.z) == e0 + k;
       const float mn = holder ? sm.y : sm.x;
-      const uint32_t sk = X.s32[c[k] >> 5] >> (c[k] & 31);
+      const uint32_t sk = PK ? X.s32[c[k] >> 5] >> (c[k] & 31) : (uint32_t)X.s8[c[k]];
       const uint32_t neg = ((__float_as_uint(sm.w) >> 31) ^ sign_bit(o[k]) ^ sk) & 1u;
       const float mag = __fmul_rn(alpha, mn);
       mcv[k] = neg ? -mag : mag;
@@ -188,11 +193,16 @@ __device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tabl
   }
   const uint32_t e_new = L <= 0.0f ? 1u : 0u;
   const uint32_t bit = 1u << (v & 31);
-  if (e_new != d.e_old) {
+  const uint32_t e_old = PK ? d.e_old : (X.dec[v >> 5] & bit) ? 1u : 0u;
+  if (e_new != e_old) {
     atomicXor(&X.dec[v >> 5], bit);
 #pragma unroll
-    for (int k = 0; k < DP; ++k)
-      if (k < deg) atomicXor(&X.par32[c[k] >> 5], 1u << (c[k] & 31));
+    for (int k = 0; k < DP; ++k) {
+      if (k < deg) {
+        if (PK) atomicXor(&X.par32[c[k] >> 5], 1u << (c[k] & 31));
+        else X.par8[c[k]] ^= 1u;   // this level's only writer of check c's byte
+      }
+    }
   }
   if (lpost) lpost[v] = L;
 }
@@ -256,18 +266,21 @@ __device__ __forceinline__ bool in_chunk(const Chunk& c, int nl, int lane) {
 
 // Decodes shot `shot` of problem t with one warp. base: the warp's shared memory; gs: its global
 // scratch (messages, posterior, LLR accumulator, candidate records).
-template <typename MT, int DP>
+template <typename MT, int DP, bool PK>
 __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, uint32_t shot, unsigned char* base,
                                               unsigned char* gs, int lane, unsigned long long& my_iters,
                                               unsigned long long& my_shots, unsigned long long& my_fail,
                                               unsigned long long& my_rescans) {
   const int n = t.n, m = t.m, K = t.K, M = t.M, T = t.T, nw = t.nw, kw = t.kw;
   const int mw = t.mw;
+  const int m4 = (m + 3) >> 2;
   XShared X;
   X.summ = reinterpret_cast<float4*>(base + t.xo_summ);
   X.s32 = reinterpret_cast<uint32_t*>(base + t.xo_s);
   X.par32 = reinterpret_cast<uint32_t*>(base + t.xo_par);
-  X.dec = reinterpret_cast<uint32_t*>(gs + t.xg_dec);
+  X.s8 = base + t.xo_s;
+  X.par8 = base + t.xo_par;
+  X.dec = PK ? reinterpret_cast<uint32_t*>(gs + t.xg_dec) : reinterpret_cast<uint32_t*>(base + t.xo_dec);
   X.rlist = reinterpret_cast<int32_t*>(base + t.xo_rl);
   volatile int* rcount = reinterpret_cast<volatile int*>(base + t.xo_rc);
   MT* msg = reinterpret_cast<MT*>(gs + t.xg_msg);
@@ -278,11 +291,19 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
 
   const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
   uint32_t any = 0;
-  for (int w = lane; w < mw; w += 32) {
-    const int rem = m - 32 * w;
-    const uint32_t x = __ldg(syn + w) & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
-    X.s32[w] = x;
-    any |= x;
+  if (PK) {
+    for (int w = lane; w < mw; w += 32) {
+      const int rem = m - 32 * w;
+      const uint32_t x = __ldg(syn + w) & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
+      X.s32[w] = x;
+      any |= x;
+    }
+  } else {
+    for (int c = lane; c < 4 * m4; c += 32) {
+      const uint32_t b = c < m ? (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u : 0u;
+      X.s8[c] = (uint8_t)b;
+      any |= b;
+    }
   }
   any = __any_sync(kFull, any);
   __syncwarp();
@@ -323,8 +344,15 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       uint4* dst = reinterpret_cast<uint4*>(msg);
       const int nv = (int)(((size_t)t.E * sizeof(MT) + 15) / 16);
       for (int q = lane; q < nv; q += 32) __stcg(dst + q, __ldg(src + q));
-      for (int w = lane; w < nw; w += 32) __stcg(X.dec + w, 0u);
-      for (int w = lane; w < mw; w += 32) X.par32[w] = X.s32[w];
+      if (PK) {
+        for (int w = lane; w < nw; w += 32) __stcg(X.dec + w, 0u);
+        for (int w = lane; w < mw; w += 32) X.par32[w] = X.s32[w];
+      } else {
+        for (int w = lane; w < nw; w += 32) X.dec[w] = 0u;
+        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(X.s8);
+        uint32_t* p32 = reinterpret_cast<uint32_t*>(X.par8);
+        for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
+      }
       if (lane == 0) *rcount = 0;
     }
     __syncwarp();
@@ -345,13 +373,13 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       Chunk c = first_chunk(lo);
       Chunk c1 = next_chunk(c, lo, nl);
       Chunk c2 = next_chunk(c1, lo, nl);
-      if (in_chunk(c, nl, lane)) fetch_column<MT, DP>(__ldg(rec + c.cs + lane), t, msg, X.dec, cd);
+      if (in_chunk(c, nl, lane)) fetch_column<MT, DP, PK>(__ldg(rec + c.cs + lane), t, msg, X.dec, cd);
       uint2 r1 = in_chunk(c1, nl, lane) ? __ldg(rec + c1.cs + lane) : make_uint2(0u, 0u);
       while (c.l < nl) {
         ColData<DP> cdn;
-        if (in_chunk(c1, nl, lane)) fetch_column<MT, DP>(r1, t, msg, X.dec, cdn);
+        if (in_chunk(c1, nl, lane)) fetch_column<MT, DP, PK>(r1, t, msg, X.dec, cdn);
         const uint2 r2 = in_chunk(c2, nl, lane) ? __ldg(rec + c2.cs + lane) : make_uint2(0u, 0u);
-        if (in_chunk(c, nl, lane)) update_column_x<MT, DP>(cd, t, msg, X, const_cast<int*>(rcount), lp);
+        if (in_chunk(c, nl, lane)) update_column_x<MT, DP, PK>(cd, t, msg, X, const_cast<int*>(rcount), lp);
         __syncwarp();
         const int nres = *rcount;
         if (nres > 0) {
@@ -369,7 +397,12 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       }
       ++my_iters;
       uint32_t bad = 0;
-      for (int w = lane; w < mw; w += 32) bad |= X.par32[w];
+      if (PK) {
+        for (int w = lane; w < mw; w += 32) bad |= X.par32[w];
+      } else {
+        const uint32_t* p32 = reinterpret_cast<const uint32_t*>(X.par8);
+        for (int q = lane; q < m4; q += 32) bad |= p32[q];
+      }
       if (!__any_sync(kFull, bad)) { conv = it; break; }
     }
     if (conv) {
@@ -377,11 +410,11 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
       const int slot = ncand < M ? ncand : __shfl_sync(kFull, c_slot, M - 1);
       uint32_t* bits = cand + (size_t)slot * nw;
-      for (int w = lane; w < nw; w += 32) bits[w] = __ldcg(X.dec + w);
+      for (int w = lane; w < nw; w += 32) bits[w] = PK ? __ldcg(X.dec + w) : X.dec[w];
       // W(e) = sum of lambda_j over e_j = 1, ascending j (every lane folds the same sequence)
       float W = 0.0f;
       for (int w = 0; w < nw; ++w) {
-        uint32_t x = __ldcg(X.dec + w);
+        uint32_t x = PK ? __ldcg(X.dec + w) : X.dec[w];
         while (x) {
           const int bpos = __ffs(x) - 1;
           W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
@@ -472,9 +505,10 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
 }
 
 // MIXED: shots name their problems (dem_of_shot); the descriptors are copied to shared memory after
-// the warps' regions and shots of image-engine problems are left to that kernel. Otherwise every shot
-// decodes a.one from the parameter space.
-template <typename MT, int DP, bool MIXED>
+// the warps' regions and shots of image-engine problems are left to that kernel (mixed batches give
+// every summary-engine problem the packed layout, PK). Otherwise every shot decodes a.one from the
+// parameter space in layout PK.
+template <typename MT, int DP, bool MIXED, bool PK>
 __global__ void __launch_bounds__(kBpxWarpsPerCta * 32, MinBlocksX<MT>::value) k_bpx(const BpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -518,9 +552,9 @@ __global__ void __launch_bounds__(kBpxWarpsPerCta * 32, MinBlocksX<MT>::value) k
         continue;
       }
       if (sdem[di].engine != VIBE_ENGINE_SUMMARY) continue;   // left to the image engine
-      decode_shot_x<MT, DP>(a, sdem[di], shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
+      decode_shot_x<MT, DP, PK>(a, sdem[di], shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
     } else {
-      decode_shot_x<MT, DP>(a, a.one, shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
+      decode_shot_x<MT, DP, PK>(a, a.one, shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
     }
   }
   if (lane == 0 && a.counters) {
@@ -533,19 +567,19 @@ __global__ void __launch_bounds__(kBpxWarpsPerCta * 32, MinBlocksX<MT>::value) k
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-template <typename MT, int DP, bool MIXED>
+template <typename MT, int DP, bool MIXED, bool PK>
 cudaError_t launch_x(const BpArgs& a, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
+  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED, PK>>(smem);
   if (err != cudaSuccess) return err;
-  k_bpx<MT, DP, MIXED><<<grid, kBpxWarpsPerCta * 32, smem, s>>>(a);
+  k_bpx<MT, DP, MIXED, PK><<<grid, kBpxWarpsPerCta * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename MT, int DP, bool MIXED>
+template <typename MT, int DP, bool MIXED, bool PK>
 cudaError_t occupancy_x(size_t smem, int* out) {
-  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
+  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED, PK>>(smem);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bpx<MT, DP, MIXED>, kBpxWarpsPerCta * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bpx<MT, DP, MIXED, PK>, kBpxWarpsPerCta * 32, smem);
 }
 
 template <typename Fn>
@@ -564,8 +598,9 @@ cudaError_t launch_x_mt(const BpArgs& a, int grid, cudaStream_t s) {
   const bool mixed = a.dem_of_shot != nullptr;
   const size_t smem = bpx_cta_smem_bytes(a.bnd, mixed ? a.ndem : 0);
   return by_dp_x(a.bnd.DP, [&](auto dp) {
-    return mixed ? launch_x<MT, decltype(dp)::value, true>(a, grid, smem, s)
-                 : launch_x<MT, decltype(dp)::value, false>(a, grid, smem, s);
+    if (mixed) return launch_x<MT, decltype(dp)::value, true, true>(a, grid, smem, s);
+    return a.one.x_packed ? launch_x<MT, decltype(dp)::value, false, true>(a, grid, smem, s)
+                          : launch_x<MT, decltype(dp)::value, false, false>(a, grid, smem, s);
   });
 }
 
@@ -573,24 +608,28 @@ template <typename MT>
 cudaError_t occupancy_x_mt(const Bounds& b, int ndem, int* out) {
   const size_t smem = bpx_cta_smem_bytes(b, ndem);
   return by_dp_x(b.DP, [&](auto dp) {
-    return ndem > 0 ? occupancy_x<MT, decltype(dp)::value, true>(smem, out)
-                    : occupancy_x<MT, decltype(dp)::value, false>(smem, out);
+    if (ndem > 0) return occupancy_x<MT, decltype(dp)::value, true, true>(smem, out);
+    return b.x_packed ? occupancy_x<MT, decltype(dp)::value, false, true>(smem, out)
+                      : occupancy_x<MT, decltype(dp)::value, false, false>(smem, out);
   });
 }
 
 }  // namespace
 
 void bpx_layout(Tables* t, int msg_fp16) {
+  const bool pk = t->x_packed != 0;
+  const size_t flag_bytes = pk ? 4 * (size_t)t->mw : ((size_t)t->m + 3) / 4 * 4;   // syndrome / parity
   size_t o = 0;
   t->xo_summ = (int)o;  o = a16(o + 16 * (size_t)t->m);
-  t->xo_s = (int)o;     o = a16(o + 4 * (size_t)t->mw);
-  t->xo_par = (int)o;   o = a16(o + 4 * (size_t)t->mw);
+  t->xo_s = (int)o;     o = a16(o + flag_bytes);
+  t->xo_par = (int)o;   o = a16(o + flag_bytes);
+  t->xo_dec = (int)o;   o = a16(o + (pk ? 0 : 4 * (size_t)t->nw));
   t->xo_rl = (int)o;    o = a16(o + 4 * 32 * (size_t)t->DP);
   t->xo_rc = (int)o;    o = a16(o + 4);
   t->x_warp_smem = (int)o;
   long long g = 0;
   t->xg_msg = g;   g += (long long)a16((size_t)t->E * (msg_fp16 ? 2 : 4));
-  t->xg_dec = g;   g += (long long)a16(4 * (size_t)t->nw);
+  t->xg_dec = g;   g += (long long)a16(pk ? 4 * (size_t)t->nw : 0);
   t->xg_lpost = g; g += (long long)a16(4 * (size_t)t->n);
   t->xg_acc = g;   g += (long long)a16(4 * (size_t)t->n);
   t->xg_cand = g;  g += (long long)a16(4 * (size_t)t->M * t->nw);

@@ -49,7 +49,8 @@ struct Tables {
   int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // image engine: per-warp shared memory, bytes
   int engine;    // VIBE_ENGINE_IMAGE or VIBE_ENGINE_SUMMARY
   // summary engine: shared memory of one warp (bytes) and global scratch of one warp (bytes, 16-aligned parts)
-  int xo_summ, xo_s, xo_par, xo_rl, xo_rc, x_warp_smem;
+  int x_packed;  // summary-engine state layout: 1 packed (decisions in global memory, bit words), 0 bytes
+  int xo_summ, xo_s, xo_par, xo_dec, xo_rl, xo_rc, x_warp_smem;
   // xg_cpost = x_warp_scratch: the M*n candidate posteriors (soft output only) follow the fixed part
   long long xg_msg, xg_dec, xg_lpost, xg_acc, xg_cand, xg_cpost, x_warp_scratch;
   const int32_t* rowptr;   // H CSR
@@ -80,6 +81,7 @@ struct Bounds {
   int x_warp_smem;    // largest summary-engine shared memory per warp (0 if no problem uses that engine)
   long long x_warp_scratch;   // largest summary-engine global scratch per warp, bytes
   int engines;     // bit 0: some problem uses the image engine, bit 1: the summary engine
+  int x_packed;    // single-problem launch: the summary engine's layout (Tables::x_packed)
 };
 
 struct BpArgs {
