@@ -192,7 +192,8 @@ int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, 
 
 /*
  * vibe_autotune -- times the decode of a sample batch (d_syndromes: B >= 1 shots, device) on each BP
- * engine the problem fits (VIBE_ENGINE_IMAGE, VIBE_ENGINE_SUMMARY) with a few persistent-grid sizes
+ * engine the problem fits (VIBE_ENGINE_IMAGE; VIBE_ENGINE_SUMMARY in both of its warp-state layouts,
+ * decision bits in shared memory or in global memory) with a few persistent-grid sizes
  * (occupancy maximum, 3/4 and 1/2 of it for BP; maximum and half for LSD) and keeps the fastest
  * engine and sizes for this handle. Decoding results do not depend on the engine or the grid sizes
  * (shots are independent; each shot's arithmetic is fixed), only the time does. Synchronous;
