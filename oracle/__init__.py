@@ -59,6 +59,8 @@ def _bind(path):
     lib.or_prior_llr.argtypes = [i32, vp, vp, vp]
     lib.or_bp_member.argtypes = [vp, vp, vp, i32, ctypes.c_float, i32, i32, vp, vp]
     lib.or_bp_member.restype = i32
+    lib.or_bp_member_flood.argtypes = [vp, vp, i32, ctypes.c_float, i32, i32, vp, vp]
+    lib.or_bp_member_flood.restype = i32
     lib.or_decode.argtypes = [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, i32]
     lib.or_decode.restype = i32
     lib.or_lsd.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
@@ -172,6 +174,19 @@ def decode(dem, perms, syndromes, T, alpha, M, lsd_order=0, mode=FP32, nthreads=
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return dict(corrections=corr, logical=logi, stats=stats, soft=soft)
+
+
+def bp_member_flood(dem, syndrome_bits, T, alpha, mode=FP32, early_stop=True):
+    """One parallel-schedule (flooding) BP member, Algorithm 1's other branch.
+    Returns (t_conv, posterior f64[n], ebits u8[n])."""
+    lib = _load()
+    P = Problem(dem)
+    s = np.ascontiguousarray(syndrome_bits, dtype=np.uint8)
+    post = np.zeros(P.n, np.float64)
+    eb = np.zeros(P.n, np.uint8)
+    t = lib.or_bp_member_flood(ctypes.byref(P.c), _ptr(s), int(T), float(alpha), int(mode),
+                               int(bool(early_stop)), _ptr(post), _ptr(eb))
+    return int(t), post, eb
 
 
 def lsd(dem, soft, syndrome_bits, order=0, mode=FP32):

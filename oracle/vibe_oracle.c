@@ -24,6 +24,11 @@
  *     j mod 32, ascending) combined pairwise at distances 16, 8, 4, 2, 1. Only finite entries enter
  *     the norm and get divided; an infinite entry (a hard constraint, R2b) is added as it is; a zero
  *     norm makes the finite entries' terms 0.
+ *  R8 Parallel (flooding) schedule, the other branch of Algorithm 1: iteration t computes every
+ *     m_{c->v} from the m_{v->c} of iteration t-1 (the priors at t = 1), with R2's rule, then every
+ *     posterior L_v and every m_{v->c} from those m_{c->v}, with R3's sums in the same order. With
+ *     FP16 storage the m_{v->c} are rounded to binary16 when stored; the m_{c->v} of an iteration
+ *     are float temporaries.
  *  R7 LSD (Sec. III.C): columns ranked by soft value ascending, ties by index; one cluster per flipped
  *     check; in each round every cluster whose syndrome is outside the span of its columns adds its
  *     best-ranked adjacent free column together with all that column's checks; clusters sharing a
@@ -149,6 +154,69 @@ static void sweep_f64(const graph* g, const uint32_t* perm, const uint8_t* s, co
       double a = lam[v];
       for (int k2 = 0; k2 < deg; ++k2)
         if (k2 != k) a = a + mcv[k2];
+      msg[g->col_edge[b + k]] = a;
+    }
+    post[v] = L;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* One parallel (flooding) iteration of Algorithm 1 (R2, R8). c2v: E temporaries (CSR order).  */
+/* ------------------------------------------------------------------------------------------ */
+static void flood_f32(const graph* g, const uint8_t* s, const float* lam, float alpha, int fp16, float* msg,
+                      float* c2v, float* post) {
+  for (int c = 0; c < g->m; ++c)            /* every check-to-variable message, old messages only */
+    for (int own = g->rowptr[c]; own < g->rowptr[c + 1]; ++own) {
+      int neg = s[c];
+      float mn = INFINITY;
+      for (int e = g->rowptr[c]; e < g->rowptr[c + 1]; ++e) {
+        if (e == own) continue;
+        float x = msg[e];
+        if (x < 0.0f) neg ^= 1;
+        float ax = fabsf(x);
+        if (ax < mn) mn = ax;
+      }
+      float mag = alpha * mn;
+      c2v[own] = neg ? -mag : mag;
+    }
+  for (int v = 0; v < g->n; ++v) {          /* every posterior and variable-to-check message */
+    int b = g->colptr[v], deg = g->colptr[v + 1] - b;
+    float L = lam[v];
+    for (int k = 0; k < deg; ++k) L = L + c2v[g->col_edge[b + k]];
+    for (int k = 0; k < deg; ++k) {
+      float a = lam[v];
+      for (int k2 = 0; k2 < deg; ++k2)
+        if (k2 != k) a = a + c2v[g->col_edge[b + k2]];
+      msg[g->col_edge[b + k]] = store_msg(a, fp16);
+    }
+    post[v] = L;
+  }
+}
+
+static void flood_f64(const graph* g, const uint8_t* s, const double* lam, double alpha, double* msg,
+                      double* c2v, double* post) {
+  for (int c = 0; c < g->m; ++c)
+    for (int own = g->rowptr[c]; own < g->rowptr[c + 1]; ++own) {
+      int neg = s[c];
+      double mn = INFINITY;
+      for (int e = g->rowptr[c]; e < g->rowptr[c + 1]; ++e) {
+        if (e == own) continue;
+        double x = msg[e];
+        if (x < 0.0) neg ^= 1;
+        double ax = fabs(x);
+        if (ax < mn) mn = ax;
+      }
+      double mag = alpha * mn;
+      c2v[own] = neg ? -mag : mag;
+    }
+  for (int v = 0; v < g->n; ++v) {
+    int b = g->colptr[v], deg = g->colptr[v + 1] - b;
+    double L = lam[v];
+    for (int k = 0; k < deg; ++k) L = L + c2v[g->col_edge[b + k]];
+    for (int k = 0; k < deg; ++k) {
+      double a = lam[v];
+      for (int k2 = 0; k2 < deg; ++k2)
+        if (k2 != k) a = a + c2v[g->col_edge[b + k2]];
       msg[g->col_edge[b + k]] = a;
     }
     post[v] = L;
@@ -597,6 +665,39 @@ int32_t or_bp_member(const or_problem* P, const uint8_t* syndrome, const uint32_
     if (posterior) posterior[j] = L;
     if (ebits) ebits[j] = (uint8_t)(L <= 0.0);
   }
+  ws_free(&w);
+  return conv;
+}
+
+int32_t or_bp_member_flood(const or_problem* P, const uint8_t* syndrome, int32_t T, float alpha, int32_t mode,
+                           int32_t early_stop, double* posterior, uint8_t* ebits) {
+  workspace w;
+  ws_init(&w, P, 1, mode);
+  memcpy(w.s, syndrome, (size_t)P->m);
+  init_member(&w, 0);
+  const size_t E = (size_t)w.g.E > 0 ? (size_t)w.g.E : 1;
+  float* c2v32 = (float*)malloc(sizeof(float) * E);
+  double* c2v64 = (double*)malloc(sizeof(double) * E);
+  int conv = 0;
+  for (int t = 1; t <= T; ++t) {
+    int ok;
+    if (mode == OR_FP64) {
+      flood_f64(&w.g, w.s, w.lam64, (double)alpha, w.msg64, c2v64, w.post64);
+      ok = satisfies_f64(&w.g, w.s, w.post64);
+    } else {
+      flood_f32(&w.g, w.s, w.lam32, alpha, mode == OR_FP16MSG, w.msg32, c2v32, w.post32);
+      ok = satisfies_f32(&w.g, w.s, w.post32);
+    }
+    if (ok && !conv) conv = t;
+    if (ok && early_stop) break;
+  }
+  for (int j = 0; j < P->n; ++j) {
+    double L = mode == OR_FP64 ? w.post64[j] : (double)w.post32[j];
+    if (posterior) posterior[j] = L;
+    if (ebits) ebits[j] = (uint8_t)(L <= 0.0);
+  }
+  free(c2v32);
+  free(c2v64);
   ws_free(&w);
   return conv;
 }

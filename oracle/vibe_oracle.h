@@ -62,6 +62,11 @@ int32_t or_bp_member(const or_problem* P, const uint8_t* syndrome, const uint32_
                      int32_t T, float alpha, int32_t mode, int32_t early_stop, double* posterior,
                      uint8_t* ebits);
 
+/* One parallel (flooding) min-sum BP member (Algorithm 1, parallel branch; reading R8): same
+ * inputs and outputs as or_bp_member without a permutation. */
+int32_t or_bp_member_flood(const or_problem* P, const uint8_t* syndrome, int32_t T, float alpha, int32_t mode,
+                           int32_t early_stop, double* posterior, uint8_t* ebits);
+
 /* Full VibeLSD on B shots. syndromes: uint32[B][ceil(m/32)] bit-packed; perms uint32[K][n].
  * Outputs (any may be NULL except corrections): corrections uint32[B][ceil(n/32)],
  * logical uint32[B][ceil(k/32)], stats[B], soft double[B][n] (posterior of the chosen member, or the

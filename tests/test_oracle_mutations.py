@@ -38,6 +38,17 @@ MUTATIONS = {
 
 PIN_SUITES = ["tests/test_oracle_bp.py", "tests/test_oracle_decoder.py", "tests/test_oracle_lsd.py"]
 
+# mistakes in the parallel-schedule (flooding) member, run against its own pins
+FLOOD_MUTATIONS = {
+    "flooding posterior without the prior": ("    float L = lam[v];\n    for (int k = 0; k < deg; ++k) L = L + c2v[",
+                                             "    float L = 0.0f;\n    for (int k = 0; k < deg; ++k) L = L + c2v["),
+    "flooding own message kept in the exclusion sum": ("        if (k2 != k) a = a + c2v[g->col_edge[b + k2]];\n      msg[g->col_edge[b + k]] = store_msg",
+                                                       "        a = a + c2v[g->col_edge[b + k2]];\n      msg[g->col_edge[b + k]] = store_msg"),
+    "flooding uses messages of the same iteration": ("      c2v[own] = neg ? -mag : mag;\n    }\n  for (int v = 0; v < g->n; ++v) {          /* every posterior and variable-to-check message */\n    int b = g->colptr[v], deg = g->colptr[v + 1] - b;\n    float L",
+                                                     "      c2v[own] = neg ? -mag : mag;\n      msg[own] = lam[g->edge_col[own]] + c2v[own];\n    }\n  for (int v = 0; v < g->n; ++v) {          /* every posterior and variable-to-check message */\n    int b = g->colptr[v], deg = g->colptr[v + 1] - b;\n    float L"),
+    "flooding scaling factor not applied": ("      float mag = alpha * mn;\n      c2v[own]", "      float mag = mn;\n      c2v[own]"),
+}
+
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(name, tmp_path):
@@ -48,4 +59,16 @@ def test_planted_mistake_is_caught(name, tmp_path):
     env = dict(os.environ, VIBE_ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PIN_SUITES],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(FLOOD_MUTATIONS))
+def test_planted_flooding_mistake_is_caught(name, tmp_path):
+    old, new = FLOOD_MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) >= 1, f"mutation site not found: {name}"
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_mut.so"))
+    env = dict(os.environ, VIBE_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_flood.py"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
