@@ -15,6 +15,7 @@
  *     left folds in ascending check index (the literal formula of Algorithm 1).
  *  R4 e_v = 1 iff L_v <= 0; a member converges at the first iteration t whose e satisfies H e = s.
  *  R5 Members run in lock step; after iteration t, once M members have converged the rest stop.
+ *     (Members 0 .. n_flood-1 may run the parallel schedule of R8; the rule is the same.)
  *     The candidates are the first min(M, #converged) members in (t, member) order; the chosen one
  *     minimises W(e) = sum_{e_j = 1} lambda_j (float left fold, ascending j), ties to the earlier.
  *  R2b A check of degree 1 has an empty N(c)\v: its minimum is +inf and its sign product +1, so it
@@ -253,6 +254,7 @@ typedef struct {
   float* msg32; double* msg64;     /* K * E */
   float* post32; double* post64;   /* K * n */
   float* mcv32; double* mcv64;     /* maxcol */
+  float* c2v32; double* c2v64;     /* E: check-to-variable temporaries of a flooding iteration */
   int32_t* conv_t;                 /* K */
   uint8_t* s;                      /* m */
   uint8_t* ebits;                  /* n */
@@ -287,6 +289,8 @@ static void ws_init(workspace* w, const or_problem* P, int K, int mode) {
   }
   w->mcv32 = (float*)malloc(sizeof(float) * (size_t)(w->g.maxcol + 1));
   w->mcv64 = (double*)malloc(sizeof(double) * (size_t)(w->g.maxcol + 1));
+  w->c2v32 = (float*)malloc(sizeof(float) * (size_t)(w->g.E + 1));
+  w->c2v64 = (double*)malloc(sizeof(double) * (size_t)(w->g.E + 1));
   w->conv_t = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
   w->s = (uint8_t*)malloc((size_t)m + 1);
   w->ebits = (uint8_t*)malloc((size_t)n + 1);
@@ -307,7 +311,7 @@ static void ws_init(workspace* w, const or_problem* P, int K, int mode) {
 static void ws_free(workspace* w) {
   graph_free(&w->g);
   free(w->lam32); free(w->lam64); free(w->msg32); free(w->msg64); free(w->post32); free(w->post64);
-  free(w->mcv32); free(w->mcv64); free(w->conv_t); free(w->s); free(w->ebits); free(w->soft);
+  free(w->mcv32); free(w->mcv64); free(w->c2v32); free(w->c2v64); free(w->conv_t); free(w->s); free(w->ebits); free(w->soft);
   free(w->ck_par); free(w->col_root); free(w->roots); free(w->picks); free(w->cl_checks);
   free(w->cl_cols); free(w->tmp); free(w->mat); free(w->pivrow); free(w->x); free(w->xbest); free(w->asc);
 }
@@ -525,12 +529,20 @@ static void decode_one(workspace* w, const uint32_t* perms, const or_params* prm
       const uint32_t* perm = perms + (size_t)i * n;
       int ok;
       if (fp64) {
-        sweep_f64(g, perm, w->s, w->lam64, (double)prm->alpha, w->msg64 + (size_t)i * g->E,
-                  w->post64 + (size_t)i * n, w->mcv64);
+        if (i < prm->n_flood)
+          flood_f64(g, w->s, w->lam64, (double)prm->alpha, w->msg64 + (size_t)i * g->E, w->c2v64,
+                    w->post64 + (size_t)i * n);
+        else
+          sweep_f64(g, perm, w->s, w->lam64, (double)prm->alpha, w->msg64 + (size_t)i * g->E,
+                    w->post64 + (size_t)i * n, w->mcv64);
         ok = satisfies_f64(g, w->s, w->post64 + (size_t)i * n);
       } else {
-        sweep_f32(g, perm, w->s, w->lam32, prm->alpha, fp16, w->msg32 + (size_t)i * g->E,
-                  w->post32 + (size_t)i * n, w->mcv32);
+        if (i < prm->n_flood)
+          flood_f32(g, w->s, w->lam32, prm->alpha, fp16, w->msg32 + (size_t)i * g->E, w->c2v32,
+                    w->post32 + (size_t)i * n);
+        else
+          sweep_f32(g, perm, w->s, w->lam32, prm->alpha, fp16, w->msg32 + (size_t)i * g->E,
+                    w->post32 + (size_t)i * n, w->mcv32);
         ok = satisfies_f32(g, w->s, w->post32 + (size_t)i * n);
       }
       if (ok) { w->conv_t[i] = t; ++nconv; }
@@ -675,9 +687,8 @@ int32_t or_bp_member_flood(const or_problem* P, const uint8_t* syndrome, int32_t
   ws_init(&w, P, 1, mode);
   memcpy(w.s, syndrome, (size_t)P->m);
   init_member(&w, 0);
-  const size_t E = (size_t)w.g.E > 0 ? (size_t)w.g.E : 1;
-  float* c2v32 = (float*)malloc(sizeof(float) * E);
-  double* c2v64 = (double*)malloc(sizeof(double) * E);
+  float* c2v32 = w.c2v32;
+  double* c2v64 = w.c2v64;
   int conv = 0;
   for (int t = 1; t <= T; ++t) {
     int ok;
@@ -696,8 +707,6 @@ int32_t or_bp_member_flood(const or_problem* P, const uint8_t* syndrome, int32_t
     if (posterior) posterior[j] = L;
     if (ebits) ebits[j] = (uint8_t)(L <= 0.0);
   }
-  free(c2v32);
-  free(c2v64);
   ws_free(&w);
   return conv;
 }

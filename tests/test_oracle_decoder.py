@@ -70,24 +70,26 @@ def test_zero_syndrome():
     assert (st["chosen_member"] == 0).all() and (st["lsd_invoked"] == 0).all()
 
 
-def _members(dm, perms, s, T, mode):
-    runs = [oracle.bp_member(dm, s, p, T, 0.625, mode) for p in perms]
+def _members(dm, perms, s, T, mode, n_flood=0):
+    runs = [oracle.bp_member_flood(dm, s, T, 0.625, mode) if i < n_flood else oracle.bp_member(dm, s, p, T, 0.625, mode)
+            for i, p in enumerate(perms)]
     return [r[0] for r in runs], [r[1] for r in runs], [r[2] for r in runs]
 
 
-@pytest.mark.parametrize("mode", [oracle.FP32, oracle.FP16MSG])
-def test_correction_limit_and_ranking_from_independent_members(mode):
+@pytest.mark.parametrize("mode,n_flood", [(oracle.FP32, 0), (oracle.FP16MSG, 0), (oracle.FP32, 4)])
+def test_correction_limit_and_ranking_from_independent_members(mode, n_flood):
+    """n_flood > 0: a mixed ensemble whose first members run the parallel schedule (reading R8)."""
     dm = D.build_workload("cc666_d9_pheno")
     K, M, T = 16, 5, 30
     perms = D.schedules(dm.n, K, 2)
     syn, _ = D.sample(dm, 40, 21)
-    out = oracle.decode(dm, perms, syn, T, 0.625, M, mode=mode)
+    out = oracle.decode(dm, perms, syn, T, 0.625, M, mode=mode, n_flood=n_flood)
     l32, _ = oracle.prior_llr(dm.priors)
     st = out["stats"]
     seen_bp = 0
     for b in range(len(syn)):
         s = D.unpack_bits(syn[b:b + 1], dm.m)[0]
-        tconv, posts, ebits = _members(dm, perms, s, T, mode)
+        tconv, posts, ebits = _members(dm, perms, s, T, mode, n_flood)
         conv = sorted((t, i) for i, t in enumerate(tconv) if t > 0)
         cand = conv[:M]
         if not cand:
