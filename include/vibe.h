@@ -60,6 +60,10 @@ typedef struct {
   int32_t msg_fp16;  /* 0: FP32 messages; 1: FP16 storage of variable-to-check messages, FP32 arithmetic */
   uint64_t seed;     /* seeds the schedules when vibe_create gets schedules == NULL */
   int32_t bp_engine; /* BP kernel: VIBE_ENGINE_AUTO, _IMAGE or _SUMMARY (same results) */
+  int32_t n_flood;   /* members 0 .. n_flood-1 use Algorithm 1's parallel (flooding) schedule instead of
+                        a serial one (their schedules are ignored); 0 <= n_flood <= K. Supported on the
+                        image engine with FP32 messages; otherwise vibe_create returns
+                        VIBE_ERR_UNSUPPORTED */
 } vibe_params;
 
 /* BP engines; both run one warp per shot and give the same bits. IMAGE: the member's whole message

@@ -384,7 +384,12 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   if (p->lsd_order < 0 || p->lsd_order > 10) return fail(VIBE_ERR_INVALID, "lsd_order must be in 0..10");
   if (p->msg_fp16 != 0 && p->msg_fp16 != 1) return fail(VIBE_ERR_INVALID, "msg_fp16 must be 0 or 1");
   if (p->bp_engine < VIBE_ENGINE_AUTO || p->bp_engine > VIBE_ENGINE_SUMMARY)
-    return fail(VIBE_ERR_INVALID, "bp_engine must be VIBE_ENGINE_AUTO, _WARP or _CTA");
+    return fail(VIBE_ERR_INVALID, "bp_engine must be VIBE_ENGINE_AUTO, _IMAGE or _SUMMARY");
+  if (p->n_flood < 0 || p->n_flood > K) return fail(VIBE_ERR_INVALID, "n_flood must be in 0..K");
+  if (p->n_flood > 0 && p->msg_fp16)
+    return fail(VIBE_ERR_UNSUPPORTED, "flooding members run with FP32 messages only");
+  if (p->n_flood > 0 && p->bp_engine == VIBE_ENGINE_SUMMARY)
+    return fail(VIBE_ERR_UNSUPPORTED, "flooding members run on the image engine only");
   for (int j = 0; j < n; ++j)
     if (!(priors[j] > 0.0 && priors[j] < 0.5)) return fail(VIBE_ERR_INVALID, "prior %d = %g outside (0, 0.5)", j, priors[j]);
   if (n >= (1 << 23)) return fail(VIBE_ERR_UNSUPPORTED, "n must be below 2^23");
@@ -425,7 +430,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   t.RP = std::max(8, (maxrow + 7) / 8 * 8);
   t.DP = maxcol <= 4 ? 4 : maxcol <= 8 ? 8 : maxcol <= 16 ? 16 : 32;
   t.mw = (m + 31) / 32; t.nw = (n + 31) / 32; t.kw = (k + 31) / 32; t.W = t.mw;
-  t.T = p->max_iter; t.M = p->M; t.lsd_order = p->lsd_order; t.alpha = p->alpha;
+  t.T = p->max_iter; t.M = p->M; t.lsd_order = p->lsd_order; t.alpha = p->alpha; t.n_flood = p->n_flood;
   vibe::bp_warp_smem_bytes(&t, p->msg_fp16);
   t.x_packed = m < kBytesLayoutChecks ? 1 : 0;
   vibe::bpx_layout(&t, p->msg_fp16);
@@ -438,8 +443,11 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
     const Bounds bw = bounds_over(&t, 1);
     t.engine = VIBE_ENGINE_SUMMARY;
     if (vibe::bp_cta_smem_bytes(bw, 0) <= (size_t)optin &&
-        vibe::bp_occupancy(bw, 0, p->msg_fp16, &blocks) == cudaSuccess && blocks * vibe::kBpWarpsPerCta >= 8)
+        vibe::bp_occupancy(bw, 0, p->msg_fp16, &blocks) == cudaSuccess &&
+        (blocks * vibe::kBpWarpsPerCta >= 8 || (p->n_flood > 0 && blocks >= 1)))
       t.engine = VIBE_ENGINE_IMAGE;
+    if (p->n_flood > 0 && t.engine != VIBE_ENGINE_IMAGE)
+      return bail(fail(VIBE_ERR_UNSUPPORTED, "flooding members need the image engine; the message image does not fit"));
   }
   const int Lnnz = L->rowptr[k];
   const size_t msg_bytes = (size_t)m * t.RP * (p->msg_fp16 ? 2 : 4);
@@ -614,6 +622,8 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
 // Moves handle h to BP engine `engine` and, for the summary engine, state layout `packed` (descriptor
 // on the device, bounds, launch sizes); the handle is unchanged if the engine cannot run this problem.
 static int set_engine(vibe_handle* h, int engine, int packed) {
+  if (engine == VIBE_ENGINE_SUMMARY && h->t.n_flood > 0)
+    return fail(VIBE_ERR_UNSUPPORTED, "flooding members run on the image engine only");
   Tables t = h->t;
   t.engine = engine;
   t.x_packed = packed;

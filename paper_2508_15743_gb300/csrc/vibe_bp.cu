@@ -143,6 +143,86 @@ __device__ __forceinline__ void update_column(uint32_t v, int deg, const uint32_
   if (lpost) lpost[v] = L;
 }
 
+// One parallel (flooding) iteration of Algorithm 1 on the warp's FP32 message image.
+// Check pass: a lane takes whole rows; from the smallest magnitude, the second smallest, the slot
+// holding the smallest and the sign parity of the row's variable-to-check messages it overwrites each
+// real slot with that edge's check-to-variable message (minimum and sign product over the other
+// slots: exactly the exclusion over N(c) \ v). Column pass: a lane takes whole columns and turns its
+// own slots into the new variable-to-check messages with the sums of the serial update. Every column
+// reads only its own slots, so the passes need no second image. Parity pass: (H e)_c XOR s_c from
+// the decisions (many columns touch a check in the column pass).
+template <int DP>
+__device__ __forceinline__ void flood_sweep(const Tables& t, float* msgs, uint8_t* dec8, const uint8_t* s8,
+                                            uint8_t* par8, float* lpost, int lane) {
+  const int m = t.m, n = t.n;
+  const uint32_t RP = (uint32_t)t.RP;
+  const float alpha = t.alpha;
+  for (int c = lane; c < m; c += 32) {
+    const int deg = __ldg(t.rowptr + c + 1) - __ldg(t.rowptr + c);
+    float* row = msgs + (size_t)c * RP;
+    float m1 = __int_as_float(0x7f800000), m2 = m1;
+    int a1 = -1;
+    uint32_t sx = 0;
+    for (int j = 0; j < deg; ++j) {
+      const float x = row[row_position((uint32_t)c, (uint32_t)j, (int)RP, 4)];
+      const float ax = fabsf(x);
+      sx ^= __float_as_uint(x) >> 31;
+      if (ax < m1) { m2 = m1; m1 = ax; a1 = j; }
+      else if (ax < m2) m2 = ax;
+    }
+    for (int j = 0; j < deg; ++j) {
+      const uint32_t pos = row_position((uint32_t)c, (uint32_t)j, (int)RP, 4);
+      const float x = row[pos];
+      const float mn = j == a1 ? m2 : m1;
+      const uint32_t neg = (sx ^ (__float_as_uint(x) >> 31) ^ (uint32_t)s8[c]) & 1u;
+      const float mag = __fmul_rn(alpha, mn);
+      row[pos] = neg ? -mag : mag;
+    }
+  }
+  __syncwarp();
+  for (int v = lane; v < n; v += 32) {
+    const int deg = __ldg(t.colptr + v + 1) - __ldg(t.colptr + v);
+    float* slot[DP];
+    float cv[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      slot[k] = msgs;
+      cv[k] = 0.0f;
+      if (k < deg) {
+        const uint32_t ent = __ldg(t.csc_ent + (size_t)v * t.DP + k);
+        slot[k] = msgs + (size_t)(ent >> 9) * RP + (ent & 0xffu);
+        cv[k] = *slot[k];
+      }
+    }
+    const float lamv = __ldg(t.lam + v);
+    float L = lamv;
+#pragma unroll
+    for (int k = 0; k < DP; ++k)
+      if (k < deg) L = __fadd_rn(L, cv[k]);
+    float pre = lamv;   // lambda + m_0 + ... + m_{k-1}, the shared head of every exclusion sum
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      if (k < deg) {
+        float a = pre;
+#pragma unroll
+        for (int k2 = k + 1; k2 < DP; ++k2)
+          if (k2 < deg) a = __fadd_rn(a, cv[k2]);
+        *slot[k] = a;
+        pre = __fadd_rn(pre, cv[k]);
+      }
+    }
+    dec8[v] = L <= 0.0f ? 1u : 0u;
+    if (lpost) lpost[v] = L;
+  }
+  __syncwarp();
+  for (int c = lane; c < m; c += 32) {
+    uint32_t p = s8[c];
+    for (int e = __ldg(t.rowptr + c); e < __ldg(t.rowptr + c + 1); ++e) p ^= dec8[__ldg(t.colidx + e)];
+    par8[c] = (uint8_t)p;
+  }
+  __syncwarp();
+}
+
 // Blocks per SM the register budget targets: FP16 states are small enough for 24 warps per SM,
 // FP32 states (twice the message bytes) fill shared memory at about 16-18.
 template <typename MT>
@@ -231,7 +311,14 @@ __device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, ui
       // the posterior is needed after the last possible sweep of a member that may end without
       // converging (LLR average) and, for soft output, after every sweep
       float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
-      for (int l = 0; l < nl; ++l) {
+      bool flooded = false;
+      if constexpr (std::is_same<MT, float>::value) {
+        if (i < t.n_flood) {   // parallel schedule (the host allows it with FP32 messages only)
+          flood_sweep<DP>(t, msgs, dec8, s8, par8, lp, lane);
+          flooded = true;
+        }
+      }
+      for (int l = 0; l < nl && !flooded; ++l) {
         const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
         for (uint32_t idx = b + lane; idx < e; idx += 32) {
           const uint32_t ent = __ldg(sch + idx);

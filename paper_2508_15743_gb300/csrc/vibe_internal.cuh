@@ -45,6 +45,7 @@ struct Tables {
   int mw, nw, kw;
   int W;         // words of a bit vector over the checks: ceil(m/32)
   int T, M, lsd_order;
+  int n_flood;   // members 0 .. n_flood-1 run the parallel (flooding) schedule
   float alpha;
   int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // image engine: per-warp shared memory, bytes
   int engine;    // VIBE_ENGINE_IMAGE or VIBE_ENGINE_SUMMARY
