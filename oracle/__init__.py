@@ -50,7 +50,8 @@ class _Problem(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("alpha", ctypes.c_float), ("M", ctypes.c_int32),
-                ("lsd_order", ctypes.c_int32), ("mode", ctypes.c_int32), ("n_flood", ctypes.c_int32)]
+                ("lsd_order", ctypes.c_int32), ("mode", ctypes.c_int32), ("n_flood", ctypes.c_int32),
+                ("member_alpha", ctypes.c_void_p)]
 
 
 def _bind(path):
@@ -153,8 +154,11 @@ def bp_member(dem, syndrome_bits, perm, T, alpha, mode=FP32, early_stop=True):
     return int(t), post, eb
 
 
-def decode(dem, perms, syndromes, T, alpha, M, lsd_order=0, mode=FP32, nthreads=1, want_soft=True, n_flood=0):
+def decode(dem, perms, syndromes, T, alpha, M, lsd_order=0, mode=FP32, nthreads=1, want_soft=True, n_flood=0,
+           member_alpha=None):
     """Full VibeLSD on packed syndromes uint32 [B, ceil(m/32)] with schedules uint32 [K, n].
+
+    member_alpha: None, or K scaling factors, member i using member_alpha[i] instead of alpha.
 
     Returns dict(corrections uint32 [B, ceil(n/32)], logical uint32 [B, ceil(k/32)], stats, soft f64 [B, n]).
     """
@@ -168,7 +172,11 @@ def decode(dem, perms, syndromes, T, alpha, M, lsd_order=0, mode=FP32, nthreads=
     logi = np.zeros((B, (P.k + 31) // 32), np.uint32)
     stats = np.zeros(B, STATS_DTYPE)
     soft = np.zeros((B, P.n), np.float64) if want_soft else None
-    prm = _Params(int(T), float(alpha), int(M), int(lsd_order), int(mode), int(n_flood))
+    ma = None if member_alpha is None else np.ascontiguousarray(member_alpha, dtype=np.float32)
+    if ma is not None and ma.shape != (K,):
+        raise ValueError("member_alpha needs one factor per member")
+    prm = _Params(int(T), float(alpha), int(M), int(lsd_order), int(mode), int(n_flood),
+                  None if ma is None else ma.ctypes.data)
     rc = lib.or_decode(ctypes.byref(P.c), K, _ptr(perms), ctypes.byref(prm), B, _ptr(syn), _ptr(corr),
                        _ptr(logi), _ptr(stats), _ptr(soft), int(nthreads))
     if rc != 0:

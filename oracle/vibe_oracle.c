@@ -30,6 +30,8 @@
  *     posterior L_v and every m_{v->c} from those m_{c->v}, with R3's sums in the same order. With
  *     FP16 storage the m_{v->c} are rounded to binary16 when stored; the m_{c->v} of an iteration
  *     are float temporaries.
+ *  R9 Ensembles mixing heuristics (Sec. V names combining heuristics across the ensemble): a member
+ *     may carry its own scaling factor alpha_i; the rest of Algorithm 1 and R5 are unchanged.
  *  R7 LSD (Sec. III.C): columns ranked by soft value ascending, ties by index; one cluster per flipped
  *     check; in each round every cluster whose syndrome is outside the span of its columns adds its
  *     best-ranked adjacent free column together with all that column's checks; clusters sharing a
@@ -527,21 +529,22 @@ static void decode_one(workspace* w, const uint32_t* perms, const or_params* prm
     for (int i = 0; i < K; ++i) {
       if (w->conv_t[i]) continue;
       const uint32_t* perm = perms + (size_t)i * n;
+      const float alpha = prm->member_alpha ? prm->member_alpha[i] : prm->alpha;
       int ok;
       if (fp64) {
         if (i < prm->n_flood)
-          flood_f64(g, w->s, w->lam64, (double)prm->alpha, w->msg64 + (size_t)i * g->E, w->c2v64,
+          flood_f64(g, w->s, w->lam64, (double)alpha, w->msg64 + (size_t)i * g->E, w->c2v64,
                     w->post64 + (size_t)i * n);
         else
-          sweep_f64(g, perm, w->s, w->lam64, (double)prm->alpha, w->msg64 + (size_t)i * g->E,
+          sweep_f64(g, perm, w->s, w->lam64, (double)alpha, w->msg64 + (size_t)i * g->E,
                     w->post64 + (size_t)i * n, w->mcv64);
         ok = satisfies_f64(g, w->s, w->post64 + (size_t)i * n);
       } else {
         if (i < prm->n_flood)
-          flood_f32(g, w->s, w->lam32, prm->alpha, fp16, w->msg32 + (size_t)i * g->E, w->c2v32,
+          flood_f32(g, w->s, w->lam32, alpha, fp16, w->msg32 + (size_t)i * g->E, w->c2v32,
                     w->post32 + (size_t)i * n);
         else
-          sweep_f32(g, perm, w->s, w->lam32, prm->alpha, fp16, w->msg32 + (size_t)i * g->E,
+          sweep_f32(g, perm, w->s, w->lam32, alpha, fp16, w->msg32 + (size_t)i * g->E,
                     w->post32 + (size_t)i * n, w->mcv32);
         ok = satisfies_f32(g, w->s, w->post32 + (size_t)i * n);
       }

@@ -51,6 +51,8 @@ typedef struct {
   int32_t mode;       /* OR_FP32, OR_FP16MSG or OR_FP64 */
   int32_t n_flood;    /* members 0 .. n_flood-1 use the parallel (flooding) schedule (R8), the rest
                          the serial one; their permutations are not used */
+  const float* member_alpha;  /* NULL, or K factors: member i scales its check messages by
+                                 member_alpha[i] instead of alpha (R9) */
 } or_params;
 
 /* Prior LLRs lambda_j = log((1 - p_j)/p_j) evaluated in double; lam32 gets the float rounding. */

@@ -70,26 +70,34 @@ def test_zero_syndrome():
     assert (st["chosen_member"] == 0).all() and (st["lsd_invoked"] == 0).all()
 
 
-def _members(dm, perms, s, T, mode, n_flood=0):
-    runs = [oracle.bp_member_flood(dm, s, T, 0.625, mode) if i < n_flood else oracle.bp_member(dm, s, p, T, 0.625, mode)
+def _members(dm, perms, s, T, mode, n_flood=0, alphas=None):
+    al = [0.625] * len(perms) if alphas is None else [float(np.float32(a)) for a in alphas]
+    runs = [oracle.bp_member_flood(dm, s, T, al[i], mode) if i < n_flood else oracle.bp_member(dm, s, p, T, al[i], mode)
             for i, p in enumerate(perms)]
     return [r[0] for r in runs], [r[1] for r in runs], [r[2] for r in runs]
 
 
-@pytest.mark.parametrize("mode,n_flood", [(oracle.FP32, 0), (oracle.FP16MSG, 0), (oracle.FP32, 4)])
-def test_correction_limit_and_ranking_from_independent_members(mode, n_flood):
-    """n_flood > 0: a mixed ensemble whose first members run the parallel schedule (reading R8)."""
+# members differing in the scaling factor (reading R9), 16 members
+MEMBER_ALPHA = np.array([0.5, 0.625, 0.75, 1.0, 0.875, 0.5625, 0.6875, 0.8125] * 2, np.float32)
+
+
+@pytest.mark.parametrize("mode,n_flood,alphas", [(oracle.FP32, 0, None), (oracle.FP16MSG, 0, None),
+                                                 (oracle.FP32, 4, None), (oracle.FP32, 0, MEMBER_ALPHA),
+                                                 (oracle.FP32, 4, MEMBER_ALPHA), (oracle.FP16MSG, 0, MEMBER_ALPHA)])
+def test_correction_limit_and_ranking_from_independent_members(mode, n_flood, alphas):
+    """n_flood > 0: a mixed ensemble whose first members run the parallel schedule (reading R8);
+    alphas: member i scales its check messages by alphas[i] (reading R9)."""
     dm = D.build_workload("cc666_d9_pheno")
     K, M, T = 16, 5, 30
     perms = D.schedules(dm.n, K, 2)
     syn, _ = D.sample(dm, 40, 21)
-    out = oracle.decode(dm, perms, syn, T, 0.625, M, mode=mode, n_flood=n_flood)
+    out = oracle.decode(dm, perms, syn, T, 0.625, M, mode=mode, n_flood=n_flood, member_alpha=alphas)
     l32, _ = oracle.prior_llr(dm.priors)
     st = out["stats"]
     seen_bp = 0
     for b in range(len(syn)):
         s = D.unpack_bits(syn[b:b + 1], dm.m)[0]
-        tconv, posts, ebits = _members(dm, perms, s, T, mode, n_flood)
+        tconv, posts, ebits = _members(dm, perms, s, T, mode, n_flood, alphas)
         conv = sorted((t, i) for i, t in enumerate(tconv) if t > 0)
         cand = conv[:M]
         if not cand:
@@ -144,20 +152,21 @@ def _canonical_norm_f32(x):
     return np.float32(np.sqrt(part[0]))
 
 
-def test_llr_average_matches_numpy_and_float32_replay():
+@pytest.mark.parametrize("alphas", [None, np.array([1.0, 0.5, 0.625, 0.75], np.float32)])
+def test_llr_average_matches_numpy_and_float32_replay(alphas):
     dm = D.build_workload("cc666_d9_pheno")
     K, M, T = 4, 2, 6
     perms = D.schedules(dm.n, K, 8)
     syn, _ = D.sample(dm, 60, 33)
-    out32 = oracle.decode(dm, perms, syn, T, 0.625, M, mode=oracle.FP32)
-    out64 = oracle.decode(dm, perms, syn, T, 0.625, M, mode=oracle.FP64)
+    out32 = oracle.decode(dm, perms, syn, T, 0.625, M, mode=oracle.FP32, member_alpha=alphas)
+    out64 = oracle.decode(dm, perms, syn, T, 0.625, M, mode=oracle.FP64, member_alpha=alphas)
     checked = 0
     for b in range(len(syn)):
         if out32["stats"]["lsd_invoked"][b] != 1:
             continue
         s = D.unpack_bits(syn[b:b + 1], dm.m)[0]
         # FP32: replay the documented order in float32
-        _, posts, _ = _members(dm, perms, s, T, oracle.FP32)
+        _, posts, _ = _members(dm, perms, s, T, oracle.FP32, alphas=alphas)
         acc = np.zeros(dm.n, np.float32)
         for p in posts:
             p = p.astype(np.float32)
@@ -169,7 +178,7 @@ def test_llr_average_matches_numpy_and_float32_replay():
         assert np.array_equal(out32["soft"][b].astype(np.float32), ref)
         # FP64 mode: the displayed formula in numpy (finite entries normalised)
         if out64["stats"]["lsd_invoked"][b] == 1:
-            _, posts64, _ = _members(dm, perms, s, T, oracle.FP64)
+            _, posts64, _ = _members(dm, perms, s, T, oracle.FP64, alphas=alphas)
             tot = np.zeros(dm.n)
             for p in posts64:
                 fin = np.isfinite(p)
@@ -231,3 +240,16 @@ def test_logical_output_is_L_times_correction():
     out = oracle.decode(dm, perms, syn, 10, 0.625, 2)
     _, o = D.syndromes_of(dm, D.unpack_bits(out["corrections"], dm.n))
     assert np.array_equal(o, out["logical"])
+
+
+def test_equal_member_alphas_equal_the_shared_alpha():
+    dm = D.build_workload("cc666_d9_pheno")
+    perms = D.schedules(dm.n, 8, 3)
+    syn, _ = D.sample(dm, 80, 4)
+    a = oracle.decode(dm, perms, syn, 20, 0.75, 3, n_flood=2)
+    b = oracle.decode(dm, perms, syn, 20, 0.625, 3, n_flood=2, member_alpha=np.full(8, 0.75, np.float32))
+    for k in ["corrections", "logical", "soft"]:
+        assert np.array_equal(a[k], b[k])
+    assert np.array_equal(a["stats"], b["stats"])
+    with pytest.raises(ValueError):
+        oracle.decode(dm, perms, syn, 20, 0.625, 3, member_alpha=np.ones(7, np.float32))

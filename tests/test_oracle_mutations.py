@@ -72,3 +72,22 @@ def test_planted_flooding_mistake_is_caught(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "tests/test_oracle_flood.py"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
+
+
+MEMBER_ALPHA_MUTATIONS = {
+    "every member takes the first member's factor": ("prm->member_alpha ? prm->member_alpha[i] : prm->alpha",
+                                                     "prm->member_alpha ? prm->member_alpha[0] : prm->alpha"),
+    "member factors ignored": ("prm->member_alpha ? prm->member_alpha[i] : prm->alpha", "prm->alpha"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MEMBER_ALPHA_MUTATIONS))
+def test_planted_member_alpha_mistake_is_caught(name, tmp_path):
+    old, new = MEMBER_ALPHA_MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation site not found: {name}"
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_mut.so"))
+    env = dict(os.environ, VIBE_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_decoder.py"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
