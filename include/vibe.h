@@ -64,6 +64,10 @@ typedef struct {
                         a serial one (their schedules are ignored); 0 <= n_flood <= K. Supported on the
                         image engine with FP32 messages; otherwise vibe_create returns
                         VIBE_ERR_UNSUPPORTED */
+  const float* member_alpha; /* NULL, or K host floats in (0, 1] (copied): member i scales its
+                        check-to-variable messages by member_alpha[i] instead of alpha, an ensemble
+                        mixing heuristics (Sec. V); results, ranking and LLR average are otherwise
+                        unchanged. Both engines, all schedules and storage precisions */
 } vibe_params;
 
 /* BP engines; both run one warp per shot and give the same bits. IMAGE: the member's whole message

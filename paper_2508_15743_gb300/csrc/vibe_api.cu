@@ -297,6 +297,7 @@ struct vibe_handle {
   uint32_t *csc_ent = nullptr, *sched = nullptr, *lvl_off = nullptr, *perm = nullptr;
   uint2* sched_rec = nullptr;
   float* lam = nullptr;
+  float* alpha_m = nullptr;
   void* msg_init = nullptr;
   uint32_t* row_edge = nullptr;
   void* msg_csc = nullptr;
@@ -319,7 +320,7 @@ struct vibe_handle {
     release_stage();
     cudaFree(tmp_counters);
     cudaFree(rowptr); cudaFree(colidx); cudaFree(colptr); cudaFree(rowidx); cudaFree(lrowptr); cudaFree(lcolidx);
-    cudaFree(nlev); cudaFree(csc_ent); cudaFree(sched); cudaFree(lvl_off); cudaFree(perm); cudaFree(lam);
+    cudaFree(nlev); cudaFree(csc_ent); cudaFree(sched); cudaFree(lvl_off); cudaFree(perm); cudaFree(lam); cudaFree(alpha_m);
     cudaFree(msg_init); cudaFree(sched_rec); cudaFree(row_edge); cudaFree(msg_csc); cudaFree(sum_init); cudaFree(d_desc);
     cudaSetDevice(prev);
   }
@@ -390,6 +391,10 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
     return fail(VIBE_ERR_UNSUPPORTED, "flooding members run with FP32 messages only");
   if (p->n_flood > 0 && p->bp_engine == VIBE_ENGINE_SUMMARY)
     return fail(VIBE_ERR_UNSUPPORTED, "flooding members run on the image engine only");
+  if (p->member_alpha)
+    for (int i = 0; i < K; ++i)
+      if (!(p->member_alpha[i] > 0.f && p->member_alpha[i] <= 1.f))
+        return fail(VIBE_ERR_INVALID, "member_alpha[%d] must be in (0, 1]", i);
   for (int j = 0; j < n; ++j)
     if (!(priors[j] > 0.0 && priors[j] < 0.5)) return fail(VIBE_ERR_INVALID, "prior %d = %g outside (0, 0.5)", j, priors[j]);
   if (n >= (1 << 23)) return fail(VIBE_ERR_UNSUPPORTED, "n must be below 2^23");
@@ -470,6 +475,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   VIBE_TRY(dalloc(&h->lvl_off, (size_t)K * (n + 1)), "tables");
   VIBE_TRY(dalloc(&h->perm, (size_t)K * n), "tables");
   VIBE_TRY(dalloc(&h->lam, n), "tables");
+  VIBE_TRY(dalloc(&h->alpha_m, K), "tables");
   VIBE_TRY(cudaMalloc(&h->msg_init, std::max<size_t>(msg_bytes, 16)), "tables");
   VIBE_TRY(dalloc(&h->row_edge, E), "tables");
   VIBE_TRY(cudaMalloc(&h->msg_csc, ((size_t)E * (p->msg_fp16 ? 2 : 4) + 15) / 16 * 16 + 16), "tables");
@@ -483,6 +489,9 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   if (Lnnz > 0)
     VIBE_TRY(cudaMemcpyAsync(h->lcolidx, L->colidx, sizeof(int32_t) * Lnnz, cudaMemcpyHostToDevice, s), "upload");
   VIBE_TRY(cudaMemcpyAsync(h->lam, lam.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s), "upload");
+  std::vector<float> alpha_m(K, p->alpha);
+  if (p->member_alpha) std::copy(p->member_alpha, p->member_alpha + K, alpha_m.begin());
+  VIBE_TRY(cudaMemcpyAsync(h->alpha_m, alpha_m.data(), sizeof(float) * K, cudaMemcpyHostToDevice, s), "upload");
   if (schedules) {
     VIBE_TRY(cudaMemcpyAsync(h->perm, schedules, sizeof(uint32_t) * (size_t)K * n, cudaMemcpyHostToDevice, s), "upload");
   } else {
@@ -493,7 +502,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
                               h->msg_csc, h->sum_init, scratch, s),
            "graph builder");
   t.rowptr = h->rowptr; t.colidx = h->colidx; t.colptr = h->colptr; t.rowidx = h->rowidx;
-  t.csc_ent = h->csc_ent; t.lam = h->lam; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
+  t.csc_ent = h->csc_ent; t.lam = h->lam; t.alpha_m = h->alpha_m; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
   t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
   t.row_edge = h->row_edge; t.msg_csc = h->msg_csc; t.sum_init = h->sum_init; t.sched_rec = h->sched_rec;
   VIBE_TRY(cudaMemcpyAsync(h->d_desc, &t, sizeof(Tables), cudaMemcpyHostToDevice, s), "upload");

@@ -152,11 +152,10 @@ __device__ __forceinline__ void update_column(uint32_t v, int deg, const uint32_
 // reads only its own slots, so the passes need no second image. Parity pass: (H e)_c XOR s_c from
 // the decisions (many columns touch a check in the column pass).
 template <int DP>
-__device__ __forceinline__ void flood_sweep(const Tables& t, float* msgs, uint8_t* dec8, const uint8_t* s8,
-                                            uint8_t* par8, float* lpost, int lane) {
+__device__ __forceinline__ void flood_sweep(const Tables& t, float alpha, float* msgs, uint8_t* dec8,
+                                            const uint8_t* s8, uint8_t* par8, float* lpost, int lane) {
   const int m = t.m, n = t.n;
   const uint32_t RP = (uint32_t)t.RP;
-  const float alpha = t.alpha;
   for (int c = lane; c < m; c += 32) {
     const int deg = __ldg(t.rowptr + c + 1) - __ldg(t.rowptr + c);
     float* row = msgs + (size_t)c * RP;
@@ -244,7 +243,6 @@ __device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, ui
   const float* lam = t.lam;
   const int dp = MIXED ? t.DP : DP;   // one problem: the pitch is the launch's
   const uint32_t rp = (uint32_t)t.RP;
-  const float alpha = t.alpha;
   MT* msgs = reinterpret_cast<MT*>(base + t.off_msg);
   uint8_t* dec8 = base + t.off_dec;
   uint8_t* s8 = base + t.off_s;
@@ -306,6 +304,7 @@ __device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, ui
     const uint32_t* sch = t.sched + (size_t)i * n;
     const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
     const int nl = __ldg(t.nlev + i);
+    const float alpha = __ldg(t.alpha_m + i);   // member i's scaling factor
     int conv = 0;
     for (int it = 1; it <= budget; ++it) {
       // the posterior is needed after the last possible sweep of a member that may end without
@@ -314,7 +313,7 @@ __device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, ui
       bool flooded = false;
       if constexpr (std::is_same<MT, float>::value) {
         if (i < t.n_flood) {   // parallel schedule (the host allows it with FP32 messages only)
-          flood_sweep<DP>(t, msgs, dec8, s8, par8, lp, lane);
+          flood_sweep<DP>(t, alpha, msgs, dec8, s8, par8, lp, lane);
           flooded = true;
         }
       }

@@ -130,14 +130,13 @@ __device__ __forceinline__ void fetch_column(uint2 rec, const Tables& t, const M
 
 // Serial-V update of column v (deg checks, edges e0 .. e0 + deg - 1 in ascending check order).
 template <typename MT, int DP, bool PK>
-__device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tables& t, MT* msg, const XShared& X,
-                                                int* rcount, float* lpost) {
+__device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tables& t, float alpha, MT* msg,
+                                                const XShared& X, int* rcount, float* lpost) {
   const uint32_t v = d.v, e0 = d.e0;
   const int deg = d.deg;
   const int* c = d.c;
   const float* o = d.o;
   const float lamv = d.lam;
-  const float alpha = t.alpha;
   float mcv[DP];
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
@@ -359,6 +358,7 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
     const uint2* rec = t.sched_rec + (size_t)i * n;
     const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
     const int nl = __ldg(t.nlev + i);
+    const float alpha = __ldg(t.alpha_m + i);   // member i's scaling factor
     int conv = 0;
     ColData<DP> cd;
     for (int it = 1; it <= budget; ++it) {
@@ -379,7 +379,7 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
         ColData<DP> cdn;
         if (in_chunk(c1, nl, lane)) fetch_column<MT, DP, PK>(r1, t, msg, X.dec, cdn);
         const uint2 r2 = in_chunk(c2, nl, lane) ? __ldg(rec + c2.cs + lane) : make_uint2(0u, 0u);
-        if (in_chunk(c, nl, lane)) update_column_x<MT, DP, PK>(cd, t, msg, X, const_cast<int*>(rcount), lp);
+        if (in_chunk(c, nl, lane)) update_column_x<MT, DP, PK>(cd, t, alpha, msg, X, const_cast<int*>(rcount), lp);
         __syncwarp();
         const int nres = *rcount;
         if (nres > 0) {

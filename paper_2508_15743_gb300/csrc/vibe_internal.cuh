@@ -46,7 +46,7 @@ struct Tables {
   int W;         // words of a bit vector over the checks: ceil(m/32)
   int T, M, lsd_order;
   int n_flood;   // members 0 .. n_flood-1 run the parallel (flooding) schedule
-  float alpha;
+  float alpha;   // the shared factor (alpha_m holds the one each member uses)
   int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // image engine: per-warp shared memory, bytes
   int engine;    // VIBE_ENGINE_IMAGE or VIBE_ENGINE_SUMMARY
   // summary engine: shared memory of one warp (bytes) and global scratch of one warp (bytes, 16-aligned parts)
@@ -60,6 +60,7 @@ struct Tables {
   const int32_t* rowidx;
   const uint32_t* csc_ent; // n*DP: csc_entry() of each edge, ascending check, zero padded
   const float* lam;        // n prior LLRs
+  const float* alpha_m;    // K scaling factors, member i's in alpha_m[i]
   const void* msg_init;    // m*RP messages (float or half): lambda of the edge's column, +inf padding
   const uint32_t* sched;   // K*n: column | (degree << 24), grouped by wavefront level
   const uint2* sched_rec;  // K*n: (sched entry, first CSC edge of the column), same order

@@ -43,7 +43,8 @@ class vibe_csr(ctypes.Structure):
 class vibe_params(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("M", ctypes.c_int32),
                 ("lsd_order", ctypes.c_int32), ("msg_fp16", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("bp_engine", ctypes.c_int32), ("n_flood", ctypes.c_int32)]
+                ("bp_engine", ctypes.c_int32), ("n_flood", ctypes.c_int32),
+                ("member_alpha", ctypes.c_void_p)]
 
 
 ENGINE_AUTO, ENGINE_IMAGE, ENGINE_SUMMARY = 0, 1, 2
@@ -220,16 +221,20 @@ class Decoder:
     """One resident decoding problem: vibe_create at construction, vibe_destroy on close()."""
 
     def __init__(self, dem, K, schedules=None, T=30, alpha=0.625, M=None, lsd_order=0, msg_fp16=False, seed=0,
-                 engine=ENGINE_AUTO, n_flood=0):
+                 engine=ENGINE_AUTO, n_flood=0, member_alpha=None):
         if M is None:
             M = 1 if K == 1 else min(5, K)
         self.dem = dem
         self.m, self.n, self.k = dem.m, dem.n, dem.k
         self.mw, self.nw, self.kw = (self.m + 31) // 32, (self.n + 31) // 32, (self.k + 31) // 32
         self.K, self.T, self.M = K, T, M
+        ma = None if member_alpha is None else np.ascontiguousarray(member_alpha, dtype=np.float32)
+        if ma is not None and ma.shape != (K,):
+            raise ValueError("member_alpha needs one factor per member")
         self.params = vibe_params(int(T), float(alpha), int(M), int(lsd_order), int(bool(msg_fp16)), int(seed),
-                                  int(engine), int(n_flood))
+                                  int(engine), int(n_flood), None if ma is None else ma.ctypes.data)
         self.handle = vibe_create(dem.H, dem.L, dem.priors, K, schedules, self.params)
+        self.params.member_alpha = None   # vibe_create copied the factors
 
     def close(self):
         if self.handle:

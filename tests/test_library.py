@@ -45,10 +45,12 @@ def test_library_is_sm103a_only():
 
 
 def _params(V, **kw):
-    p = dict(max_iter=20, alpha=0.625, M=1, lsd_order=0, msg_fp16=0, seed=0, bp_engine=0, n_flood=0)
+    p = dict(max_iter=20, alpha=0.625, M=1, lsd_order=0, msg_fp16=0, seed=0, bp_engine=0, n_flood=0,
+             member_alpha=None)
     p.update(kw)
+    ma = p["member_alpha"]
     return V.vibe_params(p["max_iter"], p["alpha"], p["M"], p["lsd_order"], p["msg_fp16"], p["seed"],
-                         p["bp_engine"], p["n_flood"])
+                         p["bp_engine"], p["n_flood"], None if ma is None else ma.ctypes.data)
 
 
 def _err(V, H, L, priors, K, sched, params):
@@ -90,6 +92,11 @@ def test_host_validation_rejects_bad_input(V):
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=2))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, msg_fp16=1))[0] == V.VIBE_ERR_UNSUPPORTED
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, bp_engine=2))[0] == V.VIBE_ERR_UNSUPPORTED
+    # per-member scaling factors in (0, 1]
+    for bad_a in [0.0, 1.5, -0.5, np.nan]:
+        ma = np.array([0.625, bad_a], np.float32)
+        code, msg = _err(V, H, L, pr, 2, None, _params(V, member_alpha=ma))
+        assert code == V.VIBE_ERR_INVALID and "member_alpha[1]" in msg
     # schedules must be permutations
     sched = np.tile(np.arange(H.ncols, dtype=np.uint32), (2, 1))
     sched[1, 0] = sched[1, 1]
