@@ -8,8 +8,14 @@ with the device counters (shots, BP sweeps, LSD shots, rescans) and the kernel t
     python -m paper_2508_15743_gb300.cases <case> --precisions [--shots B]
 
 decodes the same shots with FP32 and FP16 message storage and reports both throughputs, logical
-error rates with 2-sigma binomial intervals and the fraction of differing corrections. Inputs are
-seeded and synthetic; the bench workload's numbers come from bench.py.
+error rates with 2-sigma binomial intervals and the fraction of differing corrections.
+
+    python -m paper_2508_15743_gb300.cases <image-engine case> --ensembles [--shots B]
+
+decodes the same shots (FP32) with the serial ensemble, with its first members on the parallel
+(flooding) schedule, with members differing in the scaling factor, and with both, reporting the
+same figures against the serial ensemble. Inputs are seeded and synthetic; the bench workload's
+numbers come from bench.py.
 """
 from __future__ import annotations
 
@@ -108,13 +114,71 @@ def compare_precisions(name: str, shots: int = 0) -> dict:
     return res
 
 
+# scaling factors of a mixed-heuristic ensemble of 16 members (member i takes entry i)
+ALPHA_MIX16 = [0.5, 0.625, 0.75, 1.0, 0.875, 0.5625, 0.6875, 0.8125] * 2
+
+# name -> (members on the flooding schedule, per-member factors or None)
+ENSEMBLES = {
+    "serial": (0, None),
+    "flood4": (4, None),
+    "alpha_mix": (0, ALPHA_MIX16),
+    "flood4_alpha_mix": (4, ALPHA_MIX16),
+    "flood_all": (-1, None),
+}
+
+
+def compare_ensembles(name: str, shots: int = 0) -> dict:
+    """Decodes the same shots (FP32 messages) with each ensemble of ENSEMBLES: throughput, logical
+    error rate with its 2-sigma binomial interval, LSD fraction, sweeps per shot and the fraction of
+    corrections that differ from the serial ensemble's."""
+    import time
+
+    import torch
+
+    from . import vibe as V
+
+    build, K, T, M, _, engine, default_shots, seed = CASES[name]
+    if engine != 1 or K != len(ALPHA_MIX16):
+        raise ValueError("ensemble comparisons run on the 16-member image-engine cases")
+    dm = build()
+    B = shots or default_shots
+    syn, obs = D.sample(dm, B, seed)
+    syn_t = torch.from_numpy(syn.view(np.int32)).cuda()
+    obs_t = torch.from_numpy(obs.view(np.int32)).cuda()
+    perms = D.schedules(dm.n, K, seed)
+    res, base = {}, None
+    for label, (n_flood, alphas) in ENSEMBLES.items():
+        dec = V.Decoder(dm, K, perms, T=T, M=M, engine=engine, n_flood=K if n_flood < 0 else n_flood,
+                        member_alpha=alphas)
+        dec.decode(syn_t[:64])
+        torch.cuda.synchronize()
+        cnt = torch.zeros(V.VIBE_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+        t0 = time.perf_counter()
+        o = dec.decode(syn_t, observables=obs_t, counters=cnt)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        c = cnt.cpu().numpy()
+        corr = o["corrections"].cpu().numpy()
+        if base is None:
+            base = corr
+        res[label] = dict(shots_per_s=B / dt, ler=_ler(int(c[V.CNT_FAILURES]), B),
+                          lsd_fraction=float(c[V.CNT_LSD]) / B, sweeps_per_shot=float(c[V.CNT_PAIR_ITERS]) / B,
+                          corrections_differ_from_serial=float((corr != base).any(axis=1).mean()))
+        dec.close()
+    res.update(case=name, shots=B, n=dm.n, m=dm.m, K=K, T=T, M=M)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=sorted(CASES))
     ap.add_argument("--shots", type=int, default=0)
     ap.add_argument("--precisions", action="store_true", help="compare FP32 and FP16 message storage")
+    ap.add_argument("--ensembles", action="store_true", help="compare serial, flooding and mixed-alpha ensembles")
     args = ap.parse_args()
-    if args.precisions:
+    if args.ensembles:
+        print(json.dumps(compare_ensembles(args.case, args.shots)))
+    elif args.precisions:
         print(json.dumps(compare_precisions(args.case, args.shots)))
     else:
         print(json.dumps(run_case(args.case, args.shots)))
