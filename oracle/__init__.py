@@ -51,7 +51,7 @@ class _Problem(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("alpha", ctypes.c_float), ("M", ctypes.c_int32),
                 ("lsd_order", ctypes.c_int32), ("mode", ctypes.c_int32), ("n_flood", ctypes.c_int32),
-                ("member_alpha", ctypes.c_void_p)]
+                ("member_alpha", ctypes.c_void_p), ("n_layered", ctypes.c_int32)]
 
 
 def _bind(path):
@@ -62,6 +62,10 @@ def _bind(path):
     lib.or_bp_member.restype = i32
     lib.or_bp_member_flood.argtypes = [vp, vp, i32, ctypes.c_float, i32, i32, vp, vp]
     lib.or_bp_member_flood.restype = i32
+    lib.or_bp_member_layered.argtypes = [vp, vp, i32, ctypes.c_float, i32, i32, vp, vp, vp]
+    lib.or_bp_member_layered.restype = i32
+    lib.or_check_layers.argtypes = [vp, vp]
+    lib.or_check_layers.restype = i32
     lib.or_decode.argtypes = [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, i32]
     lib.or_decode.restype = i32
     lib.or_lsd.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
@@ -155,10 +159,12 @@ def bp_member(dem, syndrome_bits, perm, T, alpha, mode=FP32, early_stop=True):
 
 
 def decode(dem, perms, syndromes, T, alpha, M, lsd_order=0, mode=FP32, nthreads=1, want_soft=True, n_flood=0,
-           member_alpha=None):
+           member_alpha=None, n_layered=0):
     """Full VibeLSD on packed syndromes uint32 [B, ceil(m/32)] with schedules uint32 [K, n].
 
     member_alpha: None, or K scaling factors, member i using member_alpha[i] instead of alpha.
+    n_flood, n_layered: members 0 .. n_flood-1 run the flooding schedule, the next n_layered members
+    the layered one, the rest their serial schedules.
 
     Returns dict(corrections uint32 [B, ceil(n/32)], logical uint32 [B, ceil(k/32)], stats, soft f64 [B, n]).
     """
@@ -176,7 +182,7 @@ def decode(dem, perms, syndromes, T, alpha, M, lsd_order=0, mode=FP32, nthreads=
     if ma is not None and ma.shape != (K,):
         raise ValueError("member_alpha needs one factor per member")
     prm = _Params(int(T), float(alpha), int(M), int(lsd_order), int(mode), int(n_flood),
-                  None if ma is None else ma.ctypes.data)
+                  None if ma is None else ma.ctypes.data, int(n_layered))
     rc = lib.or_decode(ctypes.byref(P.c), K, _ptr(perms), ctypes.byref(prm), B, _ptr(syn), _ptr(corr),
                        _ptr(logi), _ptr(stats), _ptr(soft), int(nthreads))
     if rc != 0:
@@ -195,6 +201,29 @@ def bp_member_flood(dem, syndrome_bits, T, alpha, mode=FP32, early_stop=True):
     t = lib.or_bp_member_flood(ctypes.byref(P.c), _ptr(s), int(T), float(alpha), int(mode),
                                int(bool(early_stop)), _ptr(post), _ptr(eb))
     return int(t), post, eb
+
+
+def bp_member_layered(dem, syndrome_bits, T, alpha, mode=FP32, early_stop=True, return_layers=False):
+    """One layered-schedule BP member (reading R10). Returns (t_conv, posterior f64[n], ebits u8[n]),
+    plus the number of check layers when return_layers is set."""
+    lib = _load()
+    P = Problem(dem)
+    s = np.ascontiguousarray(syndrome_bits, dtype=np.uint8)
+    post = np.zeros(P.n, np.float64)
+    eb = np.zeros(P.n, np.uint8)
+    nl = np.zeros(1, np.int32)
+    t = lib.or_bp_member_layered(ctypes.byref(P.c), _ptr(s), int(T), float(alpha), int(mode),
+                                 int(bool(early_stop)), _ptr(post), _ptr(eb), _ptr(nl))
+    return (int(t), post, eb, int(nl[0])) if return_layers else (int(t), post, eb)
+
+
+def check_layers(dem):
+    """The check layers of reading R10: (layer of each check int32[m], number of layers)."""
+    lib = _load()
+    P = Problem(dem)
+    lay = np.zeros(max(P.m, 1), np.int32)
+    nl = lib.or_check_layers(ctypes.byref(P.c), _ptr(lay))
+    return lay[:P.m], int(nl)
 
 
 def lsd(dem, soft, syndrome_bits, order=0, mode=FP32):

@@ -30,6 +30,16 @@
  *     posterior L_v and every m_{v->c} from those m_{c->v}, with R3's sums in the same order. With
  *     FP16 storage the m_{v->c} are rounded to binary16 when stored; the m_{c->v} of an iteration
  *     are float temporaries.
+ *  R10 Layered schedule (Sec. V names layered schedules, between serial and parallel, without
+ *     defining one; this is row-layered min-sum). The checks are split into layers by greedy
+ *     colouring in ascending check order: check c joins the smallest layer holding no earlier check
+ *     that shares a variable with it, so no two checks of a layer share a variable. Each member keeps
+ *     its m_{c->v} (zero before its first iteration) and its m_{v->c} (the priors). An iteration
+ *     takes the layers in ascending order: every check of the layer computes its m_{c->v} from the
+ *     current m_{v->c} with R2's rule, then every variable of those checks recomputes all its
+ *     m_{v->c} from its current m_{c->v} with R3's exclusion sums, so later layers see the update.
+ *     After the last layer L_v = lambda_v + sum_c m_{c->v} (R3's order). FP16 storage rounds the
+ *     stored m_{v->c}; the m_{c->v} stay float.
  *  R9 Ensembles mixing heuristics (Sec. V names combining heuristics across the ensemble): a member
  *     may carry its own scaling factor alpha_i; the rest of Algorithm 1 and R5 are unchanged.
  *  R7 LSD (Sec. III.C): columns ranked by soft value ascending, ties by index; one cluster per flipped
@@ -57,6 +67,9 @@ typedef struct {
   int32_t* col_chk;  /* E: check of the k-th edge of column v */
   int32_t* col_edge; /* E: CSR edge id of that edge */
   int32_t* edge_col; /* E: column of CSR edge e */
+  int nlayer;        /* layers of the layered schedule (R10) */
+  int32_t* layer_ptr; /* nlayer+1 */
+  int32_t* layer_chk; /* m: checks of each layer, ascending */
 } graph;
 
 static void graph_build(graph* g, const or_problem* P) {
@@ -81,10 +94,35 @@ static void graph_build(graph* g, const or_problem* P) {
   g->maxcol = 0;
   for (int v = 0; v < g->n; ++v)
     if (g->colptr[v + 1] - g->colptr[v] > g->maxcol) g->maxcol = g->colptr[v + 1] - g->colptr[v];
+  /* layers (R10): smallest layer not taken by an earlier check sharing a variable with c */
+  int32_t* layer_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->m + 1));
+  uint8_t* taken = (uint8_t*)calloc((size_t)g->m + 1, 1);
+  g->nlayer = 0;
+  for (int c = 0; c < g->m; ++c) {
+    for (int e = g->rowptr[c]; e < g->rowptr[c + 1]; ++e) {
+      int v = g->colidx[e];
+      for (int k = g->colptr[v]; k < g->colptr[v + 1] && g->col_chk[k] < c; ++k) taken[layer_of[g->col_chk[k]]] = 1;
+    }
+    int l = 0;
+    while (taken[l]) ++l;
+    layer_of[c] = l;
+    if (l + 1 > g->nlayer) g->nlayer = l + 1;
+    for (int e = g->rowptr[c]; e < g->rowptr[c + 1]; ++e) {
+      int v = g->colidx[e];
+      for (int k = g->colptr[v]; k < g->colptr[v + 1] && g->col_chk[k] < c; ++k) taken[layer_of[g->col_chk[k]]] = 0;
+    }
+  }
+  g->layer_ptr = (int32_t*)calloc((size_t)g->nlayer + 2, sizeof(int32_t));
+  g->layer_chk = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->m + 1));
+  for (int c = 0; c < g->m; ++c) g->layer_ptr[layer_of[c] + 1]++;
+  for (int l = 0; l < g->nlayer; ++l) g->layer_ptr[l + 1] += g->layer_ptr[l];
+  int32_t* at = (int32_t*)calloc((size_t)g->nlayer + 1, sizeof(int32_t));
+  for (int c = 0; c < g->m; ++c) g->layer_chk[g->layer_ptr[layer_of[c]] + at[layer_of[c]]++] = c;
+  free(at); free(taken); free(layer_of);
 }
 
 static void graph_free(graph* g) {
-  free(g->colptr); free(g->col_chk); free(g->col_edge); free(g->edge_col);
+  free(g->colptr); free(g->col_chk); free(g->col_edge); free(g->edge_col); free(g->layer_ptr); free(g->layer_chk);
 }
 
 void or_prior_llr(int32_t n, const double* priors, float* lam32, double* lam64) {
@@ -226,6 +264,92 @@ static void flood_f64(const graph* g, const uint8_t* s, const double* lam, doubl
   }
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* One layered iteration (R2, R3, R10). c2v: the member's E check-to-variable messages (CSR     */
+/* order), kept between iterations.                                                             */
+/* ------------------------------------------------------------------------------------------ */
+static void layered_f32(const graph* g, const uint8_t* s, const float* lam, float alpha, int fp16, float* msg,
+                        float* c2v, float* post) {
+  for (int l = 0; l < g->nlayer; ++l) {
+    for (int q = g->layer_ptr[l]; q < g->layer_ptr[l + 1]; ++q) {   /* the layer's checks */
+      int c = g->layer_chk[q];
+      for (int own = g->rowptr[c]; own < g->rowptr[c + 1]; ++own) {
+        int neg = s[c];
+        float mn = INFINITY;
+        for (int e = g->rowptr[c]; e < g->rowptr[c + 1]; ++e) {
+          if (e == own) continue;
+          float x = msg[e];
+          if (x < 0.0f) neg ^= 1;
+          float ax = fabsf(x);
+          if (ax < mn) mn = ax;
+        }
+        float mag = alpha * mn;
+        c2v[own] = neg ? -mag : mag;
+      }
+    }
+    for (int q = g->layer_ptr[l]; q < g->layer_ptr[l + 1]; ++q) {   /* their variables */
+      int c = g->layer_chk[q];
+      for (int ce = g->rowptr[c]; ce < g->rowptr[c + 1]; ++ce) {
+        int v = g->edge_col[ce];
+        int b = g->colptr[v], deg = g->colptr[v + 1] - b;
+        for (int k = 0; k < deg; ++k) {
+          float a = lam[v];
+          for (int k2 = 0; k2 < deg; ++k2)
+            if (k2 != k) a = a + c2v[g->col_edge[b + k2]];
+          msg[g->col_edge[b + k]] = store_msg(a, fp16);
+        }
+      }
+    }
+  }
+  for (int v = 0; v < g->n; ++v) {
+    int b = g->colptr[v], deg = g->colptr[v + 1] - b;
+    float L = lam[v];
+    for (int k = 0; k < deg; ++k) L = L + c2v[g->col_edge[b + k]];
+    post[v] = L;
+  }
+}
+
+static void layered_f64(const graph* g, const uint8_t* s, const double* lam, double alpha, double* msg,
+                        double* c2v, double* post) {
+  for (int l = 0; l < g->nlayer; ++l) {
+    for (int q = g->layer_ptr[l]; q < g->layer_ptr[l + 1]; ++q) {
+      int c = g->layer_chk[q];
+      for (int own = g->rowptr[c]; own < g->rowptr[c + 1]; ++own) {
+        int neg = s[c];
+        double mn = INFINITY;
+        for (int e = g->rowptr[c]; e < g->rowptr[c + 1]; ++e) {
+          if (e == own) continue;
+          double x = msg[e];
+          if (x < 0.0) neg ^= 1;
+          double ax = fabs(x);
+          if (ax < mn) mn = ax;
+        }
+        double mag = alpha * mn;
+        c2v[own] = neg ? -mag : mag;
+      }
+    }
+    for (int q = g->layer_ptr[l]; q < g->layer_ptr[l + 1]; ++q) {
+      int c = g->layer_chk[q];
+      for (int ce = g->rowptr[c]; ce < g->rowptr[c + 1]; ++ce) {
+        int v = g->edge_col[ce];
+        int b = g->colptr[v], deg = g->colptr[v + 1] - b;
+        for (int k = 0; k < deg; ++k) {
+          double a = lam[v];
+          for (int k2 = 0; k2 < deg; ++k2)
+            if (k2 != k) a = a + c2v[g->col_edge[b + k2]];
+          msg[g->col_edge[b + k]] = a;
+        }
+      }
+    }
+  }
+  for (int v = 0; v < g->n; ++v) {
+    int b = g->colptr[v], deg = g->colptr[v + 1] - b;
+    double L = lam[v];
+    for (int k = 0; k < deg; ++k) L = L + c2v[g->col_edge[b + k]];
+    post[v] = L;
+  }
+}
+
 /* H e = s with e_v = [L_v <= 0] (R4). */
 static int satisfies_f32(const graph* g, const uint8_t* s, const float* post) {
   for (int c = 0; c < g->m; ++c) {
@@ -257,6 +381,7 @@ typedef struct {
   float* post32; double* post64;   /* K * n */
   float* mcv32; double* mcv64;     /* maxcol */
   float* c2v32; double* c2v64;     /* E: check-to-variable temporaries of a flooding iteration */
+  float* lc2v32; double* lc2v64;   /* K * E: layered members' check-to-variable messages (R10), on demand */
   int32_t* conv_t;                 /* K */
   uint8_t* s;                      /* m */
   uint8_t* ebits;                  /* n */
@@ -313,7 +438,7 @@ static void ws_init(workspace* w, const or_problem* P, int K, int mode) {
 static void ws_free(workspace* w) {
   graph_free(&w->g);
   free(w->lam32); free(w->lam64); free(w->msg32); free(w->msg64); free(w->post32); free(w->post64);
-  free(w->mcv32); free(w->mcv64); free(w->c2v32); free(w->c2v64); free(w->conv_t); free(w->s); free(w->ebits); free(w->soft);
+  free(w->mcv32); free(w->mcv64); free(w->c2v32); free(w->c2v64); free(w->lc2v32); free(w->lc2v64); free(w->conv_t); free(w->s); free(w->ebits); free(w->soft);
   free(w->ck_par); free(w->col_root); free(w->roots); free(w->picks); free(w->cl_checks);
   free(w->cl_cols); free(w->tmp); free(w->mat); free(w->pivrow); free(w->x); free(w->xbest); free(w->asc);
 }
@@ -510,10 +635,19 @@ static void init_member(workspace* w, int i) {
   if (w->mode == OR_FP64) {
     double* msg = w->msg64 + (size_t)i * g->E;
     for (int e = 0; e < g->E; ++e) msg[e] = w->lam64[g->edge_col[e]];
+    if (w->lc2v64) memset(w->lc2v64 + (size_t)i * g->E, 0, sizeof(double) * (size_t)g->E);
   } else {
     float* msg = w->msg32 + (size_t)i * g->E;
     for (int e = 0; e < g->E; ++e) msg[e] = store_msg(w->lam32[g->edge_col[e]], w->mode == OR_FP16MSG);
+    if (w->lc2v32) memset(w->lc2v32 + (size_t)i * g->E, 0, sizeof(float) * (size_t)g->E);
   }
+}
+
+/* Storage for the layered members' check-to-variable messages (all K, zeroed by init_member). */
+static void ws_layered(workspace* w) {
+  size_t ke = (size_t)w->K * (size_t)(w->g.E > 0 ? w->g.E : 1);
+  if (w->mode == OR_FP64) w->lc2v64 = (double*)calloc(ke, sizeof(double));
+  else w->lc2v32 = (float*)calloc(ke, sizeof(float));
 }
 
 static void decode_one(workspace* w, const uint32_t* perms, const or_params* prm, const uint32_t* syn,
@@ -531,10 +665,14 @@ static void decode_one(workspace* w, const uint32_t* perms, const or_params* prm
       const uint32_t* perm = perms + (size_t)i * n;
       const float alpha = prm->member_alpha ? prm->member_alpha[i] : prm->alpha;
       int ok;
+      const int layered = i >= prm->n_flood && i < prm->n_flood + prm->n_layered;
       if (fp64) {
         if (i < prm->n_flood)
           flood_f64(g, w->s, w->lam64, (double)alpha, w->msg64 + (size_t)i * g->E, w->c2v64,
                     w->post64 + (size_t)i * n);
+        else if (layered)
+          layered_f64(g, w->s, w->lam64, (double)alpha, w->msg64 + (size_t)i * g->E, w->lc2v64 + (size_t)i * g->E,
+                      w->post64 + (size_t)i * n);
         else
           sweep_f64(g, perm, w->s, w->lam64, (double)alpha, w->msg64 + (size_t)i * g->E,
                     w->post64 + (size_t)i * n, w->mcv64);
@@ -543,6 +681,9 @@ static void decode_one(workspace* w, const uint32_t* perms, const or_params* prm
         if (i < prm->n_flood)
           flood_f32(g, w->s, w->lam32, alpha, fp16, w->msg32 + (size_t)i * g->E, w->c2v32,
                     w->post32 + (size_t)i * n);
+        else if (layered)
+          layered_f32(g, w->s, w->lam32, alpha, fp16, w->msg32 + (size_t)i * g->E, w->lc2v32 + (size_t)i * g->E,
+                      w->post32 + (size_t)i * n);
         else
           sweep_f32(g, perm, w->s, w->lam32, alpha, fp16, w->msg32 + (size_t)i * g->E,
                     w->post32 + (size_t)i * n, w->mcv32);
@@ -714,6 +855,46 @@ int32_t or_bp_member_flood(const or_problem* P, const uint8_t* syndrome, int32_t
   return conv;
 }
 
+int32_t or_bp_member_layered(const or_problem* P, const uint8_t* syndrome, int32_t T, float alpha, int32_t mode,
+                             int32_t early_stop, double* posterior, uint8_t* ebits, int32_t* nlayer) {
+  workspace w;
+  ws_init(&w, P, 1, mode);
+  ws_layered(&w);
+  memcpy(w.s, syndrome, (size_t)P->m);
+  init_member(&w, 0);
+  int conv = 0;
+  for (int t = 1; t <= T; ++t) {
+    int ok;
+    if (mode == OR_FP64) {
+      layered_f64(&w.g, w.s, w.lam64, (double)alpha, w.msg64, w.lc2v64, w.post64);
+      ok = satisfies_f64(&w.g, w.s, w.post64);
+    } else {
+      layered_f32(&w.g, w.s, w.lam32, alpha, mode == OR_FP16MSG, w.msg32, w.lc2v32, w.post32);
+      ok = satisfies_f32(&w.g, w.s, w.post32);
+    }
+    if (ok && !conv) conv = t;
+    if (ok && early_stop) break;
+  }
+  for (int j = 0; j < P->n; ++j) {
+    double L = mode == OR_FP64 ? w.post64[j] : (double)w.post32[j];
+    if (posterior) posterior[j] = L;
+    if (ebits) ebits[j] = (uint8_t)(L <= 0.0);
+  }
+  if (nlayer) *nlayer = w.g.nlayer;
+  ws_free(&w);
+  return conv;
+}
+
+int32_t or_check_layers(const or_problem* P, int32_t* layer_of_check) {
+  graph g;
+  graph_build(&g, P);
+  for (int l = 0; l < g.nlayer; ++l)
+    for (int q = g.layer_ptr[l]; q < g.layer_ptr[l + 1]; ++q) layer_of_check[g.layer_chk[q]] = l;
+  int nl = g.nlayer;
+  graph_free(&g);
+  return nl;
+}
+
 int32_t or_lsd(const or_problem* P, const double* soft, const uint8_t* syndrome, int32_t order,
                const float* lam32, const double* lam64, uint8_t* ebits, int32_t* cluster_of_col,
                int32_t* n_clusters, int32_t* largest_cluster) {
@@ -737,6 +918,7 @@ static void* run_job(void* arg) {
   int mw = (P->m + 31) / 32, nw = (P->n + 31) / 32, kw = (P->k + 31) / 32;
   workspace w;
   ws_init(&w, P, j->K, j->prm->mode);
+  if (j->prm->n_layered > 0) ws_layered(&w);
   for (int64_t b = j->b0; b < j->b1; ++b) {
     or_shot_stats st;
     decode_one(&w, j->perms, j->prm, j->syn + (size_t)b * mw, j->corr + (size_t)b * nw,
@@ -751,7 +933,7 @@ int32_t or_decode(const or_problem* P, int32_t K, const uint32_t* perms, const o
                   const uint32_t* syndromes, uint32_t* corrections, uint32_t* logical,
                   or_shot_stats* stats, double* soft, int32_t nthreads) {
   if (!P || !perms || !prm || !syndromes || !corrections || K < 1 || prm->M < 1 || prm->M > K ||
-      prm->T < 1 || B < 0)
+      prm->T < 1 || B < 0 || prm->n_flood < 0 || prm->n_layered < 0 || prm->n_flood + prm->n_layered > K)
     return -1;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > B) nthreads = B > 0 ? (int32_t)B : 1;

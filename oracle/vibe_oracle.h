@@ -53,6 +53,8 @@ typedef struct {
                          the serial one; their permutations are not used */
   const float* member_alpha;  /* NULL, or K factors: member i scales its check messages by
                                  member_alpha[i] instead of alpha (R9) */
+  int32_t n_layered;  /* members n_flood .. n_flood+n_layered-1 use the layered schedule (R10);
+                         n_flood + n_layered <= K */
 } or_params;
 
 /* Prior LLRs lambda_j = log((1 - p_j)/p_j) evaluated in double; lam32 gets the float rounding. */
@@ -70,6 +72,14 @@ int32_t or_bp_member(const or_problem* P, const uint8_t* syndrome, const uint32_
  * inputs and outputs as or_bp_member without a permutation. */
 int32_t or_bp_member_flood(const or_problem* P, const uint8_t* syndrome, int32_t T, float alpha, int32_t mode,
                            int32_t early_stop, double* posterior, uint8_t* ebits);
+
+/* One layered min-sum BP member (R10): same inputs and outputs as or_bp_member_flood; *nlayer (if
+ * not NULL) receives the number of check layers. */
+int32_t or_bp_member_layered(const or_problem* P, const uint8_t* syndrome, int32_t T, float alpha, int32_t mode,
+                             int32_t early_stop, double* posterior, uint8_t* ebits, int32_t* nlayer);
+
+/* The check layers of R10: layer_of_check[m] receives each check's layer; returns the layer count. */
+int32_t or_check_layers(const or_problem* P, int32_t* layer_of_check);
 
 /* Full VibeLSD on B shots. syndromes: uint32[B][ceil(m/32)] bit-packed; perms uint32[K][n].
  * Outputs (any may be NULL except corrections): corrections uint32[B][ceil(n/32)],

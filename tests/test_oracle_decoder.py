@@ -70,10 +70,16 @@ def test_zero_syndrome():
     assert (st["chosen_member"] == 0).all() and (st["lsd_invoked"] == 0).all()
 
 
-def _members(dm, perms, s, T, mode, n_flood=0, alphas=None):
+def _members(dm, perms, s, T, mode, n_flood=0, alphas=None, n_layered=0):
     al = [0.625] * len(perms) if alphas is None else [float(np.float32(a)) for a in alphas]
-    runs = [oracle.bp_member_flood(dm, s, T, al[i], mode) if i < n_flood else oracle.bp_member(dm, s, p, T, al[i], mode)
-            for i, p in enumerate(perms)]
+
+    def one(i, p):
+        if i < n_flood:
+            return oracle.bp_member_flood(dm, s, T, al[i], mode)
+        if i < n_flood + n_layered:
+            return oracle.bp_member_layered(dm, s, T, al[i], mode)
+        return oracle.bp_member(dm, s, p, T, al[i], mode)
+    runs = [one(i, p) for i, p in enumerate(perms)]
     return [r[0] for r in runs], [r[1] for r in runs], [r[2] for r in runs]
 
 
@@ -81,23 +87,26 @@ def _members(dm, perms, s, T, mode, n_flood=0, alphas=None):
 MEMBER_ALPHA = np.array([0.5, 0.625, 0.75, 1.0, 0.875, 0.5625, 0.6875, 0.8125] * 2, np.float32)
 
 
-@pytest.mark.parametrize("mode,n_flood,alphas", [(oracle.FP32, 0, None), (oracle.FP16MSG, 0, None),
-                                                 (oracle.FP32, 4, None), (oracle.FP32, 0, MEMBER_ALPHA),
-                                                 (oracle.FP32, 4, MEMBER_ALPHA), (oracle.FP16MSG, 0, MEMBER_ALPHA)])
-def test_correction_limit_and_ranking_from_independent_members(mode, n_flood, alphas):
+@pytest.mark.parametrize("mode,n_flood,alphas,n_layered", [
+    (oracle.FP32, 0, None, 0), (oracle.FP16MSG, 0, None, 0), (oracle.FP32, 4, None, 0),
+    (oracle.FP32, 0, MEMBER_ALPHA, 0), (oracle.FP32, 4, MEMBER_ALPHA, 0), (oracle.FP16MSG, 0, MEMBER_ALPHA, 0),
+    (oracle.FP32, 0, None, 6), (oracle.FP32, 3, MEMBER_ALPHA, 5), (oracle.FP16MSG, 2, None, 4)])
+def test_correction_limit_and_ranking_from_independent_members(mode, n_flood, alphas, n_layered):
     """n_flood > 0: a mixed ensemble whose first members run the parallel schedule (reading R8);
-    alphas: member i scales its check messages by alphas[i] (reading R9)."""
+    alphas: member i scales its check messages by alphas[i] (reading R9); n_layered: the next
+    members run the layered schedule (reading R10)."""
     dm = D.build_workload("cc666_d9_pheno")
     K, M, T = 16, 5, 30
     perms = D.schedules(dm.n, K, 2)
     syn, _ = D.sample(dm, 40, 21)
-    out = oracle.decode(dm, perms, syn, T, 0.625, M, mode=mode, n_flood=n_flood, member_alpha=alphas)
+    out = oracle.decode(dm, perms, syn, T, 0.625, M, mode=mode, n_flood=n_flood, member_alpha=alphas,
+                        n_layered=n_layered)
     l32, _ = oracle.prior_llr(dm.priors)
     st = out["stats"]
     seen_bp = 0
     for b in range(len(syn)):
         s = D.unpack_bits(syn[b:b + 1], dm.m)[0]
-        tconv, posts, ebits = _members(dm, perms, s, T, mode, n_flood, alphas)
+        tconv, posts, ebits = _members(dm, perms, s, T, mode, n_flood, alphas, n_layered)
         conv = sorted((t, i) for i, t in enumerate(tconv) if t > 0)
         cand = conv[:M]
         if not cand:
@@ -253,3 +262,5 @@ def test_equal_member_alphas_equal_the_shared_alpha():
     assert np.array_equal(a["stats"], b["stats"])
     with pytest.raises(ValueError):
         oracle.decode(dm, perms, syn, 20, 0.625, 3, member_alpha=np.ones(7, np.float32))
+    with pytest.raises(ValueError):   # more flooding and layered members than members
+        oracle.decode(dm, perms, syn, 20, 0.625, 3, n_flood=5, n_layered=4)

@@ -91,3 +91,30 @@ def test_planted_member_alpha_mistake_is_caught(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "tests/test_oracle_decoder.py"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
+
+
+LAYERED_MUTATIONS = {
+    "layers ignore shared variables": ("    while (taken[l]) ++l;\n", "    while (0) ++l;\n"),
+    "layered check messages not kept between iterations": (
+        "                        float* c2v, float* post) {\n  for (int l = 0; l < g->nlayer; ++l) {",
+        "                        float* c2v, float* post) {\n  memset(c2v, 0, sizeof(float) * (size_t)g->E);\n"
+        "  for (int l = 0; l < g->nlayer; ++l) {"),
+    "layered update refreshes only the layer's own edge": (
+        "        for (int k = 0; k < deg; ++k) {\n          float a = lam[v];",
+        "        for (int k = 0; k < deg; ++k) {\n          if (g->col_edge[b + k] != ce) continue;\n"
+        "          float a = lam[v];"),
+    "layered posterior without the prior": ("    float L = lam[v];\n    for (int k = 0; k < deg; ++k) L = L + c2v[g->col_edge[b + k]];\n    post[v] = L;",
+                                            "    float L = 0.0f;\n    for (int k = 0; k < deg; ++k) L = L + c2v[g->col_edge[b + k]];\n    post[v] = L;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LAYERED_MUTATIONS))
+def test_planted_layered_mistake_is_caught(name, tmp_path):
+    old, new = LAYERED_MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation site not found: {name}"
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_mut.so"))
+    env = dict(os.environ, VIBE_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_layered.py"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
