@@ -39,6 +39,9 @@ CASES = {
     # in 2e4 shots to compare precisions
     "summary_circuit_d9_p3": (lambda: C.circuit_dem(9, 9, 0.003, noise="si1000", basis="X"), 32, 50, 5, False,
                               2, 20_000, 4),
+    # XYZ colour-code circuit (X, Y and Z plaquette measurements in turn), d=7, 7 rounds, K=16
+    "summary_circuit_xyz_d7": (lambda: C.circuit_dem(7, 7, 0.001, noise="si1000", basis="X", schedule="xyz"), 16, 30,
+                               5, False, 2, 4000, 6),
     # circuit-level d=11, the full ensemble (K=64, T=50)
     "summary_circuit_d11": (lambda: C.circuit_dem(11, 11, 0.001, noise="si1000", basis="X"), 64, 50, 5, False, 2,
                             2432, 3),

@@ -68,8 +68,9 @@ class _Builder:
         if p > 0:
             self.moments[-1][1].append((kind, args, p))
 
-    def simulate(self):
-        """Measurement-flip record of every single fault: uint64 [nmeas, words], and fault probabilities."""
+    def fault_list(self):
+        """Every single fault: (moment, "P", ((qubit, x, z), ...), p) for a Pauli applied after the moment's
+        gates, or (moment, "M", measurement index, p) for an outcome flip."""
         faults = []
         for mi, (_, fl) in enumerate(self.moments):
             for kind, args, p in fl:
@@ -90,6 +91,12 @@ class _Builder:
                 elif kind == "MFLIP":
                     for k in args:
                         faults.append((mi, "M", k, p))
+        return faults
+
+    def simulate(self):
+        """Measurement-flip record of every single fault of fault_list(): uint64 [nmeas, words] (fault f
+        is bit f % 64 of word f // 64), and the fault probabilities."""
+        faults = self.fault_list()
         F = len(faults)
         W = (F + 63) // 64
         X = np.zeros((self.nq, W), np.uint64)
@@ -104,6 +111,12 @@ class _Builder:
                     for c, t in args[0]:
                         X[t] ^= X[c]
                         Z[c] ^= Z[t]
+                elif kind == "CY":
+                    # controlled-Y: X_c -> X_c Y_t, X_t -> Z_c X_t, Z_t -> Z_c Z_t, Z_c fixed
+                    for c, t in args[0]:
+                        Z[c] ^= X[t] ^ Z[t]
+                        X[t] ^= X[c]
+                        Z[t] ^= X[c]
                 elif kind == "H":
                     for q in args[0]:
                         X[q], Z[q] = Z[q].copy(), X[q].copy()
@@ -135,13 +148,21 @@ def _unpack_rows(packed, F):
     return np.unpackbits(by, axis=1, bitorder="little")[:, :F]
 
 
-def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None) -> DEM:
-    """Detector error model of `rounds` rounds of the colour-code memory circuit in basis X or Z.
+def memory_circuit(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None, schedule="xz") -> dict:
+    """The colour-code memory circuit as a _Builder plus its detectors and observable.
 
-    noise: "si1000", "uniform", or "custom" with `custom` a dict of per-location probabilities
-    (keys data_x / data_z: flips on data before each round, meas_z / meas_x: outcome flips of the
-    Z / X plaquette measurements, final_meas: flips of the data measurement) for testing.
+    schedule "xz": every round measures all Z-type then all X-type plaquettes (module docstring).
+    schedule "xyz": round r measures every plaquette in one basis, cycling (B, Y, other) with B the
+    memory basis; a Y measurement is an ancilla in |+>, six layers of controlled-Y ancilla -> data
+    and H before the measurement. On an even-weight plaquette X_P Y_P Z_P is a constant, so the
+    outcomes of three consecutive rounds have a fixed parity: that is the detector of round r >= 2;
+    round 0 (basis B) is deterministic on its own, round 1 (Y) is random, and the final data
+    measurement is compared with the last round that measured B.
+
+    Returns dict(builder, det_meas: lists of measurement indices, det_type, obs_meas).
     """
+    if schedule not in ("xz", "xyz"):
+        raise ValueError(schedule)
     qubits, plaqs = color_code_layout(d)
     n, mp = len(qubits), len(plaqs)
     qidx = {q: k for k, q in enumerate(qubits)}
@@ -171,6 +192,44 @@ def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom
         rest = [q for q in allq if q not in busy]
         B.fault("DEP1", rest, factor * p)
 
+    def block(kind):
+        """Reset the ancillas, measure every plaquette in basis kind ("X", "Y" or "Z"); returns the
+        measurement indices, one per plaquette."""
+        B.moment()
+        B.gate("R", anc)
+        if w is not None:
+            B.fault("X", anc, w["reset"] * p)
+            idle(set(anc), w["idle_mr"])
+        if kind != "Z":
+            B.moment()
+            B.gate("H", anc)
+            if w is not None:
+                B.fault("DEP1", anc, w["h"] * p)
+                idle(set(anc), w["idle_gate"])
+        gate = {"X": "CX", "Y": "CY", "Z": "CX"}[kind]
+        for L in layers:
+            pairs = L if kind == "Z" else [(a, q) for (q, a) in L]
+            B.moment()
+            B.gate(gate, pairs)
+            if w is not None:
+                B.fault("DEP2", pairs, w["cx"] * p)
+                idle({q for pr in pairs for q in pr}, w["idle_gate"])
+        if kind != "Z":
+            B.moment()
+            B.gate("H", anc)
+            if w is not None:
+                B.fault("DEP1", anc, w["h"] * p)
+                idle(set(anc), w["idle_gate"])
+        B.moment()
+        ks = B.gate("M", anc, None)
+        B.moments[-1][0][-1] = ("M", (anc, ks))
+        if w is not None:
+            B.fault("MFLIP", ks, w["meas"] * p)
+            idle(set(anc), w["idle_mr"])
+        else:
+            B.fault("MFLIP", ks, custom.get("meas_" + kind.lower(), 0.0))
+        return ks
+
     # data preparation in the +1 eigenstate of the memory basis
     B.moment()
     B.gate("R", list(range(n)))
@@ -179,64 +238,21 @@ def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom
     if w is not None:
         B.fault("Z" if basis == "X" else "X", list(range(n)), w["reset"] * p)
         idle(set(range(n)), w["idle_mr"])
-    mz, mx = [], []
+    obasis = "Z" if basis == "X" else "X"
+    cycle = (basis, "Y", obasis)
+    meas = {"X": [], "Y": [], "Z": []}   # xz schedule: per-round indices of each type
+    seq = []                             # xyz schedule: (basis, indices) per round
     for r in range(rounds):
         if w is None:
             B.moment()
             B.fault("X", list(range(n)), custom.get("data_x", 0.0))
             B.fault("Z", list(range(n)), custom.get("data_z", 0.0))
-        # Z block
-        B.moment()
-        B.gate("R", anc)
-        if w is not None:
-            B.fault("X", anc, w["reset"] * p)
-            idle(set(anc), w["idle_mr"])
-        for L in layers:
-            B.moment()
-            B.gate("CX", L)
-            if w is not None:
-                B.fault("DEP2", L, w["cx"] * p)
-                idle({q for pr in L for q in pr}, w["idle_gate"])
-        B.moment()
-        ks = B.gate("M", anc, None)
-        B.moments[-1][0][-1] = ("M", (anc, ks))
-        mz.append(ks)
-        if w is not None:
-            B.fault("MFLIP", ks, w["meas"] * p)
-            idle(set(anc), w["idle_mr"])
+        if schedule == "xz":
+            meas["Z"].append(block("Z"))
+            meas["X"].append(block("X"))
         else:
-            B.fault("MFLIP", ks, custom.get("meas_z", 0.0))
-        # X block
-        B.moment()
-        B.gate("R", anc)
-        if w is not None:
-            B.fault("X", anc, w["reset"] * p)
-            idle(set(anc), w["idle_mr"])
-        B.moment()
-        B.gate("H", anc)
-        if w is not None:
-            B.fault("DEP1", anc, w["h"] * p)
-            idle(set(anc), w["idle_gate"])
-        for L in layers:
-            B.moment()
-            B.gate("CX", [(a, q) for (q, a) in L])
-            if w is not None:
-                B.fault("DEP2", [(a, q) for (q, a) in L], w["cx"] * p)
-                idle({q for pr in L for q in pr}, w["idle_gate"])
-        B.moment()
-        B.gate("H", anc)
-        if w is not None:
-            B.fault("DEP1", anc, w["h"] * p)
-            idle(set(anc), w["idle_gate"])
-        B.moment()
-        ks = B.gate("M", anc, None)
-        B.moments[-1][0][-1] = ("M", (anc, ks))
-        mx.append(ks)
-        if w is not None:
-            B.fault("MFLIP", ks, w["meas"] * p)
-            idle(set(anc), w["idle_mr"])
-        else:
-            B.fault("MFLIP", ks, custom.get("meas_x", 0.0))
+            kind = cycle[r % 3]
+            seq.append((kind, block(kind)))
     # final data measurement in the memory basis
     B.moment()
     if basis == "X":
@@ -249,23 +265,48 @@ def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom
     else:
         B.fault("MFLIP", kd, custom.get("final_meas", 0.0))
 
-    rec, probs = B.simulate()
-    # detectors as lists of measurement indices
     det_meas, det_type = [], []
-    same, other = (mx, mz) if basis == "X" else (mz, mx)
-    obasis = "Z" if basis == "X" else "X"
-    for r in range(rounds):
-        for P in range(mp):
-            det_meas.append([same[r][P]] if r == 0 else [same[r][P], same[r - 1][P]])
-            det_type.append(basis)
-        if r > 0:
+    if schedule == "xz":
+        same, other = meas[basis], meas[obasis]
+        for r in range(rounds):
             for P in range(mp):
-                det_meas.append([other[r][P], other[r - 1][P]])
-                det_type.append(obasis)
+                det_meas.append([same[r][P]] if r == 0 else [same[r][P], same[r - 1][P]])
+                det_type.append(basis)
+            if r > 0:
+                for P in range(mp):
+                    det_meas.append([other[r][P], other[r - 1][P]])
+                    det_type.append(obasis)
+        last = same[rounds - 1] if rounds > 0 else None
+    else:
+        for r in range(rounds):
+            if r == 0:
+                for P in range(mp):
+                    det_meas.append([seq[0][1][P]])
+                    det_type.append(basis)
+            elif r >= 2:
+                for P in range(mp):
+                    det_meas.append([seq[r - 2][1][P], seq[r - 1][1][P], seq[r][1][P]])
+                    det_type.append("XYZ")
+        mine = [ks for kind, ks in seq if kind == basis]
+        last = mine[-1] if mine else None
     for P in range(mp):
-        det_meas.append([kd[q] for q in sup[P]] + ([same[rounds - 1][P]] if rounds > 0 else []))
+        det_meas.append([kd[q] for q in sup[P]] + ([last[P]] if last is not None else []))
         det_type.append(basis)
-    obs_meas = [kd[q] for q in logical]
+    return dict(builder=B, det_meas=det_meas, det_type=det_type, obs_meas=[kd[q] for q in logical])
+
+
+def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None, schedule="xz") -> DEM:
+    """Detector error model of `rounds` rounds of the colour-code memory circuit in basis X or Z.
+
+    noise: "si1000", "uniform", or "custom" with `custom` a dict of per-location probabilities
+    (keys data_x / data_z: flips on data before each round, meas_z / meas_x / meas_y: outcome flips
+    of the plaquette measurements, final_meas: flips of the data measurement) for testing.
+    schedule: "xz" (X and Z plaquettes every round) or "xyz" (one basis per round, cycling; see
+    memory_circuit).
+    """
+    circ = memory_circuit(d, rounds, p, noise, basis, custom, schedule)
+    rec, probs = circ["builder"].simulate()
+    det_meas, obs_meas = circ["det_meas"], circ["obs_meas"]
     F = len(probs)
     Wd = rec.shape[1]
     D = np.zeros((len(det_meas) + 1, Wd), np.uint64)
@@ -300,6 +341,8 @@ def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom
     H = CSR.from_rows(rows, ncol)
     L = CSR.from_rows([lcols], ncol)
     undetectable = float(probs[(~flips_det) & (bits[-1] == 1)].sum())
-    return DEM(H, L, pcol.astype(np.float64), name=f"cc666_d{d}_circuit_{noise}_{basis}_r{rounds}_p{p}",
+    tag = "" if schedule == "xz" else "_xyz"
+    return DEM(H, L, pcol.astype(np.float64), name=f"cc666_d{d}_circuit{tag}_{noise}_{basis}_r{rounds}_p{p}",
                meta={"d": d, "rounds": rounds, "p": p, "noise": noise, "basis": basis, "faults": F,
-                     "undetectable_logical_prob": undetectable, "det_type": det_type})
+                     "schedule": schedule, "undetectable_logical_prob": undetectable,
+                     "det_type": circ["det_type"]})

@@ -194,14 +194,15 @@ def test_circuit_dem_invariants(basis):
     assert dm.priors.sum() < 5 * 1e-3 * dm.meta["faults"]
 
 
-def test_circuit_single_faults_get_valid_corrections():
+@pytest.mark.parametrize("schedule", ["xz", "xyz"])
+def test_circuit_single_faults_get_valid_corrections(schedule):
     """Every single fault of a d=3 circuit DEM gets a correction with H e = s (oracle, exhaustive).
 
     The logical class is not pinned: the schedule's hook errors give pairs of single faults with the
     same syndrome and different logical effect (circuit distance 2 at d = 3), and Si1000's unequal
     priors let lighter multi-fault explanations win."""
     import oracle
-    dm = C.circuit_dem(3, 3, 1e-3, noise="si1000", basis="X")
+    dm = C.circuit_dem(3, 3 if schedule == "xz" else 4, 1e-3, noise="si1000", basis="X", schedule=schedule)
     errs = np.eye(dm.n, dtype=np.uint8)
     syn, obs = D.syndromes_of(dm, errs)
     perms = D.schedules(dm.n, 8, 1)
