@@ -92,7 +92,9 @@ def test_host_validation_rejects_bad_input(V):
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=2))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, msg_fp16=1))[0] == V.VIBE_ERR_UNSUPPORTED
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, bp_engine=2))[0] == V.VIBE_ERR_UNSUPPORTED
-    # per-member scaling factors in (0, 1]
+    # per-member scaling factors: one per member (checked by the binding), each in (0, 1] (the library)
+    with pytest.raises(ValueError):
+        V.Decoder(dm, 2, None, T=5, M=1, member_alpha=np.array([0.5, 0.5, 0.5], np.float32))
     for bad_a in [0.0, 1.5, -0.5, np.nan]:
         ma = np.array([0.625, bad_a], np.float32)
         code, msg = _err(V, H, L, pr, 2, None, _params(V, member_alpha=ma))
