@@ -118,3 +118,36 @@ def test_planted_layered_mistake_is_caught(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "tests/test_oracle_layered.py"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
+
+
+LSD_ORDER_MUTATIONS = {
+    "order search one column short": ("      int qn = order < nfree ? order : nfree;",
+                                      "      int qn = order < nfree ? order - 1 : nfree;"),
+    "order search keeps the heaviest setting": ("        if (a == 0 || W < bestW) { bestW = W;",
+                                                "        if (a == 0 || W > bestW) { bestW = W;"),
+    "order search over the last free columns": (
+        "        for (int b = 0; b < qn; ++b) w->x[w->tmp[b]] = (uint8_t)((a >> b) & 1);\n"
+        "        for (int t = 0; t < ncol; ++t) {\n"
+        "          int pr = w->pivrow[t];\n"
+        "          if (pr < 0) continue;\n"
+        "          int val = w->mat[pr * wd + ncol];\n"
+        "          for (int b = 0; b < qn; ++b) val ^= w->mat[pr * wd + w->tmp[b]] & w->x[w->tmp[b]];",
+        "        for (int b = 0; b < qn; ++b) w->x[w->tmp[nfree - 1 - b]] = (uint8_t)((a >> b) & 1);\n"
+        "        for (int t = 0; t < ncol; ++t) {\n"
+        "          int pr = w->pivrow[t];\n"
+        "          if (pr < 0) continue;\n"
+        "          int val = w->mat[pr * wd + ncol];\n"
+        "          for (int b = 0; b < qn; ++b) val ^= w->mat[pr * wd + w->tmp[nfree - 1 - b]] & w->x[w->tmp[nfree - 1 - b]];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LSD_ORDER_MUTATIONS))
+def test_planted_lsd_order_mistake_is_caught(name, tmp_path):
+    old, new = LSD_ORDER_MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation site not found: {name}"
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_mut.so"))
+    env = dict(os.environ, VIBE_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_lsd.py"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the planted mistake '{name}':\n{r.stdout[-2000:]}"
