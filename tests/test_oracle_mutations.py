@@ -33,6 +33,15 @@ MUTATIONS = {
     "LSD grows along the worst column": ("if (w->col_root[j] < 0 && (best < 0 || ranks_before(soft, j, best))) best = j;",
                                          "if (w->col_root[j] < 0 && (best < 0 || ranks_before(soft, best, j))) best = j;"),
     "LSD right-hand side misread": ("int val = w->mat[pr * wd + ncol];", "int val = w->mat[pr * wd + 0];"),
+    "LLR norm summed in one sequential pass": (
+        "        for (int off = 16; off >= 1; off >>= 1) {\n"
+        "          float nxt[32];\n"
+        "          for (int l = 0; l < 32; ++l) nxt[l] = part[l] + part[l ^ off];\n"
+        "          memcpy(part, nxt, sizeof(part));\n"
+        "        }\n",
+        "        { float seq = 0.0f;\n"
+        "          for (int j = 0; j < n; ++j) seq = seq + (isfinite(post[j]) ? post[j] * post[j] : 0.0f);\n"
+        "          part[0] = seq; }\n"),
     "correction limit off by one": ("if (nconv >= M) { t_stop = t; break; }", "if (nconv > M) { t_stop = t; break; }"),
 }
 
