@@ -305,6 +305,22 @@ def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom
     memory_circuit).
     """
     circ = memory_circuit(d, rounds, p, noise, basis, custom, schedule)
+    H, L, pcol, F, undetectable = dem_from_circuit(circ)
+    tag = "" if schedule == "xz" else "_xyz"
+    return DEM(H, L, pcol, name=f"cc666_d{d}_circuit{tag}_{noise}_{basis}_r{rounds}_p{p}",
+               meta={"d": d, "rounds": rounds, "p": p, "noise": noise, "basis": basis, "faults": F,
+                     "schedule": schedule, "undetectable_logical_prob": undetectable,
+                     "det_type": circ["det_type"]})
+
+
+def dem_from_circuit(circ: dict):
+    """Detector error model of a circuit from memory_circuit (or any dict with builder, det_meas and
+    obs_meas): every single fault is propagated, faults that flip no detector are dropped, and faults
+    with the same detector and observable signature merge into one column whose probability is that
+    of an odd number of them, (1 - prod(1 - 2 p_i)) / 2. Columns are ordered by first appearance.
+
+    Returns (H, L, priors, number of faults, total probability of faults that flip the observable
+    and no detector)."""
     rec, probs = circ["builder"].simulate()
     det_meas, obs_meas = circ["det_meas"], circ["obs_meas"]
     F = len(probs)
@@ -341,8 +357,4 @@ def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom
     H = CSR.from_rows(rows, ncol)
     L = CSR.from_rows([lcols], ncol)
     undetectable = float(probs[(~flips_det) & (bits[-1] == 1)].sum())
-    tag = "" if schedule == "xz" else "_xyz"
-    return DEM(H, L, pcol.astype(np.float64), name=f"cc666_d{d}_circuit{tag}_{noise}_{basis}_r{rounds}_p{p}",
-               meta={"d": d, "rounds": rounds, "p": p, "noise": noise, "basis": basis, "faults": F,
-                     "schedule": schedule, "undetectable_logical_prob": undetectable,
-                     "det_type": circ["det_type"]})
+    return H, L, pcol.astype(np.float64), F, undetectable

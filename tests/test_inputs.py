@@ -215,3 +215,33 @@ def test_circuit_single_faults_get_valid_corrections(schedule):
     for j in range(dm.n):
         groups.setdefault(tuple(A[:, j]), set()).add(j in set(dm.L.row(0).tolist()))
     assert any(len(v) == 2 for v in groups.values()), "hook errors of this schedule (documented)"
+
+
+def test_merged_columns_take_the_odd_number_probability():
+    """Faults with one signature merge into one column whose prior is the probability that an odd
+    number of them occur (brute-force enumeration over the mechanisms); a fault flipping only the
+    observable is reported as undetectable."""
+    import itertools
+    p1, p2, p3, p4, p5 = 0.01, 0.03, 0.2, 0.05, 0.004
+    B = C._Builder(3)
+    B.moment()
+    B.gate("R", [0, 1, 2])
+    B.fault("X", [0], p1)
+    B.fault("X", [0], p2)
+    B.fault("X", [2], p5)
+    B.moment()
+    ks = B.gate("M", [0, 1, 2], None)
+    B.moments[-1][0][-1] = ("M", ([0, 1, 2], ks))
+    B.fault("MFLIP", [ks[0]], p3)
+    B.fault("MFLIP", [ks[1]], p4)
+    circ = dict(builder=B, det_meas=[[ks[0]], [ks[1]]], obs_meas=[ks[1], ks[2]])
+    H, L, pri, F, undetectable = C.dem_from_circuit(circ)
+    assert F == 5 and H.ncols == 2
+    assert H.to_dense().tolist() == [[1, 0], [0, 1]]
+    assert L.to_dense().tolist() == [[0, 1]]
+    ps = [p1, p2, p3]
+    odd = sum(np.prod([p if b else 1 - p for p, b in zip(ps, bits)])
+              for bits in itertools.product([0, 1], repeat=3) if sum(bits) % 2 == 1)
+    assert pri[0] == pytest.approx(odd, rel=1e-12)
+    assert pri[1] == pytest.approx(p4, rel=1e-12)
+    assert undetectable == pytest.approx(p5, rel=1e-12)
