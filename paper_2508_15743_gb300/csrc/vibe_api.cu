@@ -44,11 +44,6 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 constexpr size_t kWorkspaceBytes = size_t(4) << 30;   // LSD hand-off buffer budget per workspace
 
-// Summary engine: problems with at least this many checks start with the byte layout of the warp
-// state, the others with the packed layout (measured: packed is faster on the circuit-level colour
-// codes of d = 5 and 9, bytes on d = 11 with 990 checks). vibe_autotune times both.
-constexpr int kBytesLayoutChecks = 900;
-
 int check_csr(const vibe_csr* A, const char* name, bool rows_nonempty) {
   if (!A || !A->rowptr || (!A->colidx && A->nrows > 0)) return fail(VIBE_ERR_INVALID, "%s: NULL matrix", name);
   if (A->nrows < 0 || A->ncols < 1) return fail(VIBE_ERR_INVALID, "%s: bad shape %d x %d", name, A->nrows, A->ncols);
@@ -274,11 +269,12 @@ Bounds bounds_over(const Tables* ts, int count) {
       b.warp_smem = std::max(b.warp_smem, t.warp_smem);
     } else {
       b.engines |= 2;
-      b.x_packed = t.x_packed;   // used by single-problem launches only
+      b.XD = std::max(b.XD, t.XD);
       b.x_warp_smem = std::max(b.x_warp_smem, t.x_warp_smem);
       b.x_warp_scratch = std::max(b.x_warp_scratch, t.x_warp_scratch);
     }
   }
+  if (b.engines & 2) b.x_warp_smem += vibe::bpx_ring_bytes(b.XD);
   return b;
 }
 
@@ -295,13 +291,12 @@ struct vibe_handle {
   int32_t *rowptr = nullptr, *colidx = nullptr, *colptr = nullptr, *rowidx = nullptr;
   int32_t *lrowptr = nullptr, *lcolidx = nullptr, *nlev = nullptr;
   uint32_t *csc_ent = nullptr, *sched = nullptr, *lvl_off = nullptr, *perm = nullptr;
-  uint2* sched_rec = nullptr;
   float* lam = nullptr;
   float* alpha_m = nullptr;
   void* msg_init = nullptr;
-  uint32_t* row_edge = nullptr;
-  void* msg_csc = nullptr;
-  float4* sum_init = nullptr;
+  uint32_t *xcol = nullptr, *xrmap = nullptr;
+  uint2* xrec = nullptr;
+  float4* xsum = nullptr;
   unsigned long long* tmp_counters = nullptr;
   // host-buffer staging
   long long stage_cap = 0;
@@ -321,7 +316,7 @@ struct vibe_handle {
     cudaFree(tmp_counters);
     cudaFree(rowptr); cudaFree(colidx); cudaFree(colptr); cudaFree(rowidx); cudaFree(lrowptr); cudaFree(lcolidx);
     cudaFree(nlev); cudaFree(csc_ent); cudaFree(sched); cudaFree(lvl_off); cudaFree(perm); cudaFree(lam); cudaFree(alpha_m);
-    cudaFree(msg_init); cudaFree(sched_rec); cudaFree(row_edge); cudaFree(msg_csc); cudaFree(sum_init); cudaFree(d_desc);
+    cudaFree(msg_init); cudaFree(xcol); cudaFree(xrec); cudaFree(xrmap); cudaFree(xsum); cudaFree(d_desc);
     cudaSetDevice(prev);
   }
 };
@@ -437,9 +432,12 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   t.mw = (m + 31) / 32; t.nw = (n + 31) / 32; t.kw = (k + 31) / 32; t.W = t.mw;
   t.T = p->max_iter; t.M = p->M; t.lsd_order = p->lsd_order; t.alpha = p->alpha; t.n_flood = p->n_flood;
   vibe::bp_warp_smem_bytes(&t, p->msg_fp16);
-  t.x_packed = m < kBytesLayoutChecks ? 1 : 0;
+  t.XD = vibe::bpx_degree_bucket(maxcol);
+  t.XP = (t.XD + 3) / 4 * 4;
   vibe::bpx_layout(&t, p->msg_fp16);
   t.engine = p->bp_engine;
+  if (t.engine == VIBE_ENGINE_SUMMARY && t.XD == 0)
+    return bail(fail(VIBE_ERR_UNSUPPORTED, "the summary engine takes columns of at most 16 checks"));
   if (t.engine == VIBE_ENGINE_AUTO) {
     // the image engine when its per-warp image leaves at least 8 warps per SM, else the summary engine
     int optin = 0, blocks = 0;
@@ -449,7 +447,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
     t.engine = VIBE_ENGINE_SUMMARY;
     if (vibe::bp_cta_smem_bytes(bw, 0) <= (size_t)optin &&
         vibe::bp_occupancy(bw, 0, p->msg_fp16, &blocks) == cudaSuccess &&
-        (blocks * vibe::kBpWarpsPerCta >= 8 || (p->n_flood > 0 && blocks >= 1)))
+        (blocks * vibe::kBpWarpsPerCta >= 8 || (p->n_flood > 0 && blocks >= 1) || (t.XD == 0 && blocks >= 1)))
       t.engine = VIBE_ENGINE_IMAGE;
     if (p->n_flood > 0 && t.engine != VIBE_ENGINE_IMAGE)
       return bail(fail(VIBE_ERR_UNSUPPORTED, "flooding members need the image engine; the message image does not fit"));
@@ -471,15 +469,16 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   VIBE_TRY(dalloc(&h->nlev, K), "tables");
   VIBE_TRY(dalloc(&h->csc_ent, (size_t)n * t.DP), "tables");
   VIBE_TRY(dalloc(&h->sched, (size_t)K * n), "tables");
-  VIBE_TRY(dalloc(&h->sched_rec, (size_t)K * n), "tables");
+
   VIBE_TRY(dalloc(&h->lvl_off, (size_t)K * (n + 1)), "tables");
   VIBE_TRY(dalloc(&h->perm, (size_t)K * n), "tables");
   VIBE_TRY(dalloc(&h->lam, n), "tables");
   VIBE_TRY(dalloc(&h->alpha_m, K), "tables");
   VIBE_TRY(cudaMalloc(&h->msg_init, std::max<size_t>(msg_bytes, 16)), "tables");
-  VIBE_TRY(dalloc(&h->row_edge, E), "tables");
-  VIBE_TRY(cudaMalloc(&h->msg_csc, ((size_t)E * (p->msg_fp16 ? 2 : 4) + 15) / 16 * 16 + 16), "tables");
-  VIBE_TRY(dalloc(&h->sum_init, m), "tables");
+  VIBE_TRY(dalloc(&h->xcol, (size_t)n * t.XP), "tables");
+  VIBE_TRY(dalloc(&h->xrec, t.XP ? (size_t)K * n : 0), "tables");
+  VIBE_TRY(dalloc(&h->xrmap, t.XP ? (size_t)K * E : 0), "tables");
+  VIBE_TRY(dalloc(&h->xsum, m), "tables");
   VIBE_TRY(dalloc(&h->d_desc, 1), "tables");
   VIBE_TRY(dalloc(&scratch, lev_scratch), "tables");
   VIBE_TRY(dalloc(&h->tmp_counters, VIBE_NUM_COUNTERS), "tables");
@@ -497,14 +496,14 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   } else {
     VIBE_TRY(vibe::seeded_schedules(h->perm, n, K, p->seed, s), "schedule kernel");
   }
-  VIBE_TRY(vibe::build_tables(h->rowptr, h->colidx, m, n, K, h->perm, t.RP, t.DP, p->msg_fp16, h->lam, h->colptr,
-                              h->rowidx, h->csc_ent, h->msg_init, h->sched, h->sched_rec, h->lvl_off, h->nlev, h->row_edge,
-                              h->msg_csc, h->sum_init, scratch, s),
+  VIBE_TRY(vibe::build_tables(h->rowptr, h->colidx, m, n, K, h->perm, t.RP, t.DP, t.XP, p->msg_fp16, h->lam,
+                              h->colptr, h->rowidx, h->csc_ent, h->msg_init, h->sched, h->lvl_off, h->nlev, h->xcol,
+                              h->xrec, h->xrmap, h->xsum, scratch, s),
            "graph builder");
   t.rowptr = h->rowptr; t.colidx = h->colidx; t.colptr = h->colptr; t.rowidx = h->rowidx;
   t.csc_ent = h->csc_ent; t.lam = h->lam; t.alpha_m = h->alpha_m; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
   t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
-  t.row_edge = h->row_edge; t.msg_csc = h->msg_csc; t.sum_init = h->sum_init; t.sched_rec = h->sched_rec;
+  t.xcol = h->xcol; t.xrec = h->xrec; t.xrmap = h->xrmap; t.xsum = h->xsum;
   VIBE_TRY(cudaMemcpyAsync(h->d_desc, &t, sizeof(Tables), cudaMemcpyHostToDevice, s), "upload");
   VIBE_TRY(cudaStreamSynchronize(s), "graph builder");
   cudaFree(scratch);
@@ -628,15 +627,15 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
   return profile_read(h->prof, bp_ms, lsd_ms, bp_launches, lsd_launches);
 }
 
-// Moves handle h to BP engine `engine` and, for the summary engine, state layout `packed` (descriptor
-// on the device, bounds, launch sizes); the handle is unchanged if the engine cannot run this problem.
-static int set_engine(vibe_handle* h, int engine, int packed) {
+// Moves handle h to BP engine `engine` (descriptor on the device, bounds, launch sizes); the handle is
+// unchanged if the engine cannot run this problem.
+static int set_engine(vibe_handle* h, int engine) {
   if (engine == VIBE_ENGINE_SUMMARY && h->t.n_flood > 0)
     return fail(VIBE_ERR_UNSUPPORTED, "flooding members run on the image engine only");
+  if (engine == VIBE_ENGINE_SUMMARY && h->t.XD == 0)
+    return fail(VIBE_ERR_UNSUPPORTED, "the summary engine takes columns of at most 16 checks");
   Tables t = h->t;
   t.engine = engine;
-  t.x_packed = packed;
-  vibe::bpx_layout(&t, h->L.msg_fp16);
   Launch L = h->L;
   L.one = t;
   L.bnd = bounds_over(&t, 1);
@@ -652,21 +651,19 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
                   int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm) {
   if (!h || !d_syndromes || B < 1) return fail(VIBE_ERR_INVALID, "NULL handle/syndromes or empty sample");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int start_engine = h->t.engine, start_packed = h->t.x_packed;
+  const int start_engine = h->t.engine;
   uint32_t* corr = nullptr;
   VIBE_CUDA(dalloc(&corr, (size_t)B * h->t.nw), "autotune");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_engine = start_engine, best_packed = start_packed, best_bp = 0, best_lsd = 0;
+  int best_engine = start_engine, best_bp = 0, best_lsd = 0;
   int rc = VIBE_OK;
-  // candidates: the image engine, and the summary engine in both state layouts
-  const int cand_engine[] = {VIBE_ENGINE_IMAGE, VIBE_ENGINE_SUMMARY, VIBE_ENGINE_SUMMARY};
-  const int cand_packed[] = {start_packed, 1, 0};
-  for (int ci = 0; ci < 3 && rc == VIBE_OK; ++ci) {
+  const int cand_engine[] = {VIBE_ENGINE_IMAGE, VIBE_ENGINE_SUMMARY};
+  for (int ci = 0; ci < 2 && rc == VIBE_OK; ++ci) {
     const int engine = cand_engine[ci];
-    if (set_engine(h, engine, cand_packed[ci]) != VIBE_OK) continue;   // the problem does not fit
+    if (set_engine(h, engine) != VIBE_OK) continue;   // the problem does not fit
     int& bp_cfg = h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm;
     const int bp_max = bp_cfg, lsd_max = h->L.lsd_blocks_per_sm;
     const int bp_try[] = {bp_max, (bp_max * 3 + 3) / 4, (bp_max + 1) / 2};
@@ -685,7 +682,7 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
-          best = ms; best_engine = engine; best_packed = cand_packed[ci];
+          best = ms; best_engine = engine;
           best_bp = bp_cfg; best_lsd = h->L.lsd_blocks_per_sm;
         }
       }
@@ -694,10 +691,10 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
   cudaEventDestroy(e1);
   cudaFree(corr);
   if (rc != VIBE_OK) {
-    set_engine(h, start_engine, start_packed);
+    set_engine(h, start_engine);
     return rc;
   }
-  if ((rc = set_engine(h, best_engine, best_packed)) != VIBE_OK) return rc;
+  if ((rc = set_engine(h, best_engine)) != VIBE_OK) return rc;
   (h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm) = best_bp;
   h->L.lsd_blocks_per_sm = best_lsd;
   if (engine_out) *engine_out = best_engine;
@@ -725,12 +722,6 @@ int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** o
     if (h->device != h0->device) return fail(VIBE_ERR_INVALID, "handles live on different devices");
     if (h->L.msg_fp16 != h0->L.msg_fp16) return fail(VIBE_ERR_INVALID, "handles mix FP16 and FP32 messages");
     desc[i] = h->t;
-    if (desc[i].engine == VIBE_ENGINE_SUMMARY && !desc[i].x_packed) {
-      // the mixed summary kernel runs the packed state layout; the batch's own copy of the
-      // descriptor (the batch has its own workspace) is laid out for it
-      desc[i].x_packed = 1;
-      vibe::bpx_layout(&desc[i], h->L.msg_fp16);
-    }
   }
   const Bounds b = bounds_over(desc.data(), count);
   int cur = -1;

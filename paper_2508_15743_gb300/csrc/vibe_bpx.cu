@@ -3,46 +3,50 @@
 // results as the image engine (vibe_bp.cu), which keeps a member's whole message image in shared
 // memory; a different layout.
 //
-// Why a warp per shot. The wavefront levels of a random serial order on these graphs are short: a
-// column conflicts with every column of its ~4 checks (~600 others), so a sweep of the d=11 problem
-// has ~1000 levels of ~32 columns. One warp matches that width and synchronises with __syncwarp.
+// Why a warp per (shot, member). The wavefront levels of a random serial order on these graphs are
+// short: a column conflicts with every column of its ~4 checks (~600 others), so a sweep of the d=11
+// problem has ~1000 levels of ~32 columns. One warp matches that width and synchronises with
+// __syncwarp. Each warp decodes one shot at a time (persistent, shots from a global counter), running
+// the members one after another with the iteration budget of the correction limit (Sec. III.D.2).
 //
-// Each warp decodes one shot at a time (persistent, shots from a global counter), running the members
-// one after another with the iteration budget of the correction limit (Sec. III.D.2).
+// Check-node state: a 16-byte summary per check in shared memory.
+//   x, y   the values m1 <= m2 held by up to two "holder" edges of the row (their positions p1, p2
+//          inside the check's CSR row, bits 0-7 and 8-15 of w; nh = number of valid holders, bits
+//          16-17; a row of fewer than two entries holds a phantom second holder, position 255, +inf)
+//   z      a floor F: every entry of the row that is not a holder has magnitude >= F, and the
+//          holders' magnitudes are <= F (after a rescan, F is the third smallest magnitude, or +inf)
+//   w      also carries the parity of the sign bits of the row's messages (bit 18), the syndrome bit
+//          (bit 19) and the check's parity (H e)_c XOR s_c (bit 20).
+// The minimum over the row without the edge at position p is then m2 if p == p1 and nh == 2, m1 if
+// p != p1 and nh >= 1, and +inf if F is +inf; otherwise (the only remaining holder asks, or no holder
+// is left) the row is rescanned first -- lazily, only when a column actually needs the answer. The
+// sign product without p is the sign parity XOR the sign of p's own message. Together these are
+// exactly the minimum and sign product that Algorithm 1's check update takes over N(c) \ v.
 //
-// Check-node state. For every check c the warp keeps in shared memory a 16-byte summary of the current
-// variable-to-check messages of its row: the smallest magnitude, the second smallest (with
-// multiplicity, +inf for a one-entry row), the edges holding them, and the parity of the sign bits
-// (bit 31 of the second holder word). The magnitude minimum over the row without edge e is then
-// (e == first holder ? second : smallest), and the sign parity without e is parity XOR sign(m_e):
-// exactly the minimum and sign product that Algorithm 1's check update takes over N(c) \ v, with no
-// row scan. The messages themselves (E floats or halves per warp, in CSC edge order so that a column's
-// are contiguous) stay in global memory, where the column update reads its old values and writes the
-// new ones. Two layouts of the rest of a warp's state (same results): "bytes" keeps the decision
-// bits in shared memory and one byte per check for the syndrome and the check parity; "packed" moves
-// the decision bits to global memory (each lane fetches its column's bit with the column's data, and
-// only that column changes it) and packs syndrome and parity 32 bits to a word, for ~16 bytes of
-// shared memory per check and more resident warps. Measured on circuit-level colour codes, packed is
-// faster at d=5..9 and bytes at d=11 (the host picks by the number of checks; the tuner times both).
+// Keeping the summary exact after the edge at position p gets the new magnitude x:
+//   p holds m1:   x <= m2: m1 = x;  m2 < x <= F: the holders swap;  x > F: p leaves (nh - 1)
+//   p holds m2:   x < m1: the holders swap;  x <= F: m2 = x;  x > F: p leaves
+//   otherwise:    x < F: p becomes a holder (an empty slot, or the larger holder is evicted and its
+//                 value becomes the floor, or x itself becomes the floor if x >= m2)
+// With the floor most holders that grow stay answerable; on circuit-level colour codes this needs
+// ~2.5x fewer row rescans per sweep than two holders without a floor (117 vs 296 at d=11).
 //
-// Keeping the summary exact after column v replaces its message on c with magnitude x:
-//   v holds the smallest:  x <= second -> smallest = x;  else the row is rescanned;
-//   v holds the second:    x > second -> rescan; x < smallest -> v and the first holder swap places;
-//                          else second = x;
-//   otherwise:             x < smallest -> v holds the smallest, the old one the second;
-//                          x < second -> v holds the second.
-// Holding both holders keeps rescans rare even when many messages tie (equal priors at the start).
-// Every check is touched by one column per level, so the updates of a level never collide. Rescans
-// are queued and done after the level by the whole warp (a minimum/second-minimum reduction over the
-// row's messages), before any later level reads the summary. A column's global reads (checks, old
-// messages, prior) do not depend on the level before it, so each lane fetches its next column while
-// the current level finishes.
+// Messages. A member's variable-to-check messages live in the warp's global scratch in the member's
+// schedule order: the columns of one level (and of one 32-column chunk) are consecutive, so a chunk's
+// messages form one contiguous block and its stores coalesce. The column update never reads its old
+// messages: it needs only their signs, kept with its previous decision in a 32-bit state word per
+// schedule position (bit k: sign of the message to its k-th check; bit 31: decision). Messages are
+// read only by rescans, through a per-member map from each CSR entry of H to its message slot.
+//
+// Pipeline: each lane fetches the column data (schedule record -> checks with row positions, prior,
+// state word) two chunks ahead; none of it is written by the chunks in between.
 //
 // Arithmetic equals the oracle's bit for bit: same per-node operation order (__fadd_rn/__fmul_rn), min
 // and sign exact, FP16 storage with -0 stored as +0.
 #include <type_traits>
 
 #include "vibe_internal.cuh"
+#include "vibe_summary.cuh"
 
 namespace vibe {
 namespace {
@@ -54,10 +58,8 @@ template <>
 struct XMsg<float> {
   __device__ __forceinline__ static float load(const float* p) { return __ldcg(p); }
   __device__ __forceinline__ static float value(float x) { return x; }
-  __device__ __forceinline__ static float store(float* p, float x) {
-    __stcg(p, x);
-    return x;
-  }
+  __device__ __forceinline__ static float round(float x) { return x; }
+  __device__ __forceinline__ static float from(float x) { return x; }
 };
 
 template <>
@@ -66,183 +68,142 @@ struct XMsg<__half> {
     return __ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p)));
   }
   __device__ __forceinline__ static float value(__half x) { return __half2float(x); }
-  // rounds to half, stores -0 as +0, returns the stored value as a float
-  __device__ __forceinline__ static float store(__half* p, float x) {
+  // rounds to half, -0 as +0, and returns the stored value as a float
+  __device__ __forceinline__ static float round(float x) {
     unsigned short h = __half_as_ushort(__float2half_rn(x));
     if (h == 0x8000u) h = 0;
-    __stcg(reinterpret_cast<unsigned short*>(p), h);
     return __half2float(__ushort_as_half(h));
   }
+  __device__ __forceinline__ static __half from(float x) { return __float2half_rn(x); }   // x already rounded
 };
+
+template <typename MT>
+__device__ __forceinline__ void store_msg(MT* p, float x) {
+  if constexpr (std::is_same<MT, float>::value) __stcs(p, x);
+  else __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(x)));
+}
+
+constexpr uint32_t kInfBits = 0x7f800000u;
+constexpr uint32_t kDecBit = 1u << 31;   // decision bit of a column state word
 
 __device__ __forceinline__ uint32_t sign_bit(float x) { return __float_as_uint(x) >> 31; }
 
-__device__ __forceinline__ bool is_finite_bits(float x) {
-  return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
-}
+__device__ __forceinline__ bool is_finite_bits(float x) { return (__float_as_uint(x) & kInfBits) != kInfBits; }
 
-// Shared state of one warp for its current shot.
-struct XShared {
-  float4* summ;     // m check summaries (smallest, second, holder edges, sign parity)
-  uint32_t* s32;    // packed: ceil(m/32) syndrome words
-  uint32_t* par32;  // packed: ceil(m/32) words, (H e) XOR s
-  uint8_t* s8;      // bytes: m syndrome bytes
-  uint8_t* par8;    // bytes: m bytes, (H e)_c XOR s_c
-  uint32_t* dec;    // nw: the member's decisions, bit-packed (packed: in the warp's global scratch)
-  int32_t* rlist;   // 32 * DP: checks to rescan after the current chunk of 32 columns
-};
-
-// Blocks per SM the register budget targets (16 warps per SM).
-template <typename MT>
-struct MinBlocksX { static constexpr int value = 16 / kBpxWarpsPerCta; };
-
-// What a column update reads from global memory: its checks, its current messages and its prior.
-// None of it changes before the column's own update (a column's messages are written only by that
-// column), so it can be fetched a level early.
-template <int DP>
-struct ColData {
-  uint32_t v, e0;
-  uint32_t e_old;   // the column's current decision
-  int deg;
-  float lam;
-  int c[DP];
-  float o[DP];
-};
-
-template <typename MT, int DP, bool PK>
-__device__ __forceinline__ void fetch_column(uint2 rec, const Tables& t, const MT* msg, const uint32_t* dec,
-                                             ColData<DP>& d) {
-  d.v = rec.x & 0xffffffu;
-  d.deg = (int)(rec.x >> 24);
-  d.e0 = rec.y;
-  d.lam = __ldg(t.lam + d.v);
-  d.e_old = PK ? (__ldcg(dec + (d.v >> 5)) >> (d.v & 31)) & 1u : 0u;   // only column v writes its bit
-#pragma unroll
-  for (int k = 0; k < DP; ++k) {
-    d.c[k] = 0;
-    d.o[k] = 0.0f;
-    if (k < d.deg) {
-      d.c[k] = __ldg(t.rowidx + d.e0 + k);
-      d.o[k] = XMsg<MT>::value(XMsg<MT>::load(msg + d.e0 + k));
-    }
-  }
-}
-
-// Serial-V update of column v (deg checks, edges e0 .. e0 + deg - 1 in ascending check order).
-template <typename MT, int DP, bool PK>
-__device__ __forceinline__ void update_column_x(const ColData<DP>& d, const Tables& t, float alpha, MT* msg,
-                                                const XShared& X, int* rcount, float* lpost) {
-  const uint32_t v = d.v, e0 = d.e0;
-  const int deg = d.deg;
-  const int* c = d.c;
-  const float* o = d.o;
-  const float lamv = d.lam;
-  float mcv[DP];
-#pragma unroll
-  for (int k = 0; k < DP; ++k) {
-    mcv[k] = 0.0f;
-    if (k < deg) {
-      const float4 sm = X.summ[c[k]];
-      const bool holder = __float_as_uint(sm.z) == e0 + k;
-      const float mn = holder ? sm.y : sm.x;
-      const uint32_t sk = PK ? X.s32[c[k] >> 5] >> (c[k] & 31) : (uint32_t)X.s8[c[k]];
-      const uint32_t neg = ((__float_as_uint(sm.w) >> 31) ^ sign_bit(o[k]) ^ sk) & 1u;
-      const float mag = __fmul_rn(alpha, mn);
-      mcv[k] = neg ? -mag : mag;
-    }
-  }
-  float L = lamv;
-#pragma unroll
-  for (int k = 0; k < DP; ++k)
-    if (k < deg) L = __fadd_rn(L, mcv[k]);
-  float pre = lamv;  // lambda + m_0 + ... + m_{k-1}, the shared head of every exclusion sum
-#pragma unroll
-  for (int k = 0; k < DP; ++k) {
-    if (k < deg) {
-      float a = pre;
-#pragma unroll
-      for (int k2 = k + 1; k2 < DP; ++k2)
-        if (k2 < deg) a = __fadd_rn(a, mcv[k2]);
-      const float x = XMsg<MT>::store(msg + e0 + k, a);
-      pre = __fadd_rn(pre, mcv[k]);
-      // summary maintenance
-      const float nm = fabsf(x);
-      const uint32_t e = e0 + k;
-      float4 s = X.summ[c[k]];   // this level's only reader and writer of check c
-      uint32_t i1 = __float_as_uint(s.z), i2 = __float_as_uint(s.w) & 0x7fffffffu;
-      const uint32_t sg = (__float_as_uint(s.w) >> 31) ^ sign_bit(o[k]) ^ sign_bit(x);
-      bool rescan = false;
-      if (e == i1) {
-        if (nm <= s.y) s.x = nm;
-        else rescan = true;
-      } else if (e == i2) {
-        if (nm > s.y) rescan = true;
-        else if (nm < s.x) { s.y = s.x; i2 = i1; s.x = nm; i1 = e; }
-        else s.y = nm;
-      } else if (nm < s.x) {
-        s.y = s.x; i2 = i1; s.x = nm; i1 = e;
-      } else if (nm < s.y) {
-        s.y = nm; i2 = e;
-      }
-      s.z = __uint_as_float(i1);
-      s.w = __uint_as_float(i2 | (sg << 31));
-      X.summ[c[k]] = s;
-      if (rescan) X.rlist[atomicAdd(rcount, 1)] = c[k];
-    }
-  }
-  const uint32_t e_new = L <= 0.0f ? 1u : 0u;
-  const uint32_t bit = 1u << (v & 31);
-  const uint32_t e_old = PK ? d.e_old : (X.dec[v >> 5] & bit) ? 1u : 0u;
-  if (e_new != e_old) {
-    atomicXor(&X.dec[v >> 5], bit);
-#pragma unroll
-    for (int k = 0; k < DP; ++k) {
-      if (k < deg) {
-        if (PK) atomicXor(&X.par32[c[k] >> 5], 1u << (c[k] & 31));
-        else X.par8[c[k]] ^= 1u;   // this level's only writer of check c's byte
-      }
-    }
-  }
-  if (lpost) lpost[v] = L;
-}
-
-// (value, edge) pairs ordered by value, then edge
+// (value, position) pairs ordered by value, then position
 __device__ __forceinline__ bool before(float a, uint32_t ia, float b, uint32_t ib) {
   return a < b || (a == b && ia < ib);
 }
 
-// Warp-cooperative rescan of check c: smallest and second smallest magnitude (with multiplicity) and
-// their edges over the row's current messages; the sign parity is kept as it is.
+struct Top3 {
+  float a1, a2, a3;
+  uint32_t q1, q2;
+  __device__ __forceinline__ void init() {
+    a1 = a2 = a3 = __uint_as_float(kInfBits);
+    q1 = q2 = 255u;
+  }
+  __device__ __forceinline__ void insert(float x, uint32_t q) {
+    const bool b1 = before(x, q, a1, q1), b2 = before(x, q, a2, q2);
+    a3 = b2 ? a2 : fminf(a3, x);
+    a2 = b1 ? a1 : (b2 ? x : a2);
+    q2 = b1 ? q1 : (b2 ? q : q2);
+    a1 = b1 ? x : a1;
+    q1 = b1 ? q : q1;
+  }
+};
+
+// Summary storage of a message type: 12 bytes per check for FP32 messages, 8 for FP16.
 template <typename MT>
-__device__ __forceinline__ void rescan_row(int c, const Tables& t, const MT* msg, float4* summ, int lane) {
-  float m1 = __int_as_float(0x7f800000), m2 = m1;
-  uint32_t i1 = 0x7fffffffu, i2 = 0x7fffffffu;
-  const int b = __ldg(t.rowptr + c), e = __ldg(t.rowptr + c + 1);
-  for (int q = b + lane; q < e; q += 32) {
-    const uint32_t ed = __ldg(t.row_edge + q);
-    const float a = fabsf(XMsg<MT>::value(XMsg<MT>::load(msg + ed)));
-    if (before(a, ed, m1, i1)) { m2 = m1; i2 = i1; m1 = a; i1 = ed; }
-    else if (before(a, ed, m2, i2)) { m2 = a; i2 = ed; }
+using SumStore = typename std::conditional<std::is_same<MT, float>::value, SumStore32, SumStore16>::type;
+
+template <typename MT>
+__device__ __forceinline__ SumStore<MT> sum_store(unsigned char* p, int m);
+template <>
+__device__ __forceinline__ SumStore32 sum_store<float>(unsigned char* p, int m) {
+  return SumStore32{reinterpret_cast<float2*>(p), reinterpret_cast<uint32_t*>(p + ((8 * (size_t)m + 15) & ~(size_t)15))};
+}
+template <>
+__device__ __forceinline__ SumStore16 sum_store<__half>(unsigned char* p, int m) {
+  return SumStore16{reinterpret_cast<uint2*>(p)};
+}
+
+// Warp-cooperative rescan of check c, whose CSR row is b .. b + d: the two smallest magnitudes with
+// their positions and the third smallest as the floor; the flags are kept.
+template <typename MT>
+__device__ __forceinline__ void rescan_row(int c, int b, int d, const uint32_t* rmap, const MT* msg,
+                                           const SumStore<MT>& S, int lane) {
+  uint32_t loc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int q = lane + 32 * u;
+    loc[u] = q < d ? __ldg(rmap + b + q) : 0u;
+  }
+  Top3 T;
+  T.init();
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int q = lane + 32 * u;
+    if (q < d) T.insert(fabsf(XMsg<MT>::value(XMsg<MT>::load(msg + loc[u]))), (uint32_t)q);
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
-    const float n1 = __shfl_xor_sync(kFull, m1, off), n2 = __shfl_xor_sync(kFull, m2, off);
-    const uint32_t j1 = __shfl_xor_sync(kFull, i1, off), j2 = __shfl_xor_sync(kFull, i2, off);
-    if (before(n1, j1, m1, i1)) {   // the other's first wins; second = better of my first, its second
-      if (before(m1, i1, n2, j2)) { m2 = m1; i2 = i1; } else { m2 = n2; i2 = j2; }
-      m1 = n1; i1 = j1;
-    } else if (before(n1, j1, m2, i2)) {
-      m2 = n1; i2 = j1;
-    }
+    const float b1 = __shfl_xor_sync(kFull, T.a1, off), b2 = __shfl_xor_sync(kFull, T.a2, off);
+    const float b3 = __shfl_xor_sync(kFull, T.a3, off);
+    const uint32_t r1 = __shfl_xor_sync(kFull, T.q1, off), r2 = __shfl_xor_sync(kFull, T.q2, off);
+    T.insert(b1, r1);
+    T.insert(b2, r2);
+    T.insert(b3, 255u);
   }
   if (lane == 0) {
-    float4 s = summ[c];
-    s.x = m1; s.y = m2; s.z = __uint_as_float(i1);
-    s.w = __uint_as_float((__float_as_uint(s.w) & 0x80000000u) | i2);
-    summ[c] = s;
+    SumV v = S.load(c);
+    v.m1 = T.a1;
+    v.m2 = T.a2;
+    v.p1 = T.q1;
+    v.p2 = T.q2;
+    v.F = floor_round<!std::is_same<MT, float>::value>(T.a3);
+    S.store(c, v);
   }
 }
 
+// What a column update reads besides the check summaries: its schedule record (column, degree, first
+// message slot), its checks with their row positions, its prior and its state word. None of it is
+// written by the chunks in between, so it is copied into a shared-memory ring with cp.async ahead of
+// use: the records of chunk c+2 and the rest of chunk c+1 while chunk c is updated. The copies hold
+// no registers, so the warp waits for nothing it does not yet need.
+template <int DP>
+struct XRing {
+  static constexpr int XP = (DP + 3) / 4 * 4;   // words of a column record
+  static constexpr int kStwWords = 48;          // the 16-byte blocks covering 32 state words
+  static constexpr int kRecBytes = 3 * 32 * 8;  // three record slots: chunk q's records stay until its update
+  static constexpr int kStageBytes = 32 * XP * 4 + 32 * 4 + kStwWords * 4;
+  static constexpr int kBytes = kRecBytes + 2 * kStageBytes;
+  unsigned char* base;
+  __device__ __forceinline__ uint2* rec(uint32_t q) { return reinterpret_cast<uint2*>(base) + (q % 3u) * 32; }
+  __device__ __forceinline__ unsigned char* stage(uint32_t q) { return base + kRecBytes + (q & 1u) * kStageBytes; }
+  __device__ __forceinline__ uint32_t* xc(uint32_t q) { return reinterpret_cast<uint32_t*>(stage(q)); }
+  __device__ __forceinline__ float* lam(uint32_t q) { return reinterpret_cast<float*>(stage(q) + 32 * XP * 4); }
+  __device__ __forceinline__ uint32_t* stw(uint32_t q) {
+    return reinterpret_cast<uint32_t*>(stage(q) + 32 * XP * 4 + 32 * 4);
+  }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// cp.async in its plain form with the source size stated (equal to the copy size). Read-only tables
+// may be cached in L1 (.ca); the per-warp state words, written through L2 by earlier sweeps, are
+// copied with .cg so that no L1 line can be stale.
+__device__ __forceinline__ void cp_async_ca4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_ca8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_cg16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // A chunk of a sweep: up to 32 consecutive schedule entries [cs, min(cs + 32, e)) of level l, whose
 // entries end at e. l == nl marks the end of the sweep.
@@ -251,65 +212,260 @@ struct Chunk {
   uint32_t cs, e;
 };
 
-__device__ __forceinline__ Chunk first_chunk(const uint32_t* lo) { return Chunk{0, __ldg(lo), __ldg(lo + 1)}; }
+// The member's level offsets lo[0 .. nl] as the chunk walker needs them, one level at a time: lane l
+// holds lo[32k + l] of the current window k and lo[32k + 32 + l] of the next one, loaded 32 levels
+// before it is needed, so that starting a level costs a shuffle instead of a dependent global load.
+struct LevelWin {
+  const uint32_t* lo;
+  int nl, k;
+  uint32_t cur, nxt;
+  __device__ __forceinline__ uint32_t load(int x, int lane) const {
+    return x + lane <= nl ? __ldg(lo + x + lane) : 0u;
+  }
+  __device__ __forceinline__ void start(const uint32_t* lo_, int nl_, int lane) {
+    lo = lo_;
+    nl = nl_;
+    k = 0;
+    cur = load(0, lane);
+    nxt = load(32, lane);
+  }
+  // lo[x]; x never decreases and grows by at most one per call (warp-uniform)
+  __device__ __forceinline__ uint32_t get(int x, int lane) {
+    if (x >= 32 * (k + 1)) {
+      ++k;
+      cur = nxt;
+      nxt = load(32 * (k + 1), lane);
+    }
+    return __shfl_sync(kFull, cur, x - 32 * k);
+  }
+};
 
-__device__ __forceinline__ Chunk next_chunk(const Chunk& c, const uint32_t* lo, int nl) {
-  if (c.l >= nl) return c;
+__device__ __forceinline__ Chunk first_chunk(LevelWin& W, int lane) {
+  const uint32_t a = W.get(0, lane);
+  return Chunk{0, a, W.get(1, lane)};
+}
+
+__device__ __forceinline__ Chunk next_chunk(const Chunk& c, LevelWin& W, int lane) {
+  if (c.l >= W.nl) return c;
   if (c.cs + 32 < c.e) return Chunk{c.l, c.cs + 32, c.e};
-  return Chunk{c.l + 1, c.e, c.l + 1 < nl ? __ldg(lo + c.l + 2) : c.e};
+  return Chunk{c.l + 1, c.e, c.l + 1 < W.nl ? W.get(c.l + 2, lane) : c.e};
 }
 
 __device__ __forceinline__ bool in_chunk(const Chunk& c, int nl, int lane) {
   return c.l < nl && c.cs + (uint32_t)lane < c.e;
 }
 
+// Per-warp views of the current pair's state.
+template <typename MT>
+struct XState {
+  SumStore<MT> S;    // shared: m check summaries
+  MT* msg;           // global: E messages in the member's schedule order
+  uint32_t* stw;     // global: n column state words in schedule order
+  uint32_t* dec;     // global: nw decision bits in column order
+  const uint2* rec;  // the member's schedule records
+  const uint32_t* rmap;   // the member's CSR-entry -> message-slot map
+};
+
+// Serial-V update of one chunk (lane's column d when active). Returns the lane's change of the number
+// of unsatisfied checks.
+// The lane's column as the update sees it (read from the ring).
+template <int DP>
+struct XCol {
+  uint32_t v, deg, spos, st;
+  float lam;
+  uint32_t ent[DP];   // (check << 8) | position in the check's row
+};
+
+template <typename MT, int DP>
+__device__ __forceinline__ int update_chunk(bool active, const XCol<DP>& d, uint32_t j, const Tables& t, float alpha,
+                                            const XState<MT>& X, float* lpost, int lane, uint32_t& my_rescans) {
+  constexpr bool kHalf = !std::is_same<MT, float>::value;
+  // check-to-variable messages from the summaries (Algorithm 1's check update over N(c) \ v)
+  float mcv[DP];
+  uint32_t need = 0u;
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    mcv[k] = 0.0f;
+    if (active && (uint32_t)k < d.deg) {
+      const SumV s = X.S.load((int)(d.ent[k] >> 8));
+      float mn;
+      if (!sum_query(s, d.ent[k] & 0xffu, mn)) need |= 1u << k;
+      const float mag = __fmul_rn(alpha, mn);
+      mcv[k] = ((s.sgn ^ s.syn ^ (d.st >> k)) & 1u) ? -mag : mag;   // sign parity, syndrome, own sign
+    }
+  }
+  if (__any_sync(kFull, need != 0u)) {
+    // rescan every check whose summary could not answer (checks of one level are touched by one
+    // column each, so the rows are distinct), then ask again. Row bounds of all of them first.
+    int rb[DP], rd[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      rb[k] = 0;
+      rd[k] = 0;
+      if ((need >> k) & 1u) {
+        const int c = (int)(d.ent[k] >> 8);
+        rb[k] = __ldg(t.rowptr + c);
+        rd[k] = __ldg(t.rowptr + c + 1);
+      }
+    }
+    uint32_t pend = need;
+    while (__any_sync(kFull, pend != 0u)) {
+      const int k0 = __ffs(pend) - 1;
+      uint32_t csel = 0u;
+      int bsel = 0, esel = 0;
+#pragma unroll
+      for (int k = 0; k < DP; ++k) {
+        csel = k == k0 ? d.ent[k] >> 8 : csel;
+        bsel = k == k0 ? rb[k] : bsel;
+        esel = k == k0 ? rd[k] : esel;
+      }
+      uint32_t bal = __ballot_sync(kFull, pend != 0u);
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        bal &= bal - 1u;
+        const int b = __shfl_sync(kFull, bsel, src);
+        rescan_row<MT>((int)__shfl_sync(kFull, csel, src), b, __shfl_sync(kFull, esel, src) - b, X.rmap, X.msg,
+                       X.S, lane);
+        ++my_rescans;
+      }
+      pend &= pend - 1u;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < DP; ++k)
+      if ((need >> k) & 1u) {
+        const SumV s = X.S.load((int)(d.ent[k] >> 8));
+        float mn;
+        sum_query(s, d.ent[k] & 0xffu, mn);
+        const float mag = __fmul_rn(alpha, mn);
+        mcv[k] = ((s.sgn ^ s.syn ^ (d.st >> k)) & 1u) ? -mag : mag;
+      }
+  }
+  if (!active) return 0;
+  const uint32_t deg = d.deg;
+  float L = d.lam;
+#pragma unroll
+  for (int k = 0; k < DP; ++k)
+    if ((uint32_t)k < deg) L = __fadd_rn(L, mcv[k]);
+  const uint32_t e_new = L <= 0.0f ? 1u : 0u;
+  const bool flip = e_new != ((d.st & kDecBit) ? 1u : 0u);
+  uint32_t st = e_new << 31;
+  int dpar = 0;
+  float pre = d.lam;   // lambda + m_0 + ... + m_{k-1}, the shared head of every exclusion sum
+  MT* out = X.msg + d.spos;
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    if ((uint32_t)k < deg) {
+      float a = pre;
+#pragma unroll
+      for (int k2 = k + 1; k2 < DP; ++k2)
+        if ((uint32_t)k2 < deg) a = __fadd_rn(a, mcv[k2]);
+      const float x = XMsg<MT>::round(a);
+      store_msg<MT>(out + k, x);   // streamed: read again only by rescans
+      pre = __fadd_rn(pre, mcv[k]);
+      const uint32_t sx = sign_bit(x);
+      st |= sx << k;
+      // this level's only reader and writer of the check: the full summary update for holders and
+      // for edges that drop below the floor, a flag update for the rest
+      const int c = (int)(d.ent[k] >> 8);
+      const uint32_t p = d.ent[k] & 0xffu;
+      const SumV s = X.S.load(c);
+      const float ax = fabsf(x);
+      const bool sflip = (((d.st >> k) ^ sx) & 1u) != 0u;
+      if (flip) dpar += (s.par ^ 1u) ? 1 : -1;
+      if (sum_slow(s, p, ax)) {
+        SumV u = sum_update<kHalf>(s, p, ax);
+        u.sgn ^= sflip ? 1u : 0u;
+        u.par ^= flip ? 1u : 0u;
+        X.S.store(c, u);
+      } else if (sflip || flip) {
+        X.S.flip_flags(c, sflip, flip);
+      }
+    }
+  }
+  __stcs(X.stw + j, st);
+  if (flip) atomicXor(X.dec + (d.v >> 5), 1u << (d.v & 31));
+  if (lpost) lpost[d.v] = L;
+  return dpar;
+}
+
+// Ring copies for chunk number q. Records: each active lane copies its own 8-byte schedule record.
+template <int DP>
+__device__ __forceinline__ void issue_rec(XRing<DP>& R, uint32_t q, const Chunk& c, int nl, int lane, const uint2* rec) {
+  if (in_chunk(c, nl, lane)) cp_async_ca8(R.rec(q) + lane, rec + c.cs + lane);
+}
+
+// Column data: each active lane copies its column's record and prior (its schedule record is in the
+// ring already); lanes 0..8 copy the 16-byte blocks that cover the chunk's state words.
+template <int DP>
+__device__ __forceinline__ void issue_data(XRing<DP>& R, uint32_t q, const Chunk& c, int nl, int lane, const Tables& t,
+                                           const uint32_t* stw) {
+  if (c.l >= nl) return;
+  if (in_chunk(c, nl, lane)) {
+    const uint32_t v = R.rec(q)[lane].x & 0xffffffu;
+    const uint32_t* src = t.xcol + (size_t)v * t.XP;
+    uint32_t* dst = R.xc(q) + lane * XRing<DP>::XP;
+#pragma unroll
+    for (int b = 0; b < XRing<DP>::XP / 4; ++b)
+      if (4 * b < t.XP) cp_async_cg16(dst + 4 * b, src + 4 * b);
+    cp_async_ca4(R.lam(q) + lane, t.lam + v);
+  }
+  const uint32_t first = c.cs & ~3u, end = min(c.cs + 32u, c.e);
+  if ((uint32_t)lane < (end - first + 3u) / 4u) cp_async_cg16(R.stw(q) + 4 * lane, stw + first + 4 * lane);
+}
+
+template <int DP>
+__device__ __forceinline__ void read_col(XRing<DP>& R, uint32_t q, const Chunk& c, int lane, bool act, XCol<DP>& d) {
+  if (!act) {
+    d.deg = 0u;
+    return;
+  }
+  const uint2 r = R.rec(q)[lane];
+  d.v = r.x & 0xffffffu;
+  d.deg = r.x >> 24;
+  d.spos = r.y;
+  d.lam = R.lam(q)[lane];
+  d.st = R.stw(q)[(c.cs & 3u) + lane];
+  const uint4* src = reinterpret_cast<const uint4*>(R.xc(q) + lane * XRing<DP>::XP);
+#pragma unroll
+  for (int b = 0; b < XRing<DP>::XP / 4; ++b) {
+    const uint4 x = src[b];
+    if (4 * b + 0 < DP) d.ent[4 * b + 0] = x.x;
+    if (4 * b + 1 < DP) d.ent[4 * b + 1] = x.y;
+    if (4 * b + 2 < DP) d.ent[4 * b + 2] = x.z;
+    if (4 * b + 3 < DP) d.ent[4 * b + 3] = x.w;
+  }
+}
+
 // Decodes shot `shot` of problem t with one warp. base: the warp's shared memory; gs: its global
-// scratch (messages, posterior, LLR accumulator, candidate records).
-template <typename MT, int DP, bool PK>
+// scratch (messages, state words, decisions, posterior, LLR accumulator, candidate records).
+template <typename MT, int DP>
 __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, uint32_t shot, unsigned char* base,
-                                              unsigned char* gs, int lane, unsigned long long& my_iters,
-                                              unsigned long long& my_shots, unsigned long long& my_fail,
-                                              unsigned long long& my_rescans) {
-  const int n = t.n, m = t.m, K = t.K, M = t.M, T = t.T, nw = t.nw, kw = t.kw;
-  const int mw = t.mw;
-  const int m4 = (m + 3) >> 2;
-  XShared X;
-  X.summ = reinterpret_cast<float4*>(base + t.xo_summ);
-  X.s32 = reinterpret_cast<uint32_t*>(base + t.xo_s);
-  X.par32 = reinterpret_cast<uint32_t*>(base + t.xo_par);
-  X.s8 = base + t.xo_s;
-  X.par8 = base + t.xo_par;
-  X.dec = PK ? reinterpret_cast<uint32_t*>(gs + t.xg_dec) : reinterpret_cast<uint32_t*>(base + t.xo_dec);
-  X.rlist = reinterpret_cast<int32_t*>(base + t.xo_rl);
-  volatile int* rcount = reinterpret_cast<volatile int*>(base + t.xo_rc);
-  MT* msg = reinterpret_cast<MT*>(gs + t.xg_msg);
+                                              unsigned char* gs, int lane, uint32_t& my_iters,
+                                              uint32_t& my_shots, uint32_t& my_fail, uint32_t& my_rescans) {
+  const int n = t.n, m = t.m, K = t.K, M = t.M, T = t.T, nw = t.nw, kw = t.kw, mw = t.mw;
+  XState<MT> X;
+  X.S = sum_store<MT>(base + XRing<DP>::kBytes, m);
+  X.msg = reinterpret_cast<MT*>(gs + t.xg_msg);
+  X.stw = reinterpret_cast<uint32_t*>(gs + t.xg_st);
+  X.dec = reinterpret_cast<uint32_t*>(gs + t.xg_dec);
   float* lpost = reinterpret_cast<float*>(gs + t.xg_lpost);
   float* acc = reinterpret_cast<float*>(gs + t.xg_acc);
   uint32_t* cand = reinterpret_cast<uint32_t*>(gs + t.xg_cand);
   float* cpost = reinterpret_cast<float*>(gs + t.xg_cpost);
 
   const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
-  uint32_t any = 0;
-  if (PK) {
-    for (int w = lane; w < mw; w += 32) {
-      const int rem = m - 32 * w;
-      const uint32_t x = __ldg(syn + w) & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
-      X.s32[w] = x;
-      any |= x;
-    }
-  } else {
-    for (int c = lane; c < 4 * m4; c += 32) {
-      const uint32_t b = c < m ? (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u : 0u;
-      X.s8[c] = (uint8_t)b;
-      any |= b;
-    }
+  int nsyn = 0;
+  for (int w = lane; w < mw; w += 32) {
+    const int rem = m - 32 * w;
+    nsyn += __popc(__ldg(syn + w) & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u)));
   }
-  any = __any_sync(kFull, any);
-  __syncwarp();
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) nsyn += __shfl_xor_sync(kFull, nsyn, off);
   ++my_shots;
   uint32_t* out_corr = a.corr + (size_t)shot * a.corr_stride;
 
-  if (!any && !a.want_soft) {
+  if (nsyn == 0 && !a.want_soft) {
     // s = 0: every member converges in iteration 1 to e = 0; member 0 is chosen
     for (int w = lane; w < nw; w += 32) out_corr[w] = 0u;
     if (a.logical)
@@ -336,85 +492,88 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
   for (int i = 0; i < K; ++i) {
     const int budget = ncand < M ? T : __shfl_sync(kFull, c_t, M - 1) - 1;
     if (budget <= 0) break;
-    // member init: prior messages and summaries, decisions 0, parity = s
-    {
-      for (int c = lane; c < m; c += 32) X.summ[c] = __ldg(t.sum_init + c);
-      const uint4* src = reinterpret_cast<const uint4*>(t.msg_csc);
-      uint4* dst = reinterpret_cast<uint4*>(msg);
-      const int nv = (int)(((size_t)t.E * sizeof(MT) + 15) / 16);
-      for (int q = lane; q < nv; q += 32) __stcg(dst + q, __ldg(src + q));
-      if (PK) {
-        for (int w = lane; w < nw; w += 32) __stcg(X.dec + w, 0u);
-        for (int w = lane; w < mw; w += 32) X.par32[w] = X.s32[w];
-      } else {
-        for (int w = lane; w < nw; w += 32) X.dec[w] = 0u;
-        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(X.s8);
-        uint32_t* p32 = reinterpret_cast<uint32_t*>(X.par8);
-        for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
-      }
-      if (lane == 0) *rcount = 0;
+    X.rec = t.xrec + (size_t)i * n;
+    X.rmap = t.xrmap + (size_t)i * t.E;
+    // member init: prior summaries with this shot's syndrome (parity = s), prior messages in the
+    // member's schedule order, state words and decisions 0
+    for (int c = lane; c < m; c += 32) {
+      const float4 s = __ldg(t.xsum + c);
+      const uint32_t w = __float_as_uint(s.w);
+      SumV v;
+      v.m1 = s.x;
+      v.m2 = s.y;
+      v.F = s.z;
+      v.p1 = w & 0xffu;
+      v.p2 = (w >> 8) & 0xffu;
+      v.sgn = (w >> 18) & 1u;
+      v.syn = v.par = (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u;
+      X.S.store(c, v);
     }
+    for (int j = lane; j < n; j += 32) {
+      const uint2 r = __ldg(X.rec + j);
+      const float x = XMsg<MT>::round(__ldg(t.lam + (r.x & 0xffffffu)));
+      for (uint32_t k = 0; k < (r.x >> 24); ++k) store_msg<MT>(X.msg + r.y + k, x);
+      __stcg(X.stw + j, 0u);
+    }
+    for (int w = lane; w < nw; w += 32) __stcg(X.dec + w, 0u);
     __syncwarp();
-    const uint2* rec = t.sched_rec + (size_t)i * n;
     const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
     const int nl = __ldg(t.nlev + i);
+    XRing<DP> R{base};
     const float alpha = __ldg(t.alpha_m + i);   // member i's scaling factor
+    int unsat = nsyn;
     int conv = 0;
-    ColData<DP> cd;
     for (int it = 1; it <= budget; ++it) {
       // the posterior is needed after the last possible sweep of a member that may end without
       // converging (LLR average) and, for soft output, after every sweep
       float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
-      // the sweep in chunks of up to 32 columns of one level, one column per lane; rescans after each
-      // chunk (later chunks of the same level touch other checks). Software pipeline: chunk j+1's
-      // column data (checks, old messages, prior) is fetched before chunk j is updated -- a column's
-      // messages are written only by that column, so the early read sees the same values -- and the
-      // schedule records two chunks ahead.
-      Chunk c = first_chunk(lo);
-      Chunk c1 = next_chunk(c, lo, nl);
-      Chunk c2 = next_chunk(c1, lo, nl);
-      if (in_chunk(c, nl, lane)) fetch_column<MT, DP, PK>(__ldg(rec + c.cs + lane), t, msg, X.dec, cd);
-      uint2 r1 = in_chunk(c1, nl, lane) ? __ldg(rec + c1.cs + lane) : make_uint2(0u, 0u);
-      while (c.l < nl) {
-        ColData<DP> cdn;
-        if (in_chunk(c1, nl, lane)) fetch_column<MT, DP, PK>(r1, t, msg, X.dec, cdn);
-        const uint2 r2 = in_chunk(c2, nl, lane) ? __ldg(rec + c2.cs + lane) : make_uint2(0u, 0u);
-        if (in_chunk(c, nl, lane)) update_column_x<MT, DP, PK>(cd, t, alpha, msg, X, const_cast<int*>(rcount), lp);
+      // the sweep in chunks of up to 32 columns of one level, one column per lane, through the ring:
+      // q counts chunks; the records of chunk q+2 and the column data of chunk q+1 are in flight while
+      // chunk q is updated
+      LevelWin W;
+      W.start(lo, nl, lane);
+      Chunk c0 = first_chunk(W, lane);
+      Chunk c1 = next_chunk(c0, W, lane);
+      Chunk c2 = next_chunk(c1, W, lane);
+      issue_rec(R, 0u, c0, nl, lane, X.rec);
+      issue_rec(R, 1u, c1, nl, lane, X.rec);
+      cp_async_commit();
+      cp_async_wait<0>();
+      issue_data<DP>(R, 0u, c0, nl, lane, t, X.stw);
+      cp_async_commit();
+      int dpar = 0;
+      for (uint32_t q = 0; c0.l < nl; ++q) {
+        cp_async_wait<0>();   // chunk q's data and chunk q+1's records
         __syncwarp();
-        const int nres = *rcount;
-        if (nres > 0) {
-          for (int q = 0; q < nres; ++q) rescan_row<MT>(X.rlist[q], t, msg, X.summ, lane);
-          my_rescans += (unsigned long long)nres;
-          __syncwarp();
-          if (lane == 0) *rcount = 0;
-          __syncwarp();
-        }
-        cd = cdn;
-        r1 = r2;
-        c = c1;
+        issue_rec(R, q + 2u, c2, nl, lane, X.rec);
+        issue_data<DP>(R, q + 1u, c1, nl, lane, t, X.stw);
+        cp_async_commit();
+        const bool act = in_chunk(c0, nl, lane);
+        XCol<DP> d;
+        read_col<DP>(R, q, c0, lane, act, d);
+        dpar += update_chunk<MT, DP>(act, d, c0.cs + lane, t, alpha, X, lp, lane, my_rescans);
+        __syncwarp();
+        c0 = c1;
         c1 = c2;
-        c2 = next_chunk(c2, lo, nl);
+        c2 = next_chunk(c2, W, lane);
       }
+      cp_async_wait<0>();
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) dpar += __shfl_xor_sync(kFull, dpar, off);
+      unsat += dpar;
       ++my_iters;
-      uint32_t bad = 0;
-      if (PK) {
-        for (int w = lane; w < mw; w += 32) bad |= X.par32[w];
-      } else {
-        const uint32_t* p32 = reinterpret_cast<const uint32_t*>(X.par8);
-        for (int q = lane; q < m4; q += 32) bad |= p32[q];
-      }
-      if (!__any_sync(kFull, bad)) { conv = it; break; }
+      if (unsat == 0) { conv = it; break; }
     }
     if (conv) {
       // insert (conv, i); i exceeds every member already listed, so it goes after equal iterations
       const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
       const int slot = ncand < M ? ncand : __shfl_sync(kFull, c_slot, M - 1);
       uint32_t* bits = cand + (size_t)slot * nw;
-      for (int w = lane; w < nw; w += 32) bits[w] = PK ? __ldcg(X.dec + w) : X.dec[w];
+      for (int w = lane; w < nw; w += 32) bits[w] = __ldcg(X.dec + w);
       // W(e) = sum of lambda_j over e_j = 1, ascending j (every lane folds the same sequence)
       float W = 0.0f;
       for (int w = 0; w < nw; ++w) {
-        uint32_t x = PK ? __ldcg(X.dec + w) : X.dec[w];
+        uint32_t x = __ldcg(X.dec + w);
         while (x) {
           const int bpos = __ffs(x) - 1;
           W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
@@ -504,12 +663,14 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
   __syncwarp();
 }
 
+// Blocks (one warp each) per SM the register budget targets.
+constexpr int kMinBlocksX = 16 / kBpxWarpsPerCta;
+
 // MIXED: shots name their problems (dem_of_shot); the descriptors are copied to shared memory after
-// the warps' regions and shots of image-engine problems are left to that kernel (mixed batches give
-// every summary-engine problem the packed layout, PK). Otherwise every shot decodes a.one from the
-// parameter space in layout PK.
-template <typename MT, int DP, bool MIXED, bool PK>
-__global__ void __launch_bounds__(kBpxWarpsPerCta * 32, MinBlocksX<MT>::value) k_bpx(const BpArgs a) {
+// the warps' regions and shots of image-engine problems are left to that kernel. Otherwise every shot
+// decodes a.one from the parameter space.
+template <typename MT, int DP, bool MIXED>
+__global__ void __launch_bounds__(kBpxWarpsPerCta * 32, kMinBlocksX) k_bpx(const BpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wcta = threadIdx.x >> 5;
@@ -524,9 +685,17 @@ __global__ void __launch_bounds__(kBpxWarpsPerCta * 32, MinBlocksX<MT>::value) k
   }
   unsigned char* base = smem + (size_t)wcta * a.bnd.x_warp_smem;
   unsigned char* gs = a.xscratch + gw * a.xscratch_pitch;
-  unsigned long long my_iters = 0, my_shots = 0, my_fail = 0, my_rescans = 0;
+  uint32_t my_iters = 0, my_shots = 0, my_fail = 0, my_rescans = 0;   // flushed before they could wrap
 
   for (;;) {
+    if (my_iters > 0x70000000u || my_rescans > 0x70000000u) {
+      if (lane == 0 && a.counters) {
+        atomicAdd(a.counters + VIBE_CNT_PAIR_ITERS, (unsigned long long)my_iters);
+        atomicAdd(a.counters + VIBE_CNT_RESCANS, (unsigned long long)my_rescans);
+      }
+      my_iters = 0;
+      my_rescans = 0;
+    }
     uint32_t shot = 0;
     if (lane == 0) shot = atomicAdd(a.next_shot_x, 1u);
     shot = __shfl_sync(kFull, shot, 0);
@@ -552,43 +721,43 @@ __global__ void __launch_bounds__(kBpxWarpsPerCta * 32, MinBlocksX<MT>::value) k
         continue;
       }
       if (sdem[di].engine != VIBE_ENGINE_SUMMARY) continue;   // left to the image engine
-      decode_shot_x<MT, DP, PK>(a, sdem[di], shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
+      decode_shot_x<MT, DP>(a, sdem[di], shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
     } else {
-      decode_shot_x<MT, DP, PK>(a, a.one, shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
+      decode_shot_x<MT, DP>(a, a.one, shot, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
     }
   }
   if (lane == 0 && a.counters) {
-    atomicAdd(a.counters + VIBE_CNT_SHOTS, my_shots);
-    atomicAdd(a.counters + VIBE_CNT_PAIR_ITERS, my_iters);
-    if (my_fail) atomicAdd(a.counters + VIBE_CNT_FAILURES, my_fail);
-    if (my_rescans) atomicAdd(a.counters + VIBE_CNT_RESCANS, my_rescans);
+    atomicAdd(a.counters + VIBE_CNT_SHOTS, (unsigned long long)my_shots);
+    atomicAdd(a.counters + VIBE_CNT_PAIR_ITERS, (unsigned long long)my_iters);
+    if (my_fail) atomicAdd(a.counters + VIBE_CNT_FAILURES, (unsigned long long)my_fail);
+    if (my_rescans) atomicAdd(a.counters + VIBE_CNT_RESCANS, (unsigned long long)my_rescans);
   }
 }
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-template <typename MT, int DP, bool MIXED, bool PK>
+template <typename MT, int DP, bool MIXED>
 cudaError_t launch_x(const BpArgs& a, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED, PK>>(smem);
+  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
   if (err != cudaSuccess) return err;
-  k_bpx<MT, DP, MIXED, PK><<<grid, kBpxWarpsPerCta * 32, smem, s>>>(a);
+  k_bpx<MT, DP, MIXED><<<grid, kBpxWarpsPerCta * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename MT, int DP, bool MIXED, bool PK>
+template <typename MT, int DP, bool MIXED>
 cudaError_t occupancy_x(size_t smem, int* out) {
-  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED, PK>>(smem);
+  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bpx<MT, DP, MIXED, PK>, kBpxWarpsPerCta * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bpx<MT, DP, MIXED>, kBpxWarpsPerCta * 32, smem);
 }
 
 template <typename Fn>
-cudaError_t by_dp_x(int DP, Fn&& f) {
-  switch (DP) {
+cudaError_t by_xd(int XD, Fn&& f) {
+  switch (XD) {
     case 4: return f(std::integral_constant<int, 4>{});
+    case 6: return f(std::integral_constant<int, 6>{});
     case 8: return f(std::integral_constant<int, 8>{});
     case 16: return f(std::integral_constant<int, 16>{});
-    case 32: return f(std::integral_constant<int, 32>{});
     default: return cudaErrorInvalidValue;
   }
 }
@@ -597,39 +766,44 @@ template <typename MT>
 cudaError_t launch_x_mt(const BpArgs& a, int grid, cudaStream_t s) {
   const bool mixed = a.dem_of_shot != nullptr;
   const size_t smem = bpx_cta_smem_bytes(a.bnd, mixed ? a.ndem : 0);
-  return by_dp_x(a.bnd.DP, [&](auto dp) {
-    if (mixed) return launch_x<MT, decltype(dp)::value, true, true>(a, grid, smem, s);
-    return a.one.x_packed ? launch_x<MT, decltype(dp)::value, false, true>(a, grid, smem, s)
-                          : launch_x<MT, decltype(dp)::value, false, false>(a, grid, smem, s);
+  return by_xd(a.bnd.XD, [&](auto dp) {
+    if (mixed) return launch_x<MT, decltype(dp)::value, true>(a, grid, smem, s);
+    return launch_x<MT, decltype(dp)::value, false>(a, grid, smem, s);
   });
 }
 
 template <typename MT>
 cudaError_t occupancy_x_mt(const Bounds& b, int ndem, int* out) {
   const size_t smem = bpx_cta_smem_bytes(b, ndem);
-  return by_dp_x(b.DP, [&](auto dp) {
-    if (ndem > 0) return occupancy_x<MT, decltype(dp)::value, true, true>(smem, out);
-    return b.x_packed ? occupancy_x<MT, decltype(dp)::value, false, true>(smem, out)
-                      : occupancy_x<MT, decltype(dp)::value, false, false>(smem, out);
+  return by_xd(b.XD, [&](auto dp) {
+    if (ndem > 0) return occupancy_x<MT, decltype(dp)::value, true>(smem, out);
+    return occupancy_x<MT, decltype(dp)::value, false>(smem, out);
   });
 }
 
 }  // namespace
 
+int bpx_degree_bucket(int maxcol) {
+  return maxcol <= 4 ? 4 : maxcol <= 6 ? 6 : maxcol <= 8 ? 8 : maxcol <= 16 ? 16 : 0;
+}
+
+int bpx_ring_bytes(int XD) {
+  switch (XD) {
+    case 4: return XRing<4>::kBytes;
+    case 6: return XRing<6>::kBytes;
+    case 8: return XRing<8>::kBytes;
+    case 16: return XRing<16>::kBytes;
+    default: return 0;
+  }
+}
+
 void bpx_layout(Tables* t, int msg_fp16) {
-  const bool pk = t->x_packed != 0;
-  const size_t flag_bytes = pk ? 4 * (size_t)t->mw : ((size_t)t->m + 3) / 4 * 4;   // syndrome / parity
-  size_t o = 0;
-  t->xo_summ = (int)o;  o = a16(o + 16 * (size_t)t->m);
-  t->xo_s = (int)o;     o = a16(o + flag_bytes);
-  t->xo_par = (int)o;   o = a16(o + flag_bytes);
-  t->xo_dec = (int)o;   o = a16(o + (pk ? 0 : 4 * (size_t)t->nw));
-  t->xo_rl = (int)o;    o = a16(o + 4 * 32 * (size_t)t->DP);
-  t->xo_rc = (int)o;    o = a16(o + 4);
-  t->x_warp_smem = (int)o;
+  // the check summaries (12 or 8 bytes per check); the prefetch ring comes on top (bounds)
+  t->x_warp_smem = msg_fp16 ? (int)a16(8 * (size_t)t->m) : (int)(a16(8 * (size_t)t->m) + a16(4 * (size_t)t->m));
   long long g = 0;
   t->xg_msg = g;   g += (long long)a16((size_t)t->E * (msg_fp16 ? 2 : 4));
-  t->xg_dec = g;   g += (long long)a16(pk ? 4 * (size_t)t->nw : 0);
+  t->xg_st = g;    g += (long long)a16(4 * (size_t)t->n);
+  t->xg_dec = g;   g += (long long)a16(4 * (size_t)t->nw);
   t->xg_lpost = g; g += (long long)a16(4 * (size_t)t->n);
   t->xg_acc = g;   g += (long long)a16(4 * (size_t)t->n);
   t->xg_cand = g;  g += (long long)a16(4 * (size_t)t->M * t->nw);

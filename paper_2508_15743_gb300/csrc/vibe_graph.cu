@@ -54,12 +54,12 @@ __global__ void k_csc_fill(const int32_t* __restrict__ rowptr, const int32_t* __
   }
 }
 
-// Sort each column's entries by check (insertion sort, degree <= 32) and emit rowidx, csc_ent and,
-// for every CSR entry, the CSC edge id of the same (check, column) pair.
-__global__ void k_csc_finish(int n, int DP, int RP, int spc, const int32_t* __restrict__ rowptr,
-                             const int32_t* __restrict__ colptr, uint32_t* __restrict__ packed,
-                             int32_t* __restrict__ rowidx, uint32_t* __restrict__ csc_ent,
-                             uint32_t* __restrict__ row_edge) {
+// Sort each column's entries by check (insertion sort, degree <= 32) and emit rowidx, csc_ent and the
+// summary engine's column records xcol (XP words per column: (check << 8) | position of the edge in
+// the check's CSR row, ascending check, zero padded; none when XP == 0).
+__global__ void k_csc_finish(int n, int DP, int RP, int spc, int XP, const int32_t* __restrict__ colptr,
+                             uint32_t* __restrict__ packed, int32_t* __restrict__ rowidx,
+                             uint32_t* __restrict__ csc_ent, uint32_t* __restrict__ xcol) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     int b = colptr[v], d = colptr[v + 1] - b;
     for (int i = 1; i < d; ++i) {
@@ -71,11 +71,9 @@ __global__ void k_csc_finish(int n, int DP, int RP, int spc, const int32_t* __re
     for (int k = 0; k < DP; ++k) {
       uint32_t x = k < d ? packed[b + k] : 0u;
       csc_ent[(size_t)v * DP + k] = k < d ? csc_entry(x >> 8, x & 0xffu, RP, spc) : 0u;
-      if (k < d) {
-        rowidx[b + k] = (int32_t)(x >> 8);
-        row_edge[rowptr[x >> 8] + (x & 0xffu)] = (uint32_t)(b + k);
-      }
+      if (k < d) rowidx[b + k] = (int32_t)(x >> 8);
     }
+    for (int k = 0; k < XP; ++k) xcol[(size_t)v * XP + k] = k < d ? packed[b + k] : 0u;
   }
 }
 
@@ -108,34 +106,27 @@ __device__ __forceinline__ float msg_magnitude<float>(float x) { return fabsf(x)
 template <>
 __device__ __forceinline__ float msg_magnitude<__half>(__half x) { return fabsf(__half2float(x)); }
 
-// Summary engine: prior messages in CSC edge order.
+// Summary engine: the summary of each check's prior messages -- the two smallest magnitudes (ordered by
+// value, then row position) with their positions, the third smallest as the floor (+inf when the row
+// is shorter; a missing second holder is position 255 with +inf), two valid holders, and the parity
+// of the messages' sign bits (bit 18). The syndrome and parity bits are set per shot by the kernel.
 template <typename MT>
-__global__ void k_msg_csc(const int32_t* __restrict__ colptr, int n, const float* __restrict__ lam,
-                          MT* __restrict__ out) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    const MT x = to_msg<MT>(lam[v]);
-    for (int e = colptr[v]; e < colptr[v + 1]; ++e) out[e] = x;
-  }
-}
-
-// Summary engine: per check, the smallest and second smallest prior-message magnitude over its row (with
-// multiplicity), the CSC edge ids holding them (first ones in row order; 0x7fffffff for none), and the
-// parity of the signs in bit 31 of the second holder word.
-template <typename MT>
-__global__ void k_sum_init(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int m,
-                           const uint32_t* __restrict__ row_edge, const float* __restrict__ lam,
-                           float4* __restrict__ out) {
+__global__ void k_xsum(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int m,
+                       const float* __restrict__ lam, float4* __restrict__ out) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-    float m1 = __int_as_float(0x7f800000), m2 = m1;
-    uint32_t i1 = 0x7fffffffu, i2 = 0x7fffffffu, sg = 0u;
+    const float inf = __int_as_float(0x7f800000);
+    float a1 = inf, a2 = inf, a3 = inf;
+    uint32_t q1 = 255u, q2 = 255u, sg = 0u;
     for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
       const MT x = to_msg<MT>(lam[colidx[q]]);
       const float a = msg_magnitude<MT>(x);
+      const uint32_t p = (uint32_t)(q - rowptr[c]);
       sg ^= (float)x < 0.0f ? 1u : 0u;
-      if (a < m1) { m2 = m1; i2 = i1; m1 = a; i1 = row_edge[q]; }
-      else if (a < m2) { m2 = a; i2 = row_edge[q]; }
+      if (a < a1 || (a == a1 && p < q1)) { a3 = a2; a2 = a1; q2 = q1; a1 = a; q1 = p; }
+      else if (a < a2 || (a == a2 && p < q2)) { a3 = a2; a2 = a; q2 = p; }
+      else if (a < a3) a3 = a;
     }
-    out[c] = make_float4(m1, m2, __uint_as_float(i1), __uint_as_float(i2 | (sg << 31)));
+    out[c] = make_float4(a1, a2, a3, __uint_as_float(q1 | (q2 << 8) | (2u << 16) | (sg << 18)));
   }
 }
 
@@ -186,14 +177,48 @@ __global__ void k_levels(const uint32_t* __restrict__ perm, int n, int m, int K,
   nlev[i] = nl;
 }
 
-// Summary engine: each schedule entry with its column's first CSC edge, so that a column update needs
-// one dependent load less.
-__global__ void k_sched_rec(const uint32_t* __restrict__ sched, long long total, const int32_t* __restrict__ colptr,
-                            uint2* __restrict__ rec) {
+// Summary engine: each member's schedule entries with the offset of the column's first message in the
+// member's schedule-ordered message array (exclusive prefix sum of the degrees). One CTA per member.
+__global__ void k_xrec(const uint32_t* __restrict__ sched, int n, uint2* __restrict__ rec) {
+  __shared__ uint32_t part[1024];
+  __shared__ uint32_t carry;
+  const uint32_t* sc = sched + (size_t)blockIdx.x * n;
+  uint2* out = rec + (size_t)blockIdx.x * n;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    const int j = base + threadIdx.x;
+    const uint32_t ent = j < n ? sc[j] : 0u;
+    const uint32_t d = ent >> 24;
+    part[threadIdx.x] = d;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const uint32_t add = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (j < n) out[j] = make_uint2(ent, carry + part[threadIdx.x] - d);
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+}
+
+// Summary engine: for every member and every CSR entry q = (check c, column v) of H, the slot of the
+// message v -> c in the member's schedule-ordered message array.
+__global__ void k_xrmap(const uint2* __restrict__ rec, long long total, int n, int E, int XP,
+                        const uint32_t* __restrict__ xcol, const int32_t* __restrict__ rowptr,
+                        uint32_t* __restrict__ rmap) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
-    const uint32_t ent = sched[q];
-    rec[q] = make_uint2(ent, (uint32_t)colptr[ent & 0xffffffu]);
+    const long long i = q / n;
+    const uint2 r = rec[q];
+    const uint32_t v = r.x & 0xffffffu, d = r.x >> 24;
+    for (uint32_t k = 0; k < d; ++k) {
+      const uint32_t x = xcol[(size_t)v * XP + k];
+      rmap[(size_t)i * E + rowptr[x >> 8] + (x & 0xffu)] = r.y + k;
+    }
   }
 }
 
@@ -232,10 +257,10 @@ cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cuda
 }
 
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K, const uint32_t* d_perm,
-                         int RP, int DP, int msg_fp16, const float* d_lam, int32_t* d_colptr, int32_t* d_rowidx,
-                         uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint2* d_sched_rec, uint32_t* d_lvl_off,
-                         int32_t* d_nlev, uint32_t* d_row_edge, void* d_msg_csc, float4* d_sum_init,
-                         int32_t* d_scratch, cudaStream_t s) {
+                         int RP, int DP, int XP, int msg_fp16, const float* d_lam, int32_t* d_colptr, int32_t* d_rowidx,
+                         uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev,
+                         uint32_t* d_xcol, uint2* d_xrec, uint32_t* d_xrmap, float4* d_xsum, int32_t* d_scratch,
+                         cudaStream_t s) {
   // scratch layout: cnt[n] | fill[n] | packed[E] ; later reused by k_levels (K*(m+3n+1))
   int E = 0;
   cudaError_t err = cudaMemcpyAsync(&E, d_rowptr + m, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -248,23 +273,23 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
   k_col_count<<<grid_for(E, 256), 256, 0, s>>>(d_colidx, E, cnt);
   k_scan_single<<<1, 1024, 0, s>>>(cnt, n, d_colptr);
   k_csc_fill<<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_colptr, fill, packed);
-  k_csc_finish<<<grid_for(n, 128), 128, 0, s>>>(n, DP, RP, msg_fp16 ? 8 : 4, d_rowptr, d_colptr, packed, d_rowidx,
-                                                 d_csc_ent, d_row_edge);
+  k_csc_finish<<<grid_for(n, 128), 128, 0, s>>>(n, DP, RP, msg_fp16 ? 8 : 4, XP, d_colptr, packed, d_rowidx,
+                                                 d_csc_ent, d_xcol);
   if (msg_fp16) {
-    k_msg_csc<__half><<<grid_for(n, 128), 128, 0, s>>>(d_colptr, n, d_lam, static_cast<__half*>(d_msg_csc));
-    k_sum_init<__half><<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_row_edge, d_lam, d_sum_init);
-  } else {
-    k_msg_csc<float><<<grid_for(n, 128), 128, 0, s>>>(d_colptr, n, d_lam, static_cast<float*>(d_msg_csc));
-    k_sum_init<float><<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_row_edge, d_lam, d_sum_init);
-  }
-  if (msg_fp16)
+    k_xsum<__half><<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_lam, d_xsum);
     k_msg_init<__half><<<grid_for((long long)m * RP, 256), 256, 0, s>>>(d_rowptr, d_colidx, m, RP, d_lam,
                                                                        static_cast<__half*>(d_msg_init));
-  else
+  } else {
+    k_xsum<float><<<grid_for(m, 128), 128, 0, s>>>(d_rowptr, d_colidx, m, d_lam, d_xsum);
     k_msg_init<float><<<grid_for((long long)m * RP, 256), 256, 0, s>>>(d_rowptr, d_colidx, m, RP, d_lam,
                                                                       static_cast<float*>(d_msg_init));
+  }
   k_levels<<<(K + 31) / 32, 32, 0, s>>>(d_perm, n, m, K, d_colptr, d_rowidx, d_sched, d_lvl_off, d_nlev, d_scratch);
-  k_sched_rec<<<grid_for((long long)K * n, 256), 256, 0, s>>>(d_sched, (long long)K * n, d_colptr, d_sched_rec);
+  if (XP > 0) {
+    k_xrec<<<K, 1024, 0, s>>>(d_sched, n, d_xrec);
+    k_xrmap<<<grid_for((long long)K * n, 256), 256, 0, s>>>(d_xrec, (long long)K * n, n, E, XP, d_xcol, d_rowptr,
+                                                            d_xrmap);
+  }
   return cudaGetLastError();
 }
 

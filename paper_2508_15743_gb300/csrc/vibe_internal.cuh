@@ -12,7 +12,7 @@
 namespace vibe {
 
 constexpr int kBpWarpsPerCta = 2;   // image engine: warps per CTA, one shot per warp
-constexpr int kBpxWarpsPerCta = 2;  // summary engine: warps per CTA, one shot per warp
+constexpr int kBpxWarpsPerCta = 1;  // summary engine: warps per CTA, one shot per warp
 constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
 constexpr int kMaxRowDeg = 255;     // position of an edge inside its check row fits in 8 bits
 constexpr int kMaxColDeg = 32;
@@ -49,11 +49,12 @@ struct Tables {
   float alpha;   // the shared factor (alpha_m holds the one each member uses)
   int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // image engine: per-warp shared memory, bytes
   int engine;    // VIBE_ENGINE_IMAGE or VIBE_ENGINE_SUMMARY
-  // summary engine: shared memory of one warp (bytes) and global scratch of one warp (bytes, 16-aligned parts)
-  int x_packed;  // summary-engine state layout: 1 packed (decisions in global memory, bit words), 0 bytes
-  int xo_summ, xo_s, xo_par, xo_dec, xo_rl, xo_rc, x_warp_smem;
+  // summary engine: column-degree bound XD (4, 6, 8 or 16; 0 when a column has more than 16 checks and
+  // the engine cannot run the problem), xcol pitch XP, shared memory of one warp (the m check
+  // summaries, bytes) and the parts of one warp's global scratch (bytes, 16-aligned)
+  int XD, XP, x_warp_smem;   // x_warp_smem: the m check summaries only
   // xg_cpost = x_warp_scratch: the M*n candidate posteriors (soft output only) follow the fixed part
-  long long xg_msg, xg_dec, xg_lpost, xg_acc, xg_cand, xg_cpost, x_warp_scratch;
+  long long xg_msg, xg_st, xg_dec, xg_lpost, xg_acc, xg_cand, xg_cpost, x_warp_scratch;
   const int32_t* rowptr;   // H CSR
   const int32_t* colidx;
   const int32_t* colptr;   // H CSC, checks ascending in each column
@@ -63,15 +64,16 @@ struct Tables {
   const float* alpha_m;    // K scaling factors, member i's in alpha_m[i]
   const void* msg_init;    // m*RP messages (float or half): lambda of the edge's column, +inf padding
   const uint32_t* sched;   // K*n: column | (degree << 24), grouped by wavefront level
-  const uint2* sched_rec;  // K*n: (sched entry, first CSC edge of the column), same order
   const uint32_t* lvl_off; // K*(n+1): level offsets into sched
   const int32_t* nlev;     // K level counts
   const int32_t* lrowptr;  // L CSR
   const int32_t* lcolidx;
   // summary engine
-  const uint32_t* row_edge; // E: for each CSR entry of H, the CSC edge id of the same (check, column)
-  const void* msg_csc;      // E messages (float or half) in CSC edge order: lambda of the edge's column
-  const float4* sum_init;   // m: (min1, min2, edge id of min1, sign parity) of the prior messages per row
+  const uint32_t* xcol;    // n*XP: (check << 8) | position of the edge in the check's CSR row, ascending check
+  const uint2* xrec;       // K*n: (sched entry, offset of the column's first message in the member's
+                           // schedule-ordered message array), same order as sched
+  const uint32_t* xrmap;   // K*E: per member, the message slot of each CSR entry of H
+  const float4* xsum;      // m: summaries of the prior messages (see vibe_bpx.cu)
 };
 
 // Sizes that bound every problem of a launch (shared-memory layouts, strides, scratch pitches).
@@ -80,10 +82,11 @@ struct Bounds {
   int RP;          // common row pitch if all problems share it, else 0
   int warp_smem;   // largest BP per-warp layout
   int lsd_order;   // largest LSD order
-  int x_warp_smem;    // largest summary-engine shared memory per warp (0 if no problem uses that engine)
+  int x_warp_smem;    // summary-engine shared memory per warp: the prefetch ring for XD and the largest
+                      // problem's check summaries (0 if no problem uses that engine)
   long long x_warp_scratch;   // largest summary-engine global scratch per warp, bytes
   int engines;     // bit 0: some problem uses the image engine, bit 1: the summary engine
-  int x_packed;    // single-problem launch: the summary engine's layout (Tables::x_packed)
+  int XD;          // largest summary-engine column-degree bound
 };
 
 struct BpArgs {
@@ -178,11 +181,11 @@ cudaError_t ensure_dyn_smem(size_t smem) {
 int set_error(int code, const char* msg);
 
 // K0: graph builder (vibe_graph.cu)
-cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K,
-                         const uint32_t* d_perm, int RP, int DP, int msg_fp16, const float* d_lam,
-                         int32_t* d_colptr, int32_t* d_rowidx, uint32_t* d_csc_ent, void* d_msg_init,
-                         uint32_t* d_sched, uint2* d_sched_rec, uint32_t* d_lvl_off, int32_t* d_nlev, uint32_t* d_row_edge,
-                         void* d_msg_csc, float4* d_sum_init, int32_t* d_scratch, cudaStream_t s);
+cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K, const uint32_t* d_perm,
+                         int RP, int DP, int XP, int msg_fp16, const float* d_lam, int32_t* d_colptr, int32_t* d_rowidx,
+                         uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev,
+                         uint32_t* d_xcol, uint2* d_xrec, uint32_t* d_xrmap, float4* d_xsum, int32_t* d_scratch,
+                         cudaStream_t s);
 cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
 
 // K1: persistent BP + ensemble selection (vibe_bp.cu)
@@ -193,7 +196,9 @@ cudaError_t launch_bp(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
 cudaError_t bp_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_per_sm);
 
 // K1': summary-engine BP + ensemble selection (vibe_bpx.cu)
-void bpx_layout(Tables* t, int msg_fp16);   // fills t's xo_*/xg_* fields
+int bpx_degree_bucket(int maxcol);          // XD for a largest column degree (0: above 16)
+int bpx_ring_bytes(int XD);                  // per-warp shared-memory prefetch ring of a launch with bound XD
+void bpx_layout(Tables* t, int msg_fp16);   // fills t's x_warp_smem and xg_* fields
 size_t bpx_cta_smem_bytes(const Bounds& b, int ndem);
 cudaError_t launch_bpx(const BpArgs& a, int msg_fp16, int grid, cudaStream_t s);
 cudaError_t bpx_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_per_sm);
