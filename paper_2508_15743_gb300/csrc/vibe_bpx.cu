@@ -46,7 +46,6 @@
 #include <type_traits>
 
 #include "vibe_internal.cuh"
-#include "vibe_summary.cuh"
 
 namespace vibe {
 namespace {
@@ -90,6 +89,94 @@ __device__ __forceinline__ uint32_t sign_bit(float x) { return __float_as_uint(x
 
 __device__ __forceinline__ bool is_finite_bits(float x) { return (__float_as_uint(x) & kInfBits) != kInfBits; }
 
+// Check summaries in registers: float4 {m1, m2, F, w}, w = p1 | p2 << 8 | nh << 16 | sign parity << 18 |
+// syndrome << 19 | parity << 20 (see the header comment).
+constexpr uint32_t kNhShift = 16, kSgnBit = 1u << 18, kSynBit = 1u << 19, kParBit = 1u << 20;
+
+// Minimum magnitude over the row without the edge at position p; false if the summary cannot answer.
+__device__ __forceinline__ bool xquery(const float4 s, uint32_t p, float& out) {
+  const uint32_t w = __float_as_uint(s.w);
+  const uint32_t nh = (w >> kNhShift) & 3u, p1 = w & 0xffu;
+  const bool mine = p == p1;
+  out = nh == 2u ? (mine ? s.y : s.x) : (nh == 1u && !mine ? s.x : s.z);
+  return nh == 2u || (nh == 1u && !mine) || __float_as_uint(s.z) == kInfBits;   // +inf floor: all others +inf
+}
+
+// Whether the edge at position p taking magnitude x can change more than the flags: it holds m1 or
+// m2, or it drops below the floor.
+__device__ __forceinline__ bool xslow(const float4 s, uint32_t p, float x) {
+  const uint32_t w = __float_as_uint(s.w);
+  const uint32_t nh = (w >> kNhShift) & 3u;
+  return (nh >= 1u && p == (w & 0xffu)) || (nh == 2u && p == ((w >> 8) & 0xffu)) || x < s.z;
+}
+
+// The summary after the edge at position p takes magnitude x (the case analysis in the header),
+// written as: take p out of the holder list, then put (x, p) back if it stays within the floor --
+// a former holder when x <= F, any other edge when x < F -- evicting the larger holder into the
+// floor when the list is full.
+__device__ __forceinline__ float4 xupdate(const float4 s, uint32_t p, float x) {
+  const uint32_t w = __float_as_uint(s.w);
+  const uint32_t nh0 = (w >> kNhShift) & 3u, q10 = w & 0xffu, q2 = (w >> 8) & 0xffu;
+  const bool is1 = nh0 >= 1u && p == q10, is2 = nh0 == 2u && p == q2;
+  const bool was = is1 || is2;
+  const float a1 = is1 ? s.y : s.x, a2 = s.y, F = s.z;
+  const uint32_t q1 = is1 ? q2 : q10;
+  const uint32_t k = nh0 - (was ? 1u : 0u);
+  const bool ins = was ? x <= F : x < F;
+  const bool lt1 = k == 0u || x < a1;
+  const bool lt2 = k <= 1u || x < a2;
+  const float n1 = ins && lt1 ? x : a1;
+  const uint32_t r1 = ins && lt1 ? p : q1;
+  const float n2 = ins ? (lt1 ? a1 : (lt2 ? x : a2)) : a2;
+  const uint32_t r2 = ins ? (lt1 ? q1 : (lt2 ? p : q2)) : q2;
+  const float nF = ins && k == 2u ? (lt2 ? a2 : x) : F;
+  const uint32_t nk = ins ? min(k + 1u, 2u) : k;
+  return make_float4(n1, n2, nF, __uint_as_float((w & ~0x3ffffu) | r1 | (r2 << 8) | (nk << kNhShift)));
+}
+
+// Shared-memory storage of the summaries. FP32 messages: the float4 itself (16 bytes per check).
+// FP16 messages: 8 bytes, {m1 | sign parity << 15 | m2 << 16 | syndrome << 31, F | parity << 15 |
+// p1 << 16 | p2 << 24} with every magnitude a binary16 (exact: the magnitudes are those of stored
+// binary16 messages) and position 255 for an empty holder slot, from which the holder count follows.
+template <typename MT>
+struct SumIO;
+
+template <>
+struct SumIO<float> {
+  float4* v;
+  static constexpr int kBytesPerCheck = 16;
+  __device__ __forceinline__ float4 load(int c) const { return v[c]; }
+  __device__ __forceinline__ void store(int c, float4 s) const { v[c] = s; }
+  __device__ __forceinline__ void flip(int c, uint32_t bits) const { reinterpret_cast<uint32_t*>(v + c)[3] ^= bits; }
+};
+
+template <>
+struct SumIO<__half> {
+  uint2* v;
+  static constexpr int kBytesPerCheck = 8;
+  __device__ __forceinline__ static float hf(uint32_t b) { return __half2float(__ushort_as_half((unsigned short)b)); }
+  __device__ __forceinline__ static uint32_t hb(float x) { return (uint32_t)__half_as_ushort(__float2half_rn(x)); }
+  __device__ __forceinline__ float4 load(int c) const {
+    const uint2 a = v[c];
+    const uint32_t p1 = (a.y >> 16) & 0xffu, p2 = a.y >> 24;
+    const uint32_t nh = (p1 != 255u ? 1u : 0u) + (p2 != 255u ? 1u : 0u);
+    const uint32_t w = p1 | (p2 << 8) | (nh << kNhShift) | (((a.x >> 15) & 1u) << 18) | ((a.x >> 31) << 19) |
+                       (((a.y >> 15) & 1u) << 20);
+    return make_float4(hf(a.x & 0x7fffu), hf((a.x >> 16) & 0x7fffu), hf(a.y & 0x7fffu), __uint_as_float(w));
+  }
+  __device__ __forceinline__ void store(int c, float4 s) const {
+    const uint32_t w = __float_as_uint(s.w);
+    const uint32_t nh = (w >> kNhShift) & 3u;
+    const uint32_t p1 = nh >= 1u ? (w & 0xffu) : 255u, p2 = nh == 2u ? ((w >> 8) & 0xffu) : 255u;
+    v[c] = make_uint2(hb(s.x) | (((w >> 18) & 1u) << 15) | (hb(s.y) << 16) | (((w >> 19) & 1u) << 31),
+                      hb(s.z) | (((w >> 20) & 1u) << 15) | (p1 << 16) | (p2 << 24));
+  }
+  __device__ __forceinline__ void flip(int c, uint32_t bits) const {
+    if (bits & kSgnBit) v[c].x ^= 1u << 15;
+    if (bits & kParBit) v[c].y ^= 1u << 15;
+  }
+};
+
 // (value, position) pairs ordered by value, then position
 __device__ __forceinline__ bool before(float a, uint32_t ia, float b, uint32_t ib) {
   return a < b || (a == b && ia < ib);
@@ -113,25 +200,20 @@ struct Top3 {
 };
 
 // Summary storage of a message type: 12 bytes per check for FP32 messages, 8 for FP16.
-template <typename MT>
-using SumStore = typename std::conditional<std::is_same<MT, float>::value, SumStore32, SumStore16>::type;
+constexpr int kAhead = 1;   // chunks of column data in flight ahead of the update (1 or 2)
 
 template <typename MT>
-__device__ __forceinline__ SumStore<MT> sum_store(unsigned char* p, int m);
+__device__ __forceinline__ SumIO<MT> sum_io(unsigned char* p);
 template <>
-__device__ __forceinline__ SumStore32 sum_store<float>(unsigned char* p, int m) {
-  return SumStore32{reinterpret_cast<float2*>(p), reinterpret_cast<uint32_t*>(p + ((8 * (size_t)m + 15) & ~(size_t)15))};
-}
+__device__ __forceinline__ SumIO<float> sum_io<float>(unsigned char* p) { return SumIO<float>{reinterpret_cast<float4*>(p)}; }
 template <>
-__device__ __forceinline__ SumStore16 sum_store<__half>(unsigned char* p, int m) {
-  return SumStore16{reinterpret_cast<uint2*>(p)};
-}
+__device__ __forceinline__ SumIO<__half> sum_io<__half>(unsigned char* p) { return SumIO<__half>{reinterpret_cast<uint2*>(p)}; }
 
 // Warp-cooperative rescan of check c, whose CSR row is b .. b + d: the two smallest magnitudes with
 // their positions and the third smallest as the floor; the flags are kept.
 template <typename MT>
 __device__ __forceinline__ void rescan_row(int c, int b, int d, const uint32_t* rmap, const MT* msg,
-                                           const SumStore<MT>& S, int lane) {
+                                           const SumIO<MT>& S, int lane) {
   uint32_t loc[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
@@ -155,13 +237,8 @@ __device__ __forceinline__ void rescan_row(int c, int b, int d, const uint32_t* 
     T.insert(b3, 255u);
   }
   if (lane == 0) {
-    SumV v = S.load(c);
-    v.m1 = T.a1;
-    v.m2 = T.a2;
-    v.p1 = T.q1;
-    v.p2 = T.q2;
-    v.F = floor_round<!std::is_same<MT, float>::value>(T.a3);
-    S.store(c, v);
+    const uint32_t w = __float_as_uint(S.load(c).w);
+    S.store(c, make_float4(T.a1, T.a2, T.a3, __uint_as_float((w & ~0x3ffffu) | T.q1 | (T.q2 << 8) | (2u << kNhShift))));
   }
 }
 
@@ -174,12 +251,14 @@ template <int DP>
 struct XRing {
   static constexpr int XP = (DP + 3) / 4 * 4;   // words of a column record
   static constexpr int kStwWords = 48;          // the 16-byte blocks covering 32 state words
-  static constexpr int kRecBytes = 3 * 32 * 8;  // three record slots: chunk q's records stay until its update
+  static constexpr int kRecSlots = kAhead + 2;   // chunk q's records stay until its update
+  static constexpr int kStages = kAhead + 1;
+  static constexpr int kRecBytes = kRecSlots * 32 * 8;
   static constexpr int kStageBytes = 32 * XP * 4 + 32 * 4 + kStwWords * 4;
-  static constexpr int kBytes = kRecBytes + 2 * kStageBytes;
+  static constexpr int kBytes = kRecBytes + kStages * kStageBytes;
   unsigned char* base;
-  __device__ __forceinline__ uint2* rec(uint32_t q) { return reinterpret_cast<uint2*>(base) + (q % 3u) * 32; }
-  __device__ __forceinline__ unsigned char* stage(uint32_t q) { return base + kRecBytes + (q & 1u) * kStageBytes; }
+  __device__ __forceinline__ uint2* rec(uint32_t q) { return reinterpret_cast<uint2*>(base) + (q % kRecSlots) * 32; }
+  __device__ __forceinline__ unsigned char* stage(uint32_t q) { return base + kRecBytes + (q % kStages) * kStageBytes; }
   __device__ __forceinline__ uint32_t* xc(uint32_t q) { return reinterpret_cast<uint32_t*>(stage(q)); }
   __device__ __forceinline__ float* lam(uint32_t q) { return reinterpret_cast<float*>(stage(q) + 32 * XP * 4); }
   __device__ __forceinline__ uint32_t* stw(uint32_t q) {
@@ -258,7 +337,7 @@ __device__ __forceinline__ bool in_chunk(const Chunk& c, int nl, int lane) {
 // Per-warp views of the current pair's state.
 template <typename MT>
 struct XState {
-  SumStore<MT> S;    // shared: m check summaries
+  SumIO<MT> S;       // shared: m check summaries
   MT* msg;           // global: E messages in the member's schedule order
   uint32_t* stw;     // global: n column state words in schedule order
   uint32_t* dec;     // global: nw decision bits in column order
@@ -279,7 +358,6 @@ struct XCol {
 template <typename MT, int DP>
 __device__ __forceinline__ int update_chunk(bool active, const XCol<DP>& d, uint32_t j, const Tables& t, float alpha,
                                             const XState<MT>& X, float* lpost, int lane, uint32_t& my_rescans) {
-  constexpr bool kHalf = !std::is_same<MT, float>::value;
   // check-to-variable messages from the summaries (Algorithm 1's check update over N(c) \ v)
   float mcv[DP];
   uint32_t need = 0u;
@@ -287,11 +365,12 @@ __device__ __forceinline__ int update_chunk(bool active, const XCol<DP>& d, uint
   for (int k = 0; k < DP; ++k) {
     mcv[k] = 0.0f;
     if (active && (uint32_t)k < d.deg) {
-      const SumV s = X.S.load((int)(d.ent[k] >> 8));
+      const float4 s = X.S.load((int)(d.ent[k] >> 8));
       float mn;
-      if (!sum_query(s, d.ent[k] & 0xffu, mn)) need |= 1u << k;
+      if (!xquery(s, d.ent[k] & 0xffu, mn)) need |= 1u << k;
+      const uint32_t w = __float_as_uint(s.w);
       const float mag = __fmul_rn(alpha, mn);
-      mcv[k] = ((s.sgn ^ s.syn ^ (d.st >> k)) & 1u) ? -mag : mag;   // sign parity, syndrome, own sign
+      mcv[k] = (((w >> 18) ^ (w >> 19) ^ (d.st >> k)) & 1u) ? -mag : mag;   // sign parity, syndrome, own sign
     }
   }
   if (__any_sync(kFull, need != 0u)) {
@@ -334,11 +413,12 @@ __device__ __forceinline__ int update_chunk(bool active, const XCol<DP>& d, uint
 #pragma unroll
     for (int k = 0; k < DP; ++k)
       if ((need >> k) & 1u) {
-        const SumV s = X.S.load((int)(d.ent[k] >> 8));
+        const float4 s = X.S.load((int)(d.ent[k] >> 8));
         float mn;
-        sum_query(s, d.ent[k] & 0xffu, mn);
+        xquery(s, d.ent[k] & 0xffu, mn);
+        const uint32_t w = __float_as_uint(s.w);
         const float mag = __fmul_rn(alpha, mn);
-        mcv[k] = ((s.sgn ^ s.syn ^ (d.st >> k)) & 1u) ? -mag : mag;
+        mcv[k] = (((w >> 18) ^ (w >> 19) ^ (d.st >> k)) & 1u) ? -mag : mag;
       }
   }
   if (!active) return 0;
@@ -369,17 +449,16 @@ __device__ __forceinline__ int update_chunk(bool active, const XCol<DP>& d, uint
       // for edges that drop below the floor, a flag update for the rest
       const int c = (int)(d.ent[k] >> 8);
       const uint32_t p = d.ent[k] & 0xffu;
-      const SumV s = X.S.load(c);
+      const float4 s = X.S.load(c);
       const float ax = fabsf(x);
-      const bool sflip = (((d.st >> k) ^ sx) & 1u) != 0u;
-      if (flip) dpar += (s.par ^ 1u) ? 1 : -1;
-      if (sum_slow(s, p, ax)) {
-        SumV u = sum_update<kHalf>(s, p, ax);
-        u.sgn ^= sflip ? 1u : 0u;
-        u.par ^= flip ? 1u : 0u;
+      const uint32_t fl = ((((d.st >> k) ^ sx) & 1u) ? kSgnBit : 0u) | (flip ? kParBit : 0u);
+      if (flip) dpar += (__float_as_uint(s.w) & kParBit) ? -1 : 1;
+      if (xslow(s, p, ax)) {
+        float4 u = xupdate(s, p, ax);
+        u.w = __uint_as_float(__float_as_uint(u.w) ^ fl);
         X.S.store(c, u);
-      } else if (sflip || flip) {
-        X.S.flip_flags(c, sflip, flip);
+      } else if (fl) {
+        X.S.flip(c, fl);
       }
     }
   }
@@ -445,7 +524,7 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
                                               uint32_t& my_shots, uint32_t& my_fail, uint32_t& my_rescans) {
   const int n = t.n, m = t.m, K = t.K, M = t.M, T = t.T, nw = t.nw, kw = t.kw, mw = t.mw;
   XState<MT> X;
-  X.S = sum_store<MT>(base + XRing<DP>::kBytes, m);
+  X.S = sum_io<MT>(base + XRing<DP>::kBytes);
   X.msg = reinterpret_cast<MT*>(gs + t.xg_msg);
   X.stw = reinterpret_cast<uint32_t*>(gs + t.xg_st);
   X.dec = reinterpret_cast<uint32_t*>(gs + t.xg_dec);
@@ -497,17 +576,10 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
     // member init: prior summaries with this shot's syndrome (parity = s), prior messages in the
     // member's schedule order, state words and decisions 0
     for (int c = lane; c < m; c += 32) {
-      const float4 s = __ldg(t.xsum + c);
-      const uint32_t w = __float_as_uint(s.w);
-      SumV v;
-      v.m1 = s.x;
-      v.m2 = s.y;
-      v.F = s.z;
-      v.p1 = w & 0xffu;
-      v.p2 = (w >> 8) & 0xffu;
-      v.sgn = (w >> 18) & 1u;
-      v.syn = v.par = (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u;
-      X.S.store(c, v);
+      float4 s = __ldg(t.xsum + c);
+      const uint32_t sb = (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u;
+      s.w = __uint_as_float(__float_as_uint(s.w) | (sb ? (kSynBit | kParBit) : 0u));
+      X.S.store(c, s);
     }
     for (int j = lane; j < n; j += 32) {
       const uint2 r = __ldg(X.rec + j);
@@ -541,13 +613,31 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       cp_async_wait<0>();
       issue_data<DP>(R, 0u, c0, nl, lane, t, X.stw);
       cp_async_commit();
-      int dpar = 0;
-      for (uint32_t q = 0; c0.l < nl; ++q) {
-        cp_async_wait<0>();   // chunk q's data and chunk q+1's records
-        __syncwarp();
-        issue_rec(R, q + 2u, c2, nl, lane, X.rec);
-        issue_data<DP>(R, q + 1u, c1, nl, lane, t, X.stw);
+      if (kAhead == 2) {
+        issue_rec(R, 2u, c2, nl, lane, X.rec);
         cp_async_commit();
+        issue_data<DP>(R, 1u, c1, nl, lane, t, X.stw);
+        cp_async_commit();
+      }
+      int dpar = 0;
+      Chunk c3s = c2;
+      for (uint32_t q = 0; c0.l < nl; ++q) {
+        if (kAhead == 2) {
+          const Chunk c3 = next_chunk(c2, W, lane);
+          cp_async_wait<1>();   // all but chunk q+1's data: chunk q's data and chunk q+2's records
+          __syncwarp();
+          issue_rec(R, q + 3u, c3, nl, lane, X.rec);
+          cp_async_commit();
+          issue_data<DP>(R, q + 2u, c2, nl, lane, t, X.stw);
+          cp_async_commit();
+          c3s = c3;
+        } else {
+          cp_async_wait<0>();   // chunk q's data and chunk q+1's records
+          __syncwarp();
+          issue_rec(R, q + 2u, c2, nl, lane, X.rec);
+          issue_data<DP>(R, q + 1u, c1, nl, lane, t, X.stw);
+          cp_async_commit();
+        }
         const bool act = in_chunk(c0, nl, lane);
         XCol<DP> d;
         read_col<DP>(R, q, c0, lane, act, d);
@@ -555,7 +645,7 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
         __syncwarp();
         c0 = c1;
         c1 = c2;
-        c2 = next_chunk(c2, W, lane);
+        c2 = kAhead == 2 ? c3s : next_chunk(c2, W, lane);
       }
       cp_async_wait<0>();
 #pragma unroll
@@ -737,8 +827,22 @@ __global__ void __launch_bounds__(kBpxWarpsPerCta * 32, kMinBlocksX) k_bpx(const
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 template <typename MT, int DP, bool MIXED>
+cudaError_t prefer_shared() {
+  // the summaries and the ring are the working set; L1 caches little here
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return cudaSuccess;
+  if (done[dev]) return cudaSuccess;
+  cudaError_t err = cudaFuncSetAttribute(k_bpx<MT, DP, MIXED>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (err == cudaSuccess) done[dev] = true;
+  return err;
+}
+
+template <typename MT, int DP, bool MIXED>
 cudaError_t launch_x(const BpArgs& a, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
+  cudaError_t err = prefer_shared<MT, DP, MIXED>();
+  if (err != cudaSuccess) return err;
+  err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
   if (err != cudaSuccess) return err;
   k_bpx<MT, DP, MIXED><<<grid, kBpxWarpsPerCta * 32, smem, s>>>(a);
   return cudaGetLastError();
@@ -746,7 +850,9 @@ cudaError_t launch_x(const BpArgs& a, int grid, size_t smem, cudaStream_t s) {
 
 template <typename MT, int DP, bool MIXED>
 cudaError_t occupancy_x(size_t smem, int* out) {
-  cudaError_t err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
+  cudaError_t err = prefer_shared<MT, DP, MIXED>();
+  if (err != cudaSuccess) return err;
+  err = ensure_dyn_smem<k_bpx<MT, DP, MIXED>>(smem);
   if (err != cudaSuccess) return err;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bpx<MT, DP, MIXED>, kBpxWarpsPerCta * 32, smem);
 }
@@ -798,8 +904,8 @@ int bpx_ring_bytes(int XD) {
 }
 
 void bpx_layout(Tables* t, int msg_fp16) {
-  // the check summaries (12 or 8 bytes per check); the prefetch ring comes on top (bounds)
-  t->x_warp_smem = msg_fp16 ? (int)a16(8 * (size_t)t->m) : (int)(a16(8 * (size_t)t->m) + a16(4 * (size_t)t->m));
+  // the check summaries (16 or 8 bytes per check); the prefetch ring comes on top (bounds)
+  t->x_warp_smem = (int)a16((msg_fp16 ? 8 : 16) * (size_t)t->m);
   long long g = 0;
   t->xg_msg = g;   g += (long long)a16((size_t)t->E * (msg_fp16 ? 2 : 4));
   t->xg_st = g;    g += (long long)a16(4 * (size_t)t->n);
