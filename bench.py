@@ -1,15 +1,32 @@
 """Benchmark: decoded shots/s of the VibeLSD hot path on GB300, FP32 and FP16 messages.
 
-One step = one vibe_decode call over the whole batch: BP ensemble on every shot, ensemble ranking,
-LSD on the shots no member resolved, logical flips and per-shot records. The batch is the d=9
-colour-code phenomenological workload (9 noisy + 1 perfect round, p = q = 0.01; m = 300 detectors,
-n = 819 mechanisms; K = 16 seeded schedules, T = 30, M = 5, LSD-0), 10^6 shots sampled on the host
-with a seeded generator and resident in HBM before timing. Between timed steps a 256 MB buffer is
-written to flush L2; each step is timed with CUDA events on the decoding stream.
+One step = one vibe_decode call over a whole batch: BP ensemble on every shot, ensemble ranking,
+LSD on the shots no member resolved, logical flips and per-shot records. Inputs are seeded,
+synthetic and resident in HBM before timing; each step is timed with CUDA events on the decoding
+stream and a 256 MB buffer is written between timed steps to flush L2.
 
-`--impl reference` times the CPU oracle (plain C, all host cores) on a bounded sample of the same
-workload instead. Under torchrun each rank decodes its own 10^6 shots (weak scaling, no collective
-on the data path); rank 0 prints one JSON line.
+The JSON line's headline (`value`) is the d=9 colour-code phenomenological workload (9 noisy + 1
+perfect round, p = q = 0.01; m = 300, n = 819; K = 16 seeded schedules, T = 30, M = 5, LSD-0),
+10^6 shots per step, with FP16 messages, end-to-end host-buffer throughput, the CPU oracle timed on
+the host cores, and the FP64-oracle logical error rate beside it. Two more legs ride on the same
+line (skip them with --legs none):
+
+  circuit_d11   the circuit-level d=11 colour code (11 rounds, Si1000 noise at p = 1e-3; m = 990,
+                n = 32422): K = 64, T = 50, M = 5, LSD-0 with FP32 and FP16 messages and LSD order
+                5 with FP32, one timed step of 3648 shots each (twice the persistent grid);
+  mixed         colour codes d = 5..15 under circuit-level noise at p in {1, 2, 3, 5} per mille (24
+                problems, 6 graph structures), K = 32, T = 20, FP16, shots of all problems interleaved
+                at random and decoded by one mixed launch replayed from a CUDA graph.
+
+Every leg carries a roofline for its kernels (`rooflines`): the BP kernels against the measured HBM
+copy bandwidth in algorithmic bytes (2*E*b per executed sweep plus per-shot I/O), the image
+engine's shared-memory row scans against the shared-memory bandwidth, and LSD's GF(2) word
+operations against the integer ALU rate.
+
+`--impl reference` times the CPU oracle (plain C, all host cores) on a bounded sample of the
+headline workload instead. `--case NAME [--shots B]` runs one warm-up and one decode of a named case
+and prints its counters and kernel times (used for the ncu captures in profiles/). Under torchrun
+each rank decodes its own shots (weak scaling, no collective on the data path); rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -27,10 +44,15 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2508_15743_gb300 import circuit as C  # noqa: E402
 from paper_2508_15743_gb300 import dem as D  # noqa: E402
 
 WORKLOAD = "cc666_d9_pheno"
 METRIC = "decoded shots/s and p50/p99 latency at fixed logical error rate, FP16 vs FP32"
+SM_COUNT_NOMINAL = 152
+SM_CLOCK_GHZ = 2.07          # maximum SM clock of the part (the recipe's figure)
+SMEM_BYTES_PER_CLK = 128     # shared-memory bandwidth per SM and clock (32 banks x 4 bytes)
+INT_OPS_PER_CLK = 128        # 32-bit integer lanes per SM and clock
 
 
 def dist_env():
@@ -105,6 +127,17 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def ler_ci(fails, shots):
+    p = fails / shots if shots else 0.0
+    sd = (p * (1 - p) / shots) ** 0.5 if shots else 0.0
+    return {"ler": p, "two_sigma": [max(0.0, p - 2 * sd), p + 2 * sd], "failures": int(fails), "shots": int(shots)}
+
+
+def pct(a, q):
+    a = sorted(a)
+    return a[min(len(a) - 1, int(round(q * (len(a) - 1))))]
+
+
 def make_inputs(shots, seed):
     dm = D.build_workload(WORKLOAD)
     w = D.WORKLOADS[WORKLOAD]
@@ -112,6 +145,34 @@ def make_inputs(shots, seed):
     perms = D.schedules(dm.n, w["K"], w["seed"])
     return dm, w, syn, obs, perms
 
+
+def io_bytes_per_shot(dm):
+    return 4 * ((dm.m + 31) // 32) + 4 * ((dm.n + 31) // 32) + 4 * ((dm.k + 31) // 32) + 12
+
+
+def hbm_roofline(kernel, config, precision, sweeps, E, b, shots, io, launch_ms, peak, peak_src, traffic=None):
+    """The BP kernels' algorithmic bytes (every variable-to-check message read and written once per
+    executed sweep, plus the per-shot I/O) over the launch time, against the HBM copy bandwidth."""
+    by = sweeps * 2 * E * b + shots * io
+    ach = by / (launch_ms / 1000.0) / 1e9
+    return {"kernel": kernel, "config": config, "precision": precision, "bound": "hbm", "achieved": ach,
+            "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic, "peak_source": peak_src,
+            "bytes_per_launch": int(by), "launch_ms": launch_ms}
+
+
+def lsd_roofline(config, wordops, lsd_ms, lsd_shots):
+    peak = SM_COUNT_NOMINAL * INT_OPS_PER_CLK * SM_CLOCK_GHZ   # G ops/s
+    ach = wordops / (lsd_ms / 1000.0) / 1e9 if lsd_ms > 0 else 0.0
+    return {"kernel": "k_lsd (LSD-0 / order-lambda)", "config": config, "bound": "alu", "achieved": ach,
+            "peak": peak, "unit": "Gop/s", "frac": ach / peak, "traffic": None,
+            "peak_source": "152 SMs x 128 int32 lanes x 2.07 GHz", "ops_per_launch": int(wordops),
+            "launch_ms": lsd_ms, "lsd_shots": int(lsd_shots),
+            "what": "32-bit words XOR-ed by the GF(2) eliminations (VIBE_CNT_LSD_WORDOPS)"}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ------------------------------------------------------------------------------------------------
 
 def cpu_baseline(dm, w, syn, perms, target_s=12.0, max_shots=200_000):
     """The oracle as it stands, all host cores, on a bounded prefix of the same shots."""
@@ -128,6 +189,24 @@ def cpu_baseline(dm, w, syn, perms, target_s=12.0, max_shots=200_000):
     return {"value": S / dt, "unit": "shots/s", "cores": cores, "kind": "oracle",
             "sample": f"first {S} shots of the {len(syn)}-shot workload (seed {w['seed']}), FP32 oracle, "
                       f"{cores} threads, {dt:.1f} s"}, ref, S
+
+
+def fp64_oracle_ler(dm, w, syn, obs, shots):
+    """The oracle in FP64 on the first `shots` shots: the reference logical error rate."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.decode(dm, perms_of(dm, w), syn[:shots], w["T"], w["alpha"], w["M"], mode=oracle.FP64,
+                      nthreads=cores, want_soft=False)
+    fails = int((r["logical"] != obs[:shots]).any(axis=1).sum())
+    out = ler_ci(fails, shots)
+    out["seconds"] = time.perf_counter() - t0
+    out["cores"] = cores
+    return out
+
+
+def perms_of(dm, w):
+    return D.schedules(dm.n, w["K"], w["seed"])
 
 
 def run_reference(args):
@@ -170,10 +249,180 @@ def run_reference(args):
     return 0
 
 
-def ler_ci(fails, shots):
-    p = fails / shots if shots else 0.0
-    sd = (p * (1 - p) / shots) ** 0.5 if shots else 0.0
-    return {"ler": p, "two_sigma": [max(0.0, p - 2 * sd), p + 2 * sd], "failures": int(fails), "shots": int(shots)}
+# ------------------------------------------------------------------------------------------------
+# GPU legs
+# ------------------------------------------------------------------------------------------------
+
+def timed_decode(V, dec, syn_d, obs_d, dev, steps=1):
+    """Warm-up on an all-zero batch of the same size (allocates the workspace, loads the kernels,
+    costs no BP work), then `steps` timed decodes. Returns (ms per step list, counters, profile, out)."""
+    import torch
+    zero = torch.zeros_like(syn_d)
+    out = dec.decode(zero, observables=obs_d)
+    torch.cuda.synchronize()
+    cnt = torch.zeros(8, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    dec.profile(True)
+    ms = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = dec.decode(syn_d, observables=obs_d, counters=cnt, out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    prof = dec.profile_read()
+    dec.profile(False)
+    return ms, cnt.cpu().numpy(), prof, out
+
+
+def circuit_leg(V, dev, peaks, peak_src, cpu=True):
+    """Config 3: d=11 circuit-level colour code, K=64, T=50, M=5; FP32/FP16 LSD-0 and FP32 LSD-5."""
+    import torch
+    d, K, T, M, B, seed = 11, 64, 50, 5, 3648, 3
+    dm = C.circuit_dem(d, d, 1e-3, noise="si1000", basis="X")
+    syn, obs = D.sample(dm, B, seed)
+    perms = D.schedules(dm.n, K, seed)
+    syn_d = torch.from_numpy(syn.view(np.int32)).to(dev)
+    obs_d = torch.from_numpy(obs.view(np.int32)).to(dev)
+    E = dm.H.nnz
+    io = io_bytes_per_shot(dm)
+    res, rl, outs = {}, [], {}
+    for label, fp16, order in [("f32", False, 0), ("f16", True, 0), ("f32_lsd5", False, 5)]:
+        dec = V.Decoder(dm, K, perms, T=T, M=M, lsd_order=order, msg_fp16=fp16)
+        ms, c, prof, out = timed_decode(V, dec, syn_d, obs_d, dev)
+        outs[label] = out["corrections"].clone()
+        sweeps = int(c[V.CNT_PAIR_ITERS])
+        res[label] = {"value": B / (sum(ms) / 1000.0), "ms_per_step": statistics.mean(ms),
+                      "ler": ler_ci(int(c[V.CNT_FAILURES]), B), "lsd_fraction": int(c[V.CNT_LSD]) / B,
+                      "sweeps_per_shot": sweeps / B, "rescans_per_sweep": int(c[V.CNT_RESCANS]) / max(1, sweeps),
+                      "bp_ms": prof["bp_ms"], "lsd_ms": prof["lsd_ms"]}
+        if order == 0:
+            rl.append(hbm_roofline("k_bpx (summary engine)", "circuit_d11", "f16" if fp16 else "f32", sweeps, E,
+                                   2 if fp16 else 4, B, io, prof["bp_ms"], float(peaks.get("hbm_gbs", 6800.0)),
+                                   peak_src))
+        rl.append(lsd_roofline("circuit_d11 " + label, int(c[V.CNT_LSD_WORDOPS]), prof["lsd_ms"], int(c[V.CNT_LSD])))
+        dec.close()
+    res["f16"]["corrections_differ_vs_f32"] = int((outs["f16"] != outs["f32"]).any(dim=1).sum().item()) / B
+    f32 = res["f32"]["ler"]
+    res["f16"]["ler_inside_f32_two_sigma"] = bool(f32["two_sigma"][0] <= res["f16"]["ler"]["ler"] <= f32["two_sigma"][1])
+    leg = {"workload": f"circuit_d11: colour code d=11, 11 rounds, Si1000 p=1e-3 (X memory), m={dm.m}, n={dm.n}, "
+                       f"E={E}; K={K} seeded serial schedules, T={T}, M={M}, alpha=0.625; {B} shots per step "
+                       f"(seed {seed}), one timed step per precision after an all-zero warm-up batch",
+           "shots_per_step": B, **res}
+    if cpu:
+        import oracle
+        cores = os.cpu_count() or 1
+        S = cores
+        t0 = time.perf_counter()
+        r = oracle.decode(dm, perms, syn[:S], T, 0.625, M, nthreads=cores, want_soft=False)
+        dt = time.perf_counter() - t0
+        leg["cpu_baseline"] = {"value": S / dt, "unit": "shots/s", "cores": cores, "kind": "oracle",
+                               "sample": f"first {S} shots (seed {seed}), FP32 oracle, one shot per thread, {dt:.1f} s"}
+        leg["parity_sample"] = {"shots": S, "corrections_equal": bool(np.array_equal(
+            outs["f32"][:S].cpu().numpy().view(np.uint32), r["corrections"]))}
+    return leg, rl
+
+
+MIXED_DS = (5, 7, 9, 11, 13, 15)
+MIXED_PS = (1e-3, 2e-3, 3e-3, 5e-3)
+
+
+def mixed_leg(V, dev, peaks, peak_src):
+    """Config 4: 24 circuit-level problems in one mixed launch replayed from a CUDA graph."""
+    import torch
+    K, T, per_dem, seed = 32, 20, 152, 4
+    dems, decs, names = [], [], []
+    for d in MIXED_DS:
+        for p in MIXED_PS:
+            dm = C.circuit_dem(d, d, p, noise="si1000", basis="X")
+            M = 5 if d <= 11 else 7
+            decs.append(V.Decoder(dm, K, D.schedules(dm.n, K, 100 + d), T=T, M=M, msg_fp16=True))
+            dems.append(dm)
+            names.append(f"d{d}_p{p:g}")
+    mb = V.MixedBatch(decs)
+    rng = np.random.default_rng(seed)
+    B = per_dem * len(dems)
+    pid = rng.permutation(np.repeat(np.arange(len(dems), dtype=np.int32), per_dem))
+    syn = np.zeros((B, mb.mw), np.uint32)
+    obs = np.zeros((B, mb.kw), np.uint32)
+    for i, dm in enumerate(dems):
+        rows = np.nonzero(pid == i)[0]
+        s, o = D.sample(dm, len(rows), 400 + i)
+        syn[rows, :s.shape[1]] = s
+        obs[rows, :o.shape[1]] = o
+    pid_d = torch.from_numpy(pid).to(dev)
+    syn_d = torch.from_numpy(syn.view(np.int32)).to(dev)
+    obs_d = torch.from_numpy(obs.view(np.int32)).to(dev)
+    cnt = torch.zeros(8, dtype=torch.int64, device=dev)
+    out = mb.decode(pid_d, torch.zeros_like(syn_d), observables=obs_d, counters=cnt)   # workspace, modules
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            mb.decode(pid_d, syn_d, observables=obs_d, counters=cnt, stream=s, out=out)
+    torch.cuda.synchronize()
+    cnt.zero_()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):   # replay() launches on the current stream: time it there
+        a.record(s)
+        g.replay()
+        b.record(s)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    c = cnt.cpu().numpy()
+    logical = out["logical"].cpu().numpy().view(np.uint32)
+    fails = (logical != obs).any(axis=1)
+    per = {}
+    for i, nm in enumerate(names):
+        rows = pid == i
+        per[nm] = ler_ci(int(fails[rows].sum()), int(rows.sum()))
+    leg = {"workload": f"mixed: colour codes d in {list(MIXED_DS)} x Si1000 p in {list(MIXED_PS)} (24 problems), "
+                       f"K={K}, T={T}, M=5 (d<=11) / 7 (d>=13), FP16 messages; {per_dem} shots per problem "
+                       f"interleaved at random (seed {seed}), one mixed launch replayed from a CUDA graph",
+           "shots_per_step": B, "value": B / (ms / 1000.0), "ms_per_step": ms,
+           "latency_ms": {"p50": ms, "p99": ms, "per": f"graph replay of the whole {B}-shot batch"},
+           "lsd_fraction": int(c[V.CNT_LSD]) / B, "ler_per_problem": per,
+           "sweeps_per_shot": int(c[V.CNT_PAIR_ITERS]) / B}
+    mb.close()
+    for dc in decs:
+        dc.close()
+    return leg, []
+
+
+def run_case(args):
+    """One warm-up and one decode of a named case, for profiling."""
+    import torch
+    from paper_2508_15743_gb300 import vibe as V
+    cases = {
+        "pheno_d9": (lambda: D.build_workload(WORKLOAD), 16, 30, 5, False, 20_000, 2),
+        "pheno_d9_fp16": (lambda: D.build_workload(WORKLOAD), 16, 30, 5, True, 20_000, 2),
+        "circuit_d11_k16": (lambda: C.circuit_dem(11, 11, 1e-3, noise="si1000", basis="X"), 16, 50, 5, False, 1824, 3),
+        "circuit_d11_k16_fp16": (lambda: C.circuit_dem(11, 11, 1e-3, noise="si1000", basis="X"), 16, 50, 5, True, 2432,
+                                 3),
+    }
+    build, K, T, M, fp16, shots, seed = cases[args.case]
+    dm = build()
+    B = args.shots or shots
+    dec = V.Decoder(dm, K, D.schedules(dm.n, K, seed), T=T, M=M, msg_fp16=fp16)
+    syn, obs = D.sample(dm, B, seed)
+    syn_t = torch.from_numpy(syn.view(np.int32)).cuda()
+    dec.decode(syn_t[:64])
+    torch.cuda.synchronize()
+    cnt = torch.zeros(V.VIBE_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    dec.profile(True)
+    dec.decode(syn_t, counters=cnt)
+    torch.cuda.synchronize()
+    prof = dec.profile_read()
+    c = cnt.cpu().numpy()
+    dec.close()
+    print(json.dumps(dict(case=args.case, shots=int(c[V.CNT_SHOTS]), sweeps=int(c[V.CNT_PAIR_ITERS]),
+                          lsd=int(c[V.CNT_LSD]), rescans=int(c[V.CNT_RESCANS]), lsd_wordops=int(c[V.CNT_LSD_WORDOPS]),
+                          bp_ms=prof["bp_ms"], lsd_ms=prof["lsd_ms"], n=dm.n, m=dm.m, E=int(dm.H.nnz))))
+    return 0
 
 
 def run_vibe(args):
@@ -195,6 +444,8 @@ def run_vibe(args):
     obs_d = torch.from_numpy(obs.view(np.int32)).to(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
 
     def barrier():
         if world > 1:
@@ -241,7 +492,8 @@ def run_vibe(args):
         c = cnt.cpu().numpy()
         total_ms = max_over_ranks(sum(step_ms))
         results[label] = dict(step_ms=step_ms, total_ms=total_ms, prof=prof, counters=c, clocks=clk, wall=wall,
-                              corr=out["corrections"].clone(), logical=out["logical"].clone())
+                              corr=out["corrections"].clone(), logical=out["logical"].clone(),
+                              RP=int(np.diff(dm.H.rowptr).max() + 7) // 8 * 8)
         # end to end through the host-buffer entry point (H2D + decode + D2H every step)
         if label == "f32":
             hsyn = torch.from_numpy(syn.view(np.int32)).pin_memory()
@@ -271,19 +523,31 @@ def run_vibe(args):
     differ = int((r32["corr"] != r16["corr"]).any(dim=1).sum().item())
     value = B * world * args.steps / (r32["total_ms"] / 1000.0)
     v16 = B * world * args.steps / (r16["total_ms"] / 1000.0)
-    peaks, peak_src = measured_peaks()
     E = dm.H.nnz
-    pair_iters = int(r32["counters"][3]) // args.steps
-    io_bytes_per_shot = 4 * (dm.m + 31) // 32 + 4 * ((dm.n + 31) // 32) + 4 + 12
-    bp_bytes = pair_iters * 2 * E * 4 + B * io_bytes_per_shot
-    bp_ms = r32["prof"]["bp_ms"] / max(1, r32["prof"]["bp_launches"])
-    achieved = bp_bytes / (bp_ms / 1000.0) / 1e9
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    lat = sorted(r32["step_ms"])
-    lat16 = sorted(r16["step_ms"])
-
-    def pct(a, q):
-        return a[min(len(a) - 1, int(round(q * (len(a) - 1))))]
+    io = io_bytes_per_shot(dm)
+    rooflines = []
+    for label, b in [("f32", 4), ("f16", 2)]:
+        r = results[label]
+        sweeps = int(r["counters"][3]) // args.steps
+        ms = r["prof"]["bp_ms"] / max(1, r["prof"]["bp_launches"])
+        entry = hbm_roofline("k_bp (image engine)", WORKLOAD, label, sweeps, E, b, B, io, ms, hbm_peak, peak_src)
+        # shared-memory view: each column update scans the whole padded row of each of its checks
+        # (RP slots of b bytes) and writes its messages back
+        smem_bytes = sweeps * E * (r["RP"] + 1) * b
+        smem_peak = SM_COUNT_NOMINAL * SMEM_BYTES_PER_CLK * SM_CLOCK_GHZ   # GB/s
+        smem_ach = smem_bytes / (ms / 1000.0) / 1e9
+        entry["smem_row_scans"] = {"bound": "smem", "achieved": smem_ach, "peak": smem_peak, "unit": "GB/s",
+                                   "frac": smem_ach / smem_peak, "bytes_per_launch": int(smem_bytes),
+                                   "peak_source": "152 SMs x 128 B/clk x 2.07 GHz"}
+        rooflines.append(entry)
+        rooflines.append(lsd_roofline(WORKLOAD + " " + label, int(r["counters"][7]) // args.steps,
+                                      r["prof"]["lsd_ms"] / max(1, r["prof"]["lsd_launches"]),
+                                      int(r["counters"][2]) // args.steps))
+    main_rl = dict(rooflines[0])
+    main_rl.pop("smem_row_scans", None)
+    main_rl["kernel"] = "k_bp (persistent BP ensemble, image engine)"
+    main_rl["lsd_kernel_ms"] = r32["prof"]["lsd_ms"] / max(1, r32["prof"]["lsd_launches"])
+    lat, lat16 = r32["step_ms"], r16["step_ms"]
 
     line = {
         "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
@@ -299,12 +563,9 @@ def run_vibe(args):
                  "ler": ler_ci(f16_fail, B), "corrections_differ_vs_f32": differ / B},
         "ler": ler_ci(f32_fail, B),
         "lsd_fraction": int(r32["counters"][2]) / (B * args.steps),
-        "pair_iters_per_shot": pair_iters / B,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_bp (persistent BP ensemble)",
-                     "peak_source": peak_src,
-                     "bytes_per_launch": bp_bytes, "launch_ms": bp_ms,
-                     "lsd_kernel_ms": r32["prof"]["lsd_ms"] / max(1, r32["prof"]["lsd_launches"])},
+        "pair_iters_per_shot": int(r32["counters"][3]) / (B * args.steps),
+        "roofline": main_rl,
+        "rooflines": rooflines,
         "e2e": {"value": results["e2e"]["value"], "unit": "shots/s", "h2d_bytes_per_step": results["e2e"]["h2d"],
                 "d2h_bytes_per_step": results["e2e"]["d2h"]},
         "gpu_launches": int(r32["prof"]["bp_launches"] + r32["prof"]["lsd_launches"]),
@@ -315,6 +576,23 @@ def run_vibe(args):
         gpu_corr = r32["corr"][:S].cpu().numpy().view(np.uint32)
         line["cpu_baseline"] = cb
         line["parity_sample"] = {"shots": S, "corrections_equal": bool(np.array_equal(gpu_corr, ref["corrections"]))}
+        ref64 = fp64_oracle_ler(dm, w, syn, obs, min(B, 30_000))
+        line["ler_fp64_oracle"] = dict(ref64, sample=f"first {ref64['shots']} shots, oracle in FP64",
+                                       fp16_inside_two_sigma=bool(ref64["two_sigma"][0] <= line["fp16"]["ler"]["ler"]
+                                                                  <= ref64["two_sigma"][1]),
+                                       fp32_inside_two_sigma=bool(ref64["two_sigma"][0] <= line["ler"]["ler"]
+                                                                  <= ref64["two_sigma"][1]))
+    if rank == 0 and args.legs != "none":
+        legs = args.legs.split(",") if args.legs != "all" else ["circuit_d11", "mixed"]
+        if "circuit_d11" in legs:
+            leg, rl = circuit_leg(V, dev, peaks, peak_src, cpu=world == 1 and not args.no_cpu_baseline)
+            line["circuit_d11"] = leg
+            line["rooflines"] += rl
+            line["gpu_launches"] += 6
+        if "mixed" in legs:
+            leg, rl = mixed_leg(V, dev, peaks, peak_src)
+            line["mixed"] = leg
+            line["gpu_launches"] += 3
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -331,9 +609,13 @@ def main():
     ap.add_argument("--impl", default="vibe", choices=["vibe", "reference"])
     ap.add_argument("--shots", type=int, default=0, help="override shots per GPU (default: the workload's 10^6)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="all", help="all, none, or a comma list of circuit_d11,mixed")
+    ap.add_argument("--case", default="", help="run one named profiling case and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_vibe(args)

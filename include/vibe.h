@@ -97,7 +97,8 @@ typedef struct {
 #define VIBE_CNT_PAIR_ITERS 3  /* BP sweeps executed, summed over (shot, member) pairs */
 #define VIBE_CNT_UNSOLVABLE 4
 #define VIBE_CNT_BAD_PROBLEM 5 /* vibe_batch_decode shots with an out-of-range problem index */
-#define VIBE_CNT_RESCANS 6     /* summary engine: check rows rescanned (a min holder's message grew) */
+#define VIBE_CNT_RESCANS 6     /* summary engine: check rows rescanned (a summary could not answer) */
+#define VIBE_CNT_LSD_WORDOPS 7 /* LSD: 32-bit words XOR-ed by its GF(2) eliminations (its integer work) */
 #define VIBE_NUM_COUNTERS 8
 
 typedef struct vibe_handle vibe_handle;

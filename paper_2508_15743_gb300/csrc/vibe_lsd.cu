@@ -111,13 +111,16 @@ __device__ __forceinline__ int lowest_bit(const uint32_t (&x)[WP], int lane) {
 
 // x <- x reduced by the basis rows listed from `head` (insertion order); comb tracks the same XORs
 // over the rows' column combinations when TRACK.
+// ops counts the 32-bit words XOR-ed (the same on every lane of the warp).
 template <int WP, bool TRACK>
 __device__ __forceinline__ void reduce(uint32_t (&x)[WP], uint32_t (&comb)[WP], int head, const LsdShared& S,
-                                       const uint32_t* basis, const uint32_t* combrow, int W, int CW, int lane) {
+                                       const uint32_t* basis, const uint32_t* combrow, int W, int CW, int lane,
+                                       unsigned long long& ops) {
   const int maxrows = 32 * W;   // a basis never has more rows than checks
   int g = 0;
   for (int p = head; p >= 0 && g < maxrows; p = S.piv_next[p], ++g) {
     if (get_bit<WP>(x, p, lane)) {
+      ops += (unsigned long long)(W + (TRACK ? CW : 0));
 #pragma unroll
       for (int q = 0; q < WP; ++q) {
         const int w = lane + 32 * q;
@@ -183,6 +186,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
   // combination records cover the first 32 * CW columns of a cluster in reliability order
   const int mB = a.bnd.m, nB = a.bnd.n, WB = a.bnd.W, nwB = a.bnd.nw, CWB = min((a.bnd.n + 31) / 32, 32 * WP);
   const bool cols_smem = lsd_cols_in_smem(a.bnd);
+  unsigned long long gf2_ops = 0;   // words this warp XOR-ed in eliminations (VIBE_CNT_LSD_WORDOPS)
   uint32_t* basis = a.scratch + (long long)blockIdx.x * a.scratch_pitch;   // m * W
   LsdShared S;
   Tables* sdem;
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
         int guard = 0;
         for (int j = S.p_head[r]; j >= 0 && guard < n; j = S.pend_next[j], ++guard) {
           load_column<WP>(t, j, x, lane);
-          reduce<WP, false>(x, dummy, S.b_head[r], S, basis, combrow, W, CW, lane);
+          reduce<WP, false>(x, dummy, S.b_head[r], S, basis, combrow, W, CW, lane, gf2_ops);
           if (any_bits<WP>(x)) {
             const int p = lowest_bit<WP>(x, lane);
             append_row<WP, false>(x, dummy, p, r, S, basis, combrow, W, CW, &S.b_head[r], &S.b_tail[r], lane);
@@ -363,7 +367,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
           }
           x[qq] = keep;
         }
-        reduce<WP, false>(x, dummy, S.b_head[r], S, basis, combrow, W, CW, lane);
+        reduce<WP, false>(x, dummy, S.b_head[r], S, basis, combrow, W, CW, lane, gf2_ops);
         const bool ok = !any_bits<WP>(x);
         if (lane == 0) S.valid[r] = ok ? 1 : 0;
         __syncwarp();
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
 #pragma unroll
           for (int qq = 0; qq < WP; ++qq)
             comb[qq] = ((tp >> 5) == lane + 32 * qq) ? (1u << (tp & 31)) : 0u;
-          reduce<WP, true>(x, comb, S.b_head[r], S, basis, combrow, W, CW, lane);
+          reduce<WP, true>(x, comb, S.b_head[r], S, basis, combrow, W, CW, lane, gf2_ops);
           if (any_bits<WP>(x)) {
             const int p = lowest_bit<WP>(x, lane);
             append_row<WP, true>(x, comb, p, r, S, basis, combrow, W, CW, &S.b_head[r], &S.b_tail[r], lane);
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
           x[qq] = keep;
           comb[qq] = 0u;
         }
-        reduce<WP, true>(x, comb, S.b_head[r], S, basis, combrow, W, CW, lane);
+        reduce<WP, true>(x, comb, S.b_head[r], S, basis, combrow, W, CW, lane, gf2_ops);
         const int q = min(t.lsd_order, nfree);
         if (q == 0) {
 #pragma unroll
@@ -556,6 +560,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
       }
     }
   }
+  if (lane == 0 && a.counters && gf2_ops) atomicAdd(a.counters + VIBE_CNT_LSD_WORDOPS, gf2_ops);
 }
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }

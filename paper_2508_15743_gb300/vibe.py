@@ -21,6 +21,7 @@ VIBE_ERR_CUDA = -3
 VIBE_ERR_UNSUPPORTED = -4
 VIBE_NUM_COUNTERS = 8
 CNT_SHOTS, CNT_FAILURES, CNT_LSD, CNT_PAIR_ITERS, CNT_UNSOLVABLE, CNT_BAD_PROBLEM, CNT_RESCANS = 0, 1, 2, 3, 4, 5, 6
+CNT_LSD_WORDOPS = 7
 VIBE_STATUS_OK, VIBE_STATUS_UNSOLVABLE, VIBE_STATUS_BAD_PROBLEM, VIBE_STATUS_CLUSTER_LIMIT = 0, 1, 2, 3
 
 STATS_DTYPE = np.dtype([("status", "u1"), ("lsd_invoked", "u1"), ("n_converged", "u1"),
