@@ -546,6 +546,9 @@ def run_vibe(args):
     main_rl = dict(rooflines[0])
     main_rl.pop("smem_row_scans", None)
     main_rl["kernel"] = "k_bp (persistent BP ensemble, image engine)"
+    main_rl["what"] = ("algorithmic message bytes (2*E*4 per executed sweep plus per-shot I/O) over the measured HBM "
+                       "copy bandwidth; the messages live in shared memory, so DRAM carries only the I/O (traffic) "
+                       "and rooflines[0].smem_row_scans gives the shared-memory view")
     main_rl["lsd_kernel_ms"] = r32["prof"]["lsd_ms"] / max(1, r32["prof"]["lsd_launches"])
     lat, lat16 = r32["step_ms"], r16["step_ms"]
 

@@ -188,13 +188,17 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
  *   (counters, one n-float accumulator per BP warp, one row set per LSD CTA); a batch that does not
  *   fit returns VIBE_ERR_UNSUPPORTED with the largest batch that does (about 15,000 shots for the
  *   d=9 phenomenological problem) -- split larger batches into several calls.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with the
- *   handle's device current; make that first call before any stream capture.
+ *   CUDA loads device code lazily by default (CUDA_MODULE_LOADING=EAGER changes that), so the array is
+ *   placed on a device, and its address looked up (cudaGetSymbolAddress, with the handle's device
+ *   current), at the first call on that device -- which may need 64 MiB of free device memory. A call
+ *   with B = 0 does exactly that set-up and decodes nothing: make one per device while allocation is
+ *   still allowed and before any stream capture. The address is kept for the life of the process; do
+ *   not use this entry point after cudaDeviceReset.
  *   Every call on a device shares the one array, and its contents persist between calls (the call
  *   clears the counters it needs). Calls whose work overlaps on the GPU -- on different streams or
  *   from different threads without ordering -- race on it and must be serialised by the caller.
  *   Errors: VIBE_ERR_INVALID (NULL handle/pointers, B < 0, handle's device not current),
- *   VIBE_ERR_UNSUPPORTED (batch too large), VIBE_ERR_CUDA. B = 0 is a no-op.
+ *   VIBE_ERR_UNSUPPORTED (batch too large), VIBE_ERR_CUDA. B = 0 performs only the set-up above.
  */
 int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
                         uint32_t* d_logical, vibe_shot_stats* d_stats, void* stream);

@@ -4,8 +4,17 @@
 // outgrows it. Some callers cannot allow that: a control loop that must keep a fixed memory
 // footprint once it is running, a process that shares the GPU under a hard memory budget, or code
 // that runs where the CUDA allocator may not be entered. For them this entry point decodes with
-// scratch memory that exists from the moment the library is loaded: one file-scope device array of
-// kStaticBytes (64 MiB) on every GPU that loads the library, held until the process exits.
+// scratch memory in one file-scope device array of kStaticBytes (64 MiB) per GPU, held until the
+// process exits.
+//
+// When the array comes into being: CUDA loads a library's device code lazily by default (since
+// CUDA 12.2, unless CUDA_MODULE_LOADING=EAGER), so the array is placed on a device the first time
+// this file's set-up asks for its address -- the first call of this entry point on that device,
+// which may therefore need 64 MiB of free device memory. A call with B = 0 does that set-up and
+// decodes nothing: make one on each device while allocation is still allowed (and before any
+// stream capture); every later call allocates nothing. The address is kept per device for the
+// life of the process: after cudaDeviceReset (or anything else that destroys the primary
+// context) the entry point must not be used again in that process.
 //
 // The kernels are the same BP ensemble and LSD kernels vibe_decode runs; only their scratch
 // (shot and LSD counters, the LSD hand-off queue, the per-warp LLR accumulators, the per-CTA LSD
@@ -53,7 +62,13 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   int rc = vibe::handle_view(h, &v);
   if (rc != VIBE_OK) return rc;
   if (B < 0) return vibe::set_error(VIBE_ERR_INVALID, "negative batch");
-  if (B == 0) return VIBE_OK;
+  if (B == 0) {   // set-up only: place the array on this device and look up its address
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != v.device)
+      return vibe::set_error(VIBE_ERR_INVALID, "the handle's device must be current");
+    unsigned char* base = nullptr;
+    return scratch_address(v.device, &base);
+  }
   if (!d_syndromes || !d_corrections) return vibe::set_error(VIBE_ERR_INVALID, "NULL syndromes or corrections");
   const vibe::Tables& t = v.t;
   if (t.engine != VIBE_ENGINE_IMAGE)

@@ -1,8 +1,9 @@
 """vibe_decode_noalloc against vibe_decode, through the C ABI, on two calls in a row.
 
 The no-allocation entry point serves callers that cannot allocate device memory once they are
-decoding; it must give exactly what vibe_decode gives. This file runs last (collection order) so
-that a failure here does not hide the other GPU tests; it must also pass alone in a fresh process.
+decoding; it must give exactly what vibe_decode gives, and after its zero-shot set-up call the
+device's free memory must not change across a call. This file runs last (collection order) so that
+a failure here does not hide the other GPU tests; it must also pass alone in a fresh process.
 """
 import numpy as np
 import pytest
@@ -30,6 +31,7 @@ def test_noalloc_matches_decode_on_two_calls(V, fp16):
     dm = D.build_workload("cc666_d9_pheno")
     perms = D.schedules(dm.n, w["K"], w["seed"])
     dec = V.Decoder(dm, w["K"], perms, T=w["T"], alpha=w["alpha"], M=w["M"], msg_fp16=fp16)
+    V.vibe_decode_noalloc(dec.handle, None, 0, None)   # set-up: places the static array on this device
     for call, (B, seed) in enumerate([(3000, 501), (1777, 502)]):
         syn, _ = D.sample(dm, B, seed)
         syn_t = torch.from_numpy(syn.view(np.int32)).cuda()
@@ -37,8 +39,11 @@ def test_noalloc_matches_decode_on_two_calls(V, fp16):
         corr = torch.full((B, dec.nw), -1, dtype=torch.int32, device="cuda")
         logi = torch.full((B, dec.kw), -1, dtype=torch.int32, device="cuda")
         stats = torch.full((B, 12), 255, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         V.vibe_decode_noalloc(dec.handle, syn_t, B, corr, logi, stats)
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, f"call {call}: device memory was allocated"
         assert torch.equal(corr, ref["corrections"]), f"call {call}: corrections differ"
         assert torch.equal(logi, ref["logical"]), f"call {call}: logical flips differ"
         assert torch.equal(stats, ref["stats"]), f"call {call}: per-shot records differ"
