@@ -68,6 +68,11 @@ typedef struct {
                         check-to-variable messages by member_alpha[i] instead of alpha, an ensemble
                         mixing heuristics (Sec. V); results, ranking and LLR average are otherwise
                         unchanged. Both engines, all schedules and storage precisions */
+  int32_t pair_mode; /* 0: one warp per shot runs the shot's members one after another (throughput);
+                        1: one warp per (shot, member) pair, so a shot's members run at the same time
+                        and its BP latency is that of its slowest member, not the sum (latency). The
+                        outputs are identical; pair mode does more sweeps in total (members run until
+                        they see M earlier candidates) and keeps every member's record per shot */
 } vibe_params;
 
 /* BP engines; both run one warp per shot and give the same bits. IMAGE: the member's whole message

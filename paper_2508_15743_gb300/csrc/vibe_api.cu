@@ -79,6 +79,7 @@ struct Launch {
   int msg_fp16 = 0;
   int device = 0, num_sms = 0;
   int bp_blocks_per_sm = 0, bpx_blocks_per_sm = 0, lsd_blocks_per_sm = 0;
+  int pair_mode = 0;                // one warp per (shot, member) pair (vibe_params.pair_mode)
   bool warp_engine() const { return (bnd.engines & 1) != 0; }
   bool cta_engine() const { return (bnd.engines & 2) != 0; }
   int bp_grid() const { return warp_engine() ? std::max(1, bp_blocks_per_sm * num_sms) : 0; }
@@ -88,43 +89,84 @@ struct Launch {
   long long bpx_pitch(bool soft) const {
     return (bnd.x_warp_scratch + (soft ? 4LL * bnd.M * bnd.n : 0LL) + 15) & ~15LL;
   }
+  // pair mode: bytes of one shot's member records (iteration, weight, correction, LLR term, posterior)
+  long long pair_shot_bytes(bool soft) const {
+    return (long long)bnd.K * (8LL + 4LL * bnd.nw + 4LL * bnd.n * (soft ? 2 : 1)) + 4;
+  }
+  // pair mode: shots per launch -- enough pairs for two per warp, within kPairBytes of records
+  long long pair_chunk(bool soft) const {
+    const long long warps = (long long)bp_grid() * vibe::kBpWarpsPerCta + (long long)bpx_grid() * vibe::kBpxWarpsPerCta;
+    const long long want = std::max(8LL, (2 * warps + bnd.K - 1) / std::max(1, bnd.K));
+    const long long cap = std::max(1LL, kPairBytes / pair_shot_bytes(soft));
+    return std::min(want, cap);
+  }
+  static constexpr long long kPairBytes = 1LL << 30;
 };
 
 // Device memory a decode uses besides its inputs and outputs; grown on demand, reused afterwards.
 struct Workspace {
   long long chunk = 0, chunk_max = 0;
+  long long pk_nw = 0, pk_n = 0;   // pair records' sizes per shot the buffers were made for
   int bp_warps = 0, lsd_ctas = 0;
   long long bpx_bytes = 0;
   unsigned int* ctrl = nullptr;   // [0] next shot (image engine), [1] LSD count, [2] next LSD shot,
-                                  // [3] next shot (summary engine)
+                                  // [3] next shot (summary engine), [4] / [5] next pair (image / summary)
   uint32_t* lsd_shots = nullptr;
   float* lsd_soft = nullptr;
   float* bp_scratch = nullptr;
   unsigned char* bpx_scratch = nullptr;
   uint32_t* lsd_scratch = nullptr;
+  // pair mode: member records of `pair_shots` shots (see BpArgs)
+  long long pair_shots = 0;
+  bool pair_soft = false;
+  int* pconv = nullptr;
+  float* pW = nullptr;
+  uint32_t* pbits = nullptr;
+  float* pterms = nullptr;
+  float* ppost = nullptr;
+  unsigned int* pdone = nullptr;
 
   void release() {
     cudaFree(ctrl); cudaFree(lsd_shots); cudaFree(lsd_soft); cudaFree(bp_scratch); cudaFree(bpx_scratch);
     cudaFree(lsd_scratch);
+    cudaFree(pconv); cudaFree(pW); cudaFree(pbits); cudaFree(pterms); cudaFree(ppost); cudaFree(pdone);
     ctrl = nullptr; lsd_shots = nullptr; lsd_soft = nullptr; bp_scratch = nullptr; bpx_scratch = nullptr;
     lsd_scratch = nullptr;
-    chunk = 0; bp_warps = 0; lsd_ctas = 0; bpx_bytes = 0;
+    pconv = nullptr; pW = nullptr; pbits = nullptr; pterms = nullptr; ppost = nullptr; pdone = nullptr;
+    chunk = 0; bp_warps = 0; lsd_ctas = 0; bpx_bytes = 0; pair_shots = 0; pair_soft = false;
   }
   int ensure(const Launch& L, long long need, bool soft) {
-    const long long want = std::min(need, chunk_max);
+    const long long ps = L.pair_mode ? std::min(need, L.pair_chunk(soft)) : 0;
+    const long long want = std::min(L.pair_mode ? ps : need, chunk_max);
     const int warps = L.bp_grid() * vibe::kBpWarpsPerCta;
     const long long xb = (long long)L.bpx_grid() * vibe::kBpxWarpsPerCta * L.bpx_pitch(soft);
-    if (ctrl && want <= chunk && warps <= bp_warps && L.lsd_grid() <= lsd_ctas && xb <= bpx_bytes) return VIBE_OK;
+    const bool pair_ok = !L.pair_mode || (ps <= pair_shots && (!soft || pair_soft) && L.bnd.K * L.bnd.nw <= pk_nw &&
+                                          L.bnd.K * L.bnd.n <= pk_n);
+    if (ctrl && want <= chunk && warps <= bp_warps && L.lsd_grid() <= lsd_ctas && xb <= bpx_bytes && pair_ok)
+      return VIBE_OK;
     const long long c = std::max(want, chunk);
     const long long xkeep = std::max(xb, bpx_bytes);
     release();
     const Bounds& b = L.bnd;
-    VIBE_CUDA(dalloc(&ctrl, 4), "workspace");
+    VIBE_CUDA(dalloc(&ctrl, 8), "workspace");
     VIBE_CUDA(dalloc(&lsd_shots, (size_t)c), "workspace");
     VIBE_CUDA(dalloc(&lsd_soft, (size_t)c * b.n), "workspace");
     VIBE_CUDA(dalloc(&bp_scratch, (size_t)warps * (size_t)(2 + b.M) * b.n), "workspace");
     VIBE_CUDA(dalloc(&bpx_scratch, (size_t)xkeep), "workspace");
     VIBE_CUDA(dalloc(&lsd_scratch, (size_t)L.lsd_grid() * (size_t)vibe::lsd_scratch_words(b)), "workspace");
+    if (L.pair_mode) {
+      const size_t S = (size_t)ps;
+      VIBE_CUDA(dalloc(&pconv, S * b.K), "workspace");
+      VIBE_CUDA(dalloc(&pW, S * b.K), "workspace");
+      VIBE_CUDA(dalloc(&pbits, S * b.K * (size_t)b.nw), "workspace");
+      VIBE_CUDA(dalloc(&pterms, S * b.K * (size_t)b.n), "workspace");
+      if (soft) VIBE_CUDA(dalloc(&ppost, S * b.K * (size_t)b.n), "workspace");
+      VIBE_CUDA(dalloc(&pdone, S), "workspace");
+      pair_shots = ps;
+      pair_soft = soft;
+      pk_nw = (long long)b.K * b.nw;
+      pk_n = (long long)b.K * b.n;
+    }
     chunk = c;
     bp_warps = warps;
     lsd_ctas = L.lsd_grid();
@@ -172,9 +214,14 @@ struct Batch {
 int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, cudaStream_t s) {
   int rc = ws.ensure(L, q.B, q.soft != nullptr);
   if (rc != VIBE_OK) return rc;
-  for (long long b0 = 0; b0 < q.B; b0 += ws.chunk) {
-    const long long nb = std::min(ws.chunk, q.B - b0);
-    VIBE_CUDA(cudaMemsetAsync(ws.ctrl, 0, 4 * sizeof(unsigned int), s), "decode");
+  const long long step = L.pair_mode ? std::min(ws.chunk, ws.pair_shots) : ws.chunk;
+  for (long long b0 = 0; b0 < q.B; b0 += step) {
+    const long long nb = std::min(step, q.B - b0);
+    VIBE_CUDA(cudaMemsetAsync(ws.ctrl, 0, 8 * sizeof(unsigned int), s), "decode");
+    if (L.pair_mode) {
+      VIBE_CUDA(cudaMemsetAsync(ws.pconv, 0, sizeof(int) * (size_t)nb * L.bnd.K, s), "decode");
+      VIBE_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(unsigned int) * (size_t)nb, s), "decode");
+    }
     vibe::BpArgs a{};
     a.one = L.one;
     a.dems = L.d_desc; a.ndem = L.ndem; a.dem_of_shot = q.dem_of_shot ? q.dem_of_shot + b0 : nullptr;
@@ -194,16 +241,23 @@ int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, c
     a.xscratch = ws.bpx_scratch;
     a.xscratch_pitch = L.bpx_pitch(a.want_soft != 0);
     a.next_shot_x = ws.ctrl + 3;
+    a.pair_mode = L.pair_mode;
+    a.pair_K = L.bnd.K;
+    a.pconv = ws.pconv; a.pW = ws.pW; a.pbits = ws.pbits; a.pterms = ws.pterms; a.ppost = ws.ppost;
+    a.pdone = ws.pdone;
+    a.next_pair = ws.ctrl + 4;
+    a.next_pair_x = ws.ctrl + 5;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (prof.on) { e0 = prof.next(); e1 = prof.next(); e2 = prof.next(); }
     if (e0) cudaEventRecord(e0, s);
+    const long long units = L.pair_mode ? nb * L.bnd.K : nb;   // shots, or (shot, member) pairs
     if (L.warp_engine()) {
-      const int grid = (int)std::min<long long>(L.bp_grid(), (nb + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
+      const int grid = (int)std::min<long long>(L.bp_grid(), (units + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
       a.flag_bad = 1;
       VIBE_CUDA(vibe::launch_bp(a, L.msg_fp16, grid, s), "BP kernel launch");
     }
     if (L.cta_engine()) {
-      const int grid = (int)std::min<long long>(L.bpx_grid(), (nb + vibe::kBpxWarpsPerCta - 1) / vibe::kBpxWarpsPerCta);
+      const int grid = (int)std::min<long long>(L.bpx_grid(), (units + vibe::kBpxWarpsPerCta - 1) / vibe::kBpxWarpsPerCta);
       a.flag_bad = L.warp_engine() ? 0 : 1;
       VIBE_CUDA(vibe::launch_bpx(a, L.msg_fp16, grid, s), "BP kernel launch");
     }
@@ -260,7 +314,7 @@ Bounds bounds_over(const Tables* ts, int count) {
   for (int i = 0; i < count; ++i) {
     const Tables& t = ts[i];
     b.m = std::max(b.m, t.m); b.n = std::max(b.n, t.n); b.W = std::max(b.W, t.W); b.nw = std::max(b.nw, t.nw);
-    b.kw = std::max(b.kw, t.kw); b.M = std::max(b.M, t.M); b.DP = std::max(b.DP, t.DP);
+    b.kw = std::max(b.kw, t.kw); b.M = std::max(b.M, t.M); b.DP = std::max(b.DP, t.DP); b.K = std::max(b.K, t.K);
     b.lsd_order = std::max(b.lsd_order, t.lsd_order);
     if (t.engine == VIBE_ENGINE_IMAGE) {
       b.engines |= 1;
@@ -382,6 +436,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   if (p->bp_engine < VIBE_ENGINE_AUTO || p->bp_engine > VIBE_ENGINE_SUMMARY)
     return fail(VIBE_ERR_INVALID, "bp_engine must be VIBE_ENGINE_AUTO, _IMAGE or _SUMMARY");
   if (p->n_flood < 0 || p->n_flood > K) return fail(VIBE_ERR_INVALID, "n_flood must be in 0..K");
+  if (p->pair_mode != 0 && p->pair_mode != 1) return fail(VIBE_ERR_INVALID, "pair_mode must be 0 or 1");
   if (p->n_flood > 0 && p->msg_fp16)
     return fail(VIBE_ERR_UNSUPPORTED, "flooding members run with FP32 messages only");
   if (p->n_flood > 0 && p->bp_engine == VIBE_ENGINE_SUMMARY)
@@ -425,6 +480,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   if ((e = cudaDeviceGetAttribute(&h->L.num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
     return bail(cuda_fail(e, "device query"));
   h->L.msg_fp16 = p->msg_fp16;
+  h->L.pair_mode = p->pair_mode;
   Tables& t = h->t;
   t.m = m; t.n = n; t.k = k; t.E = E; t.K = K;
   t.RP = std::max(8, (maxrow + 7) / 8 * 8);
@@ -721,6 +777,7 @@ int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** o
     const vibe_handle* h = handles[i];
     if (h->device != h0->device) return fail(VIBE_ERR_INVALID, "handles live on different devices");
     if (h->L.msg_fp16 != h0->L.msg_fp16) return fail(VIBE_ERR_INVALID, "handles mix FP16 and FP32 messages");
+    if (h->L.pair_mode != h0->L.pair_mode) return fail(VIBE_ERR_INVALID, "handles mix pair mode and shot mode");
     desc[i] = h->t;
   }
   const Bounds b = bounds_over(desc.data(), count);
@@ -742,6 +799,7 @@ int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** o
   bt->L.ndem = count;
   bt->L.bnd = b;
   bt->L.msg_fp16 = h0->L.msg_fp16;
+  bt->L.pair_mode = h0->L.pair_mode;
   bt->L.device = h0->device;
   bt->L.num_sms = h0->L.num_sms;
   int rc = size_launch(bt->L);

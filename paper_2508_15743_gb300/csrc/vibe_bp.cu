@@ -230,6 +230,77 @@ template <>
 struct MinBlocks<__half> { static constexpr int value = 24 / kBpWarpsPerCta; };
 
 // Decodes one shot of problem t with the warp (the body of the persistent loop below).
+// One member (index i) of the shot whose syndrome bytes are in the warp's shared memory: initialises
+// the member's message image and runs up to `budget` sweeps, stopping at the first that leaves
+// H e = s, or before sweep `it` when stop(it) holds. Returns the converging sweep (0 if none) and in
+// `ran` the sweeps run; leaves the decisions in the warp's decision bytes and the posterior of the
+// last sweep in lpost when soft output is on or `keep_last` is set and the member reached sweep T.
+template <typename MT, int DP, int RPC, bool MIXED, typename Stop>
+__device__ __forceinline__ int run_member(const Tables& t, int i, int budget, bool want_soft, bool keep_last,
+                                          unsigned char* base, float* lpost, int lane, unsigned long long& my_iters,
+                                          int& ran, Stop stop) {
+  const int n = t.n, m = t.m, T = t.T;
+  const int m4 = (m + 3) >> 2;
+  const int n4 = (n + 3) >> 2;
+  const int msg_vec = (int)(((size_t)m * t.RP * sizeof(MT)) / 16);
+  const uint32_t* csc = t.csc_ent;
+  const float* lam = t.lam;
+  const int dp = MIXED ? t.DP : DP;   // one problem: the pitch is the launch's
+  const uint32_t rp = (uint32_t)t.RP;
+  MT* msgs = reinterpret_cast<MT*>(base + t.off_msg);
+  uint8_t* dec8 = base + t.off_dec;
+  uint8_t* s8 = base + t.off_s;
+  uint8_t* par8 = base + t.off_par;
+  // member init: messages from the prior image, decisions 0, parity = s
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(t.msg_init);
+    uint4* dst = reinterpret_cast<uint4*>(msgs);
+    for (int q = lane; q < msg_vec; q += 32) dst[q] = __ldg(src + q);
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(dec8);
+    for (int q = lane; q < n4; q += 32) d32[q] = 0u;
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(s8);
+    uint32_t* p32 = reinterpret_cast<uint32_t*>(par8);
+    for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
+  }
+  __syncwarp();
+
+  const uint32_t* sch = t.sched + (size_t)i * n;
+  const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
+  const int nl = __ldg(t.nlev + i);
+  const float alpha = __ldg(t.alpha_m + i);   // member i's scaling factor
+  int conv = 0;
+  ran = 0;
+  for (int it = 1; it <= budget; ++it) {
+    if (stop(it)) break;
+    // the posterior is needed after the last possible sweep of a member that may end without
+    // converging (LLR average) and, for soft output, after every sweep
+    float* lp = (want_soft || (it == T && keep_last)) ? lpost : nullptr;
+    bool flooded = false;
+    if constexpr (std::is_same<MT, float>::value) {
+      if (i < t.n_flood) {   // parallel schedule (the host allows it with FP32 messages only)
+        flood_sweep<DP>(t, alpha, msgs, dec8, s8, par8, lp, lane);
+        flooded = true;
+      }
+    }
+    for (int l = 0; l < nl && !flooded; ++l) {
+      const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
+      for (uint32_t idx = b + lane; idx < e; idx += 32) {
+        const uint32_t ent = __ldg(sch + idx);
+        update_column<MT, DP, RPC>(ent & 0xffffffu, (int)(ent >> 24), csc, dp, lam, rp, alpha, msgs, dec8, s8,
+                                   par8, lp);
+      }
+      __syncwarp();
+    }
+    ++my_iters;
+    ran = it;
+    uint32_t bad = 0;
+    const uint32_t* p32 = reinterpret_cast<const uint32_t*>(par8);
+    for (int q = lane; q < m4; q += 32) bad |= p32[q];
+    if (!__any_sync(kFull, bad)) { conv = it; break; }
+  }
+  return conv;
+}
+
 template <typename MT, int DP, int RPC, bool MIXED>
 __device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, uint32_t shot, unsigned char* base,
                                             float* acc, float* lpost, float* cand_post, int lane,
@@ -288,50 +359,9 @@ __device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, ui
   for (int i = 0; i < K; ++i) {
     const int budget = ncand < M ? T : __shfl_sync(kFull, c_t, M - 1) - 1;
     if (budget <= 0) break;
-    // member init: messages from the prior image, decisions 0, parity = s
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(t.msg_init);
-      uint4* dst = reinterpret_cast<uint4*>(msgs);
-      for (int q = lane; q < msg_vec; q += 32) dst[q] = __ldg(src + q);
-      uint32_t* d32 = reinterpret_cast<uint32_t*>(dec8);
-      for (int q = lane; q < n4; q += 32) d32[q] = 0u;
-      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(s8);
-      uint32_t* p32 = reinterpret_cast<uint32_t*>(par8);
-      for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
-    }
-    __syncwarp();
-
-    const uint32_t* sch = t.sched + (size_t)i * n;
-    const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
-    const int nl = __ldg(t.nlev + i);
-    const float alpha = __ldg(t.alpha_m + i);   // member i's scaling factor
-    int conv = 0;
-    for (int it = 1; it <= budget; ++it) {
-      // the posterior is needed after the last possible sweep of a member that may end without
-      // converging (LLR average) and, for soft output, after every sweep
-      float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
-      bool flooded = false;
-      if constexpr (std::is_same<MT, float>::value) {
-        if (i < t.n_flood) {   // parallel schedule (the host allows it with FP32 messages only)
-          flood_sweep<DP>(t, alpha, msgs, dec8, s8, par8, lp, lane);
-          flooded = true;
-        }
-      }
-      for (int l = 0; l < nl && !flooded; ++l) {
-        const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
-        for (uint32_t idx = b + lane; idx < e; idx += 32) {
-          const uint32_t ent = __ldg(sch + idx);
-          update_column<MT, DP, RPC>(ent & 0xffffffu, (int)(ent >> 24), csc, dp, lam, rp, alpha, msgs, dec8, s8,
-                                     par8, lp);
-        }
-        __syncwarp();
-      }
-      ++my_iters;
-      uint32_t bad = 0;
-      const uint32_t* p32 = reinterpret_cast<const uint32_t*>(par8);
-      for (int q = lane; q < m4; q += 32) bad |= p32[q];
-      if (!__any_sync(kFull, bad)) { conv = it; break; }
-    }
+    int ran = 0;
+    const int conv = run_member<MT, DP, RPC, MIXED>(t, i, budget, a.want_soft != 0, ncand == 0, base, lpost, lane,
+                                                    my_iters, ran, [](int) { return false; });
     if (conv) {
       // insert (conv, i); i exceeds every member already listed, so it goes after equal iterations
       const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
@@ -433,6 +463,81 @@ __device__ __forceinline__ void decode_shot(const BpArgs& a, const Tables& t, ui
   __syncwarp();
 }
 
+// Pair mode: member i of shot `shot` (slot `slot` of the chunk) with one warp; the last member of the
+// shot to finish writes the shot's outcome (pair_epilogue, vibe_internal.cuh).
+template <typename MT, int DP, int RPC, bool MIXED>
+__device__ __forceinline__ void decode_pair(const BpArgs& a, const Tables& t, uint32_t shot, int slot, int i,
+                                            unsigned char* base, float* lpost, int lane, unsigned long long& my_iters,
+                                            unsigned long long& my_shots, unsigned long long& my_fail) {
+  const int K = t.K, M = t.M, T = t.T, n = t.n, m = t.m, nw = t.nw, kw = t.kw;
+  if (i >= K) return;
+  const int m4 = (m + 3) >> 2;
+  uint8_t* s8 = base + t.off_s;
+  const uint8_t* dec8 = base + t.off_dec;
+  const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
+  uint32_t any = 0;
+  for (int c = lane; c < 4 * m4; c += 32) {
+    const uint32_t b = c < m ? (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u : 0u;
+    s8[c] = (uint8_t)b;
+    any |= b;
+  }
+  any = __any_sync(kFull, any);
+  __syncwarp();
+  if (!any && !a.want_soft) {
+    // s = 0: every member converges in iteration 1 to e = 0; member 0 is chosen -- written by member 0
+    if (i != 0) return;
+    ++my_shots;
+    for (int w = lane; w < nw; w += 32) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
+    if (a.logical)
+      for (int w = lane; w < kw; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+    if (a.obs) {
+      uint32_t f = 0;
+      for (int w = lane; w < kw; w += 32) f |= a.obs[(size_t)shot * a.log_stride + w];
+      if (__any_sync(kFull, f) && lane == 0) ++my_fail;
+    }
+    if (a.stats && lane == 0) {
+      vibe_shot_stats st;
+      st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)M; st.chosen_member = 0;
+      st.iters = 1; st.largest_cluster = 0; st.n_clusters = 0;
+      a.stats[shot] = st;
+    }
+    return;
+  }
+  if (i == 0) ++my_shots;
+  int* conv = a.pconv + (size_t)slot * a.pair_K;
+  int ran = 0;
+  const int cv = run_member<MT, DP, RPC, MIXED>(t, i, T, a.want_soft != 0, true, base, lpost, lane, my_iters, ran,
+                                                [&](int it) { return pair_should_stop(conv, K, M, i, it, lane); });
+  const size_t rec = (size_t)slot * a.pair_K + i;
+  if (cv) {
+    // the correction's bits and W(e) = sum of lambda_j over e_j = 1, ascending j
+    uint32_t* bits = a.pbits + rec * a.bnd.nw;
+    float W = 0.0f;
+    for (int w = 0; w < nw; ++w) {
+      const int v = 32 * w + lane;
+      const uint32_t word = __ballot_sync(kFull, v < n && dec8[v] != 0);
+      if (lane == 0) bits[w] = word;
+      uint32_t x = word;
+      while (x) {
+        const int bpos = __ffs(x) - 1;
+        W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
+        x &= x - 1;
+      }
+    }
+    if (lane == 0) a.pW[rec] = W;
+    if (a.want_soft)
+      for (int v = lane; v < n; v += 32) a.ppost[rec * a.bnd.n + v] = lpost[v];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile int*>(conv + i) = cv;
+  } else if (ran == T) {
+    llr_term_add(lpost, a.pterms + rec * a.bnd.n, n, true, lane);
+  }
+  __syncwarp();
+  if (pair_finish(a.pdone + slot, K, lane) && pair_epilogue(a, t, shot, slot, lane) && lane == 0) ++my_fail;
+  __syncwarp();
+}
+
 // MIXED: the shots of the launch name their problems (dem_of_shot); the problems' descriptors are
 // copied to shared memory after the warps' regions. Otherwise every shot decodes a.one, which the
 // kernel reads from its parameter space.
@@ -456,7 +561,40 @@ __global__ void __launch_bounds__(kBpWarpsPerCta * 32, MinBlocks<MT>::value) k_b
   float* cand_post = lpost + a.bnd.n;              // M * n floats (only with want_soft)
   unsigned long long my_iters = 0, my_shots = 0, my_fail = 0;
 
+  if (a.pair_mode) {
+    const unsigned long long npairs = (unsigned long long)a.nshots * (unsigned long long)a.pair_K;
+    for (;;) {
+      unsigned long long q = 0;
+      if (lane == 0) q = atomicAdd(a.next_pair, 1u);
+      q = __shfl_sync(kFull, q, 0);
+      if (q >= npairs) break;
+      const uint32_t shot = (uint32_t)(q / a.pair_K);
+      const int i = (int)(q % a.pair_K);
+      if (MIXED) {
+        const int di = __ldg(a.dem_of_shot + shot);
+        if ((unsigned)di >= (unsigned)a.ndem) {
+          if (i != 0 || !a.flag_bad) continue;
+          for (int w = lane; w < a.corr_stride; w += 32) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
+          if (a.logical)
+            for (int w = lane; w < a.log_stride; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+          if (a.stats && lane == 0) {
+            vibe_shot_stats st;
+            st.status = VIBE_STATUS_BAD_PROBLEM; st.lsd_invoked = 0; st.n_converged = 0; st.chosen_member = 0;
+            st.iters = 0; st.largest_cluster = 0; st.n_clusters = 0;
+            a.stats[shot] = st;
+          }
+          if (a.counters && lane == 0) atomicAdd(a.counters + VIBE_CNT_BAD_PROBLEM, 1ull);
+          continue;
+        }
+        if (sdem[di].engine != VIBE_ENGINE_IMAGE) continue;   // left to the summary engine
+        decode_pair<MT, DP, RPC, true>(a, sdem[di], shot, (int)shot, i, base, lpost, lane, my_iters, my_shots, my_fail);
+      } else {
+        decode_pair<MT, DP, RPC, false>(a, a.one, shot, (int)shot, i, base, lpost, lane, my_iters, my_shots, my_fail);
+      }
+    }
+  }
   for (;;) {
+    if (a.pair_mode) break;
     uint32_t shot = 0;
     if (lane == 0) shot = atomicAdd(a.next_shot, 1u);
     shot = __shfl_sync(kFull, shot, 0);

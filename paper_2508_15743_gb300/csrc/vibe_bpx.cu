@@ -144,7 +144,6 @@ struct SumIO;
 template <>
 struct SumIO<float> {
   float4* v;
-  static constexpr int kBytesPerCheck = 16;
   __device__ __forceinline__ float4 load(int c) const { return v[c]; }
   __device__ __forceinline__ void store(int c, float4 s) const { v[c] = s; }
   __device__ __forceinline__ void flip(int c, uint32_t bits) const { reinterpret_cast<uint32_t*>(v + c)[3] ^= bits; }
@@ -153,7 +152,6 @@ struct SumIO<float> {
 template <>
 struct SumIO<__half> {
   uint2* v;
-  static constexpr int kBytesPerCheck = 8;
   __device__ __forceinline__ static float hf(uint32_t b) { return __half2float(__ushort_as_half((unsigned short)b)); }
   __device__ __forceinline__ static uint32_t hb(float x) { return (uint32_t)__half_as_ushort(__float2half_rn(x)); }
   __device__ __forceinline__ float4 load(int c) const {
@@ -516,6 +514,106 @@ __device__ __forceinline__ void read_col(XRing<DP>& R, uint32_t q, const Chunk& 
   }
 }
 
+// One member (index i) on one shot: initialises the member's state and runs up to `budget` sweeps,
+// stopping at the first that leaves H e = s, or before sweep `it` when stop(it) holds. Returns the
+// converging sweep (0 if none) and in `ran` the sweeps run; leaves the decisions in X.dec and the
+// posterior of the last sweep in lpost when soft output is on or `keep_last` is set and the member
+// reached sweep T.
+template <typename MT, int DP, typename Stop>
+__device__ __forceinline__ int run_member_x(const BpArgs& a, const Tables& t, int i, const uint32_t* syn, int nsyn,
+                                            int budget, bool keep_last, XState<MT>& X, unsigned char* base,
+                                            float* lpost, int lane, uint32_t& my_iters, uint32_t& my_rescans,
+                                            int& ran, Stop stop) {
+  const int n = t.n, m = t.m, T = t.T, nw = t.nw;
+  X.rec = t.xrec + (size_t)i * n;
+  X.rmap = t.xrmap + (size_t)i * t.E;
+  // member init: prior summaries with this shot's syndrome (parity = s), prior messages in the
+  // member's schedule order, state words and decisions 0
+  for (int c = lane; c < m; c += 32) {
+    float4 s = __ldg(t.xsum + c);
+    const uint32_t sb = (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u;
+    s.w = __uint_as_float(__float_as_uint(s.w) | (sb ? (kSynBit | kParBit) : 0u));
+    X.S.store(c, s);
+  }
+  for (int j = lane; j < n; j += 32) {
+    const uint2 r = __ldg(X.rec + j);
+    const float x = XMsg<MT>::round(__ldg(t.lam + (r.x & 0xffffffu)));
+    for (uint32_t k = 0; k < (r.x >> 24); ++k) store_msg<MT>(X.msg + r.y + k, x);
+    __stcg(X.stw + j, 0u);
+  }
+  for (int w = lane; w < nw; w += 32) __stcg(X.dec + w, 0u);
+  __syncwarp();
+  const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
+  const int nl = __ldg(t.nlev + i);
+  XRing<DP> R{base};
+  const float alpha = __ldg(t.alpha_m + i);   // member i's scaling factor
+  int unsat = nsyn;
+  int conv = 0;
+  ran = 0;
+  for (int it = 1; it <= budget; ++it) {
+    if (stop(it)) break;
+    // the posterior is needed after the last possible sweep of a member that may end without
+    // converging (LLR average) and, for soft output, after every sweep
+    float* lp = (a.want_soft || (it == T && keep_last)) ? lpost : nullptr;
+    // the sweep in chunks of up to 32 columns of one level, one column per lane, through the ring:
+    // q counts chunks; the records of chunk q+2 and the column data of chunk q+1 are in flight while
+    // chunk q is updated
+    LevelWin W;
+    W.start(lo, nl, lane);
+    Chunk c0 = first_chunk(W, lane);
+    Chunk c1 = next_chunk(c0, W, lane);
+    Chunk c2 = next_chunk(c1, W, lane);
+    issue_rec(R, 0u, c0, nl, lane, X.rec);
+    issue_rec(R, 1u, c1, nl, lane, X.rec);
+    cp_async_commit();
+    cp_async_wait<0>();
+    issue_data<DP>(R, 0u, c0, nl, lane, t, X.stw);
+    cp_async_commit();
+    int dpar = 0;
+    for (uint32_t q = 0; c0.l < nl; ++q) {
+      cp_async_wait<0>();   // chunk q's data and chunk q+1's records
+      __syncwarp();
+      issue_rec(R, q + 2u, c2, nl, lane, X.rec);
+      issue_data<DP>(R, q + 1u, c1, nl, lane, t, X.stw);
+      cp_async_commit();
+      const bool act = in_chunk(c0, nl, lane);
+      XCol<DP> d;
+      read_col<DP>(R, q, c0, lane, act, d);
+      dpar += update_chunk<MT, DP>(act, d, c0.cs + lane, t, alpha, X, lp, lane, my_rescans);
+      __syncwarp();
+      c0 = c1;
+      c1 = c2;
+      c2 = next_chunk(c2, W, lane);
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) dpar += __shfl_xor_sync(kFull, dpar, off);
+    unsat += dpar;
+    ++my_iters;
+    ran = it;
+    if (unsat == 0) { conv = it; break; }
+  }
+  return conv;
+}
+
+// W(e) = sum of lambda_j over e_j = 1, ascending j, of the decisions in dec (every lane folds the same
+// sequence); with bits != NULL the decision words are copied there.
+__device__ __forceinline__ float decision_weight(const Tables& t, const uint32_t* dec, uint32_t* bits, int lane) {
+  const int nw = t.nw;
+  if (bits)
+    for (int w = lane; w < nw; w += 32) bits[w] = __ldcg(dec + w);
+  float W = 0.0f;
+  for (int w = 0; w < nw; ++w) {
+    uint32_t x = __ldcg(dec + w);
+    while (x) {
+      const int bpos = __ffs(x) - 1;
+      W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
+      x &= x - 1;
+    }
+  }
+  return W;
+}
+
 // Decodes shot `shot` of problem t with one warp. base: the warp's shared memory; gs: its global
 // scratch (messages, state words, decisions, posterior, LLR accumulator, candidate records).
 template <typename MT, int DP>
@@ -571,105 +669,14 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
   for (int i = 0; i < K; ++i) {
     const int budget = ncand < M ? T : __shfl_sync(kFull, c_t, M - 1) - 1;
     if (budget <= 0) break;
-    X.rec = t.xrec + (size_t)i * n;
-    X.rmap = t.xrmap + (size_t)i * t.E;
-    // member init: prior summaries with this shot's syndrome (parity = s), prior messages in the
-    // member's schedule order, state words and decisions 0
-    for (int c = lane; c < m; c += 32) {
-      float4 s = __ldg(t.xsum + c);
-      const uint32_t sb = (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u;
-      s.w = __uint_as_float(__float_as_uint(s.w) | (sb ? (kSynBit | kParBit) : 0u));
-      X.S.store(c, s);
-    }
-    for (int j = lane; j < n; j += 32) {
-      const uint2 r = __ldg(X.rec + j);
-      const float x = XMsg<MT>::round(__ldg(t.lam + (r.x & 0xffffffu)));
-      for (uint32_t k = 0; k < (r.x >> 24); ++k) store_msg<MT>(X.msg + r.y + k, x);
-      __stcg(X.stw + j, 0u);
-    }
-    for (int w = lane; w < nw; w += 32) __stcg(X.dec + w, 0u);
-    __syncwarp();
-    const uint32_t* lo = t.lvl_off + (size_t)i * (n + 1);
-    const int nl = __ldg(t.nlev + i);
-    XRing<DP> R{base};
-    const float alpha = __ldg(t.alpha_m + i);   // member i's scaling factor
-    int unsat = nsyn;
-    int conv = 0;
-    for (int it = 1; it <= budget; ++it) {
-      // the posterior is needed after the last possible sweep of a member that may end without
-      // converging (LLR average) and, for soft output, after every sweep
-      float* lp = (a.want_soft || (it == T && ncand == 0)) ? lpost : nullptr;
-      // the sweep in chunks of up to 32 columns of one level, one column per lane, through the ring:
-      // q counts chunks; the records of chunk q+2 and the column data of chunk q+1 are in flight while
-      // chunk q is updated
-      LevelWin W;
-      W.start(lo, nl, lane);
-      Chunk c0 = first_chunk(W, lane);
-      Chunk c1 = next_chunk(c0, W, lane);
-      Chunk c2 = next_chunk(c1, W, lane);
-      issue_rec(R, 0u, c0, nl, lane, X.rec);
-      issue_rec(R, 1u, c1, nl, lane, X.rec);
-      cp_async_commit();
-      cp_async_wait<0>();
-      issue_data<DP>(R, 0u, c0, nl, lane, t, X.stw);
-      cp_async_commit();
-      if (kAhead == 2) {
-        issue_rec(R, 2u, c2, nl, lane, X.rec);
-        cp_async_commit();
-        issue_data<DP>(R, 1u, c1, nl, lane, t, X.stw);
-        cp_async_commit();
-      }
-      int dpar = 0;
-      Chunk c3s = c2;
-      for (uint32_t q = 0; c0.l < nl; ++q) {
-        if (kAhead == 2) {
-          const Chunk c3 = next_chunk(c2, W, lane);
-          cp_async_wait<1>();   // all but chunk q+1's data: chunk q's data and chunk q+2's records
-          __syncwarp();
-          issue_rec(R, q + 3u, c3, nl, lane, X.rec);
-          cp_async_commit();
-          issue_data<DP>(R, q + 2u, c2, nl, lane, t, X.stw);
-          cp_async_commit();
-          c3s = c3;
-        } else {
-          cp_async_wait<0>();   // chunk q's data and chunk q+1's records
-          __syncwarp();
-          issue_rec(R, q + 2u, c2, nl, lane, X.rec);
-          issue_data<DP>(R, q + 1u, c1, nl, lane, t, X.stw);
-          cp_async_commit();
-        }
-        const bool act = in_chunk(c0, nl, lane);
-        XCol<DP> d;
-        read_col<DP>(R, q, c0, lane, act, d);
-        dpar += update_chunk<MT, DP>(act, d, c0.cs + lane, t, alpha, X, lp, lane, my_rescans);
-        __syncwarp();
-        c0 = c1;
-        c1 = c2;
-        c2 = kAhead == 2 ? c3s : next_chunk(c2, W, lane);
-      }
-      cp_async_wait<0>();
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) dpar += __shfl_xor_sync(kFull, dpar, off);
-      unsat += dpar;
-      ++my_iters;
-      if (unsat == 0) { conv = it; break; }
-    }
+    int ran = 0;
+    const int conv = run_member_x<MT, DP>(a, t, i, syn, nsyn, budget, ncand == 0, X, base, lpost, lane, my_iters,
+                                          my_rescans, ran, [](int) { return false; });
     if (conv) {
       // insert (conv, i); i exceeds every member already listed, so it goes after equal iterations
       const int p = __popc(__ballot_sync(kFull, lane < ncand && c_t <= conv));
       const int slot = ncand < M ? ncand : __shfl_sync(kFull, c_slot, M - 1);
-      uint32_t* bits = cand + (size_t)slot * nw;
-      for (int w = lane; w < nw; w += 32) bits[w] = __ldcg(X.dec + w);
-      // W(e) = sum of lambda_j over e_j = 1, ascending j (every lane folds the same sequence)
-      float W = 0.0f;
-      for (int w = 0; w < nw; ++w) {
-        uint32_t x = __ldcg(X.dec + w);
-        while (x) {
-          const int bpos = __ffs(x) - 1;
-          W = __fadd_rn(W, __ldg(t.lam + 32 * w + bpos));
-          x &= x - 1;
-        }
-      }
+      const float W = decision_weight(t, X.dec, cand + (size_t)slot * nw, lane);
       if (a.want_soft) {
         float* dst = cpost + (size_t)slot * n;
         for (int v = lane; v < n; v += 32) dst[v] = lpost[v];
@@ -683,19 +690,7 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
       ncand = min(ncand + 1, M);
     } else if (ncand == 0) {
       // not converged after T sweeps and no candidate yet: add LLR^i / ||LLR^i|| (finite entries)
-      float part = 0.0f;
-      for (int v = lane; v < n; v += 32) {
-        const float x = lpost[v];
-        part = __fadd_rn(part, is_finite_bits(x) ? __fmul_rn(x, x) : 0.0f);
-      }
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) part = __fadd_rn(part, __shfl_xor_sync(kFull, part, off));
-      const float nrm = __fsqrt_rn(part);
-      for (int v = lane; v < n; v += 32) {
-        const float x = lpost[v];
-        const float term = is_finite_bits(x) ? (nrm == 0.0f ? 0.0f : __fdiv_rn(x, nrm)) : x;
-        acc[v] = __fadd_rn(i == 0 ? 0.0f : acc[v], term);
-      }
+      llr_term_add(lpost, acc, n, i == 0, lane);
     }
     __syncwarp();
   }
@@ -753,6 +748,70 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
   __syncwarp();
 }
 
+// Pair mode: member i of shot `shot` (slot `slot` of the chunk) with one warp; the last member of the
+// shot to finish writes the shot's outcome (pair_epilogue, vibe_internal.cuh).
+template <typename MT, int DP>
+__device__ __forceinline__ void decode_pair_x(const BpArgs& a, const Tables& t, uint32_t shot, int slot, int i,
+                                              unsigned char* base, unsigned char* gs, int lane, uint32_t& my_iters,
+                                              uint32_t& my_shots, uint32_t& my_fail, uint32_t& my_rescans) {
+  const int K = t.K, M = t.M, T = t.T, n = t.n, m = t.m, mw = t.mw, nw = t.nw, kw = t.kw;
+  if (i >= K) return;
+  const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
+  int nsyn = 0;
+  for (int w = lane; w < mw; w += 32) {
+    const int rem = m - 32 * w;
+    nsyn += __popc(__ldg(syn + w) & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u)));
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) nsyn += __shfl_xor_sync(kFull, nsyn, off);
+  if (nsyn == 0 && !a.want_soft) {
+    // s = 0: every member converges in iteration 1 to e = 0; member 0 is chosen -- written by member 0
+    if (i != 0) return;
+    ++my_shots;
+    for (int w = lane; w < nw; w += 32) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
+    if (a.logical)
+      for (int w = lane; w < kw; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+    if (a.obs) {
+      uint32_t f = 0;
+      for (int w = lane; w < kw; w += 32) f |= a.obs[(size_t)shot * a.log_stride + w];
+      if (__any_sync(kFull, f) && lane == 0) ++my_fail;
+    }
+    if (a.stats && lane == 0) {
+      vibe_shot_stats st;
+      st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)M; st.chosen_member = 0;
+      st.iters = 1; st.largest_cluster = 0; st.n_clusters = 0;
+      a.stats[shot] = st;
+    }
+    return;
+  }
+  if (i == 0) ++my_shots;
+  XState<MT> X;
+  X.S = sum_io<MT>(base + XRing<DP>::kBytes);
+  X.msg = reinterpret_cast<MT*>(gs + t.xg_msg);
+  X.stw = reinterpret_cast<uint32_t*>(gs + t.xg_st);
+  X.dec = reinterpret_cast<uint32_t*>(gs + t.xg_dec);
+  float* lpost = reinterpret_cast<float*>(gs + t.xg_lpost);
+  int* conv = a.pconv + (size_t)slot * a.pair_K;
+  int ran = 0;
+  const int cv = run_member_x<MT, DP>(a, t, i, syn, nsyn, T, true, X, base, lpost, lane, my_iters, my_rescans, ran,
+                                      [&](int it) { return pair_should_stop(conv, K, M, i, it, lane); });
+  const size_t rec = (size_t)slot * a.pair_K + i;
+  if (cv) {
+    const float W = decision_weight(t, X.dec, a.pbits + rec * a.bnd.nw, lane);
+    if (lane == 0) a.pW[rec] = W;
+    if (a.want_soft)
+      for (int v = lane; v < n; v += 32) a.ppost[rec * a.bnd.n + v] = lpost[v];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile int*>(conv + i) = cv;
+  } else if (ran == T) {
+    llr_term_add(lpost, a.pterms + rec * a.bnd.n, n, true, lane);
+  }
+  __syncwarp();
+  if (pair_finish(a.pdone + slot, K, lane) && pair_epilogue(a, t, shot, slot, lane) && lane == 0) ++my_fail;
+  __syncwarp();
+}
+
 // Blocks (one warp each) per SM the register budget targets.
 constexpr int kMinBlocksX = 16 / kBpxWarpsPerCta;
 
@@ -777,7 +836,42 @@ __global__ void __launch_bounds__(kBpxWarpsPerCta * 32, kMinBlocksX) k_bpx(const
   unsigned char* gs = a.xscratch + gw * a.xscratch_pitch;
   uint32_t my_iters = 0, my_shots = 0, my_fail = 0, my_rescans = 0;   // flushed before they could wrap
 
+  if (a.pair_mode) {
+    const unsigned long long npairs = (unsigned long long)a.nshots * (unsigned long long)a.pair_K;
+    for (;;) {
+      unsigned long long q = 0;
+      if (lane == 0) q = atomicAdd(a.next_pair_x, 1u);
+      q = __shfl_sync(kFull, q, 0);
+      if (q >= npairs) break;
+      const uint32_t shot = (uint32_t)(q / a.pair_K);
+      const int i = (int)(q % a.pair_K);
+      if (MIXED) {
+        const int di = __ldg(a.dem_of_shot + shot);
+        if ((unsigned)di >= (unsigned)a.ndem) {
+          if (i != 0 || !a.flag_bad) continue;
+          for (int w = lane; w < a.corr_stride; w += 32) a.corr[(size_t)shot * a.corr_stride + w] = 0u;
+          if (a.logical)
+            for (int w = lane; w < a.log_stride; w += 32) a.logical[(size_t)shot * a.log_stride + w] = 0u;
+          if (lane == 0) {
+            if (a.stats) {
+              vibe_shot_stats st;
+              st.status = VIBE_STATUS_BAD_PROBLEM; st.lsd_invoked = 0; st.n_converged = 0; st.chosen_member = 0;
+              st.iters = 0; st.largest_cluster = 0; st.n_clusters = 0;
+              a.stats[shot] = st;
+            }
+            if (a.counters) atomicAdd(a.counters + VIBE_CNT_BAD_PROBLEM, 1ull);
+          }
+          continue;
+        }
+        if (sdem[di].engine != VIBE_ENGINE_SUMMARY) continue;   // left to the image engine
+        decode_pair_x<MT, DP>(a, sdem[di], shot, (int)shot, i, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
+      } else {
+        decode_pair_x<MT, DP>(a, a.one, shot, (int)shot, i, base, gs, lane, my_iters, my_shots, my_fail, my_rescans);
+      }
+    }
+  }
   for (;;) {
+    if (a.pair_mode) break;
     if (my_iters > 0x70000000u || my_rescans > 0x70000000u) {
       if (lane == 0 && a.counters) {
         atomicAdd(a.counters + VIBE_CNT_PAIR_ITERS, (unsigned long long)my_iters);

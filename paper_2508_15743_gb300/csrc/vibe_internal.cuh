@@ -87,6 +87,7 @@ struct Bounds {
   long long x_warp_scratch;   // largest summary-engine global scratch per warp, bytes
   int engines;     // bit 0: some problem uses the image engine, bit 1: the summary engine
   int XD;          // largest summary-engine column-degree bound
+  int K;           // largest ensemble size
 };
 
 struct BpArgs {
@@ -123,6 +124,19 @@ struct BpArgs {
   unsigned char* xscratch;
   long long xscratch_pitch;
   unsigned int* next_shot_x;   // the summary engine's own shot counter
+  // pair mode (one warp per (shot, member) pair; see pair_epilogue): when pair_mode is set, pairs
+  // q = shot * pair_K + member are taken from next_pair (image engine) or next_pair_x (summary
+  // engine) and each shot of the chunk has a slot, its index in the chunk
+  int pair_mode;
+  int pair_K;                  // members per shot slot: the largest K of the launch
+  int* pconv;                  // [slot][pair_K] iteration at which the member converged, 0 if not
+  float* pW;                   // [slot][pair_K] weight of a converged member's correction
+  uint32_t* pbits;             // [slot][pair_K][bnd.nw] a converged member's correction
+  float* pterms;               // [slot][pair_K][bnd.n] LLR^i / ||LLR^i|| of a member that ran T sweeps
+  float* ppost;                // [slot][pair_K][bnd.n] a converged member's posterior (soft output), or NULL
+  unsigned int* pdone;         // [slot] members finished
+  unsigned int* next_pair;
+  unsigned int* next_pair_x;
 };
 
 struct LsdArgs {
@@ -150,6 +164,145 @@ struct LsdArgs {
   uint32_t* scratch;
   long long scratch_pitch; // 32-bit words per CTA
 };
+
+// ---- pair mode: one warp per (shot, member) -------------------------------------------------------
+//
+// The members of a shot run at the same time on different warps. Member i stops before iteration t
+// once M members have converged with a smaller (iteration, member) key than (t, i): it can no longer
+// be among the first M candidates of the correction limit (Sec. III.D.2 step 3), the only ones that
+// count. A member that converges records its correction, its weight W and its iteration; a member
+// that runs all T sweeps records LLR^i / ||LLR^i|| (Sec. III.D.2 step 5). The last member of a shot
+// to finish applies the same rule as the one-warp-per-shot driver to the records: the candidates are
+// the first M converged members in (iteration, member) order, the chosen one the first of them with
+// the smallest W; with no candidate, (1/K) times the sum of the recorded terms in member order goes
+// to LSD. The outputs are therefore identical to the other driver's.
+
+// Whether member i must stop before iteration t: at least M members converged with a smaller key.
+__device__ __forceinline__ bool pair_should_stop(const int* conv, int K, int M, int i, int t, int lane) {
+  int cnt = 0;
+  for (int j0 = 0; j0 < K; j0 += 32) {
+    const int j = j0 + lane;
+    const int c = j < K ? *reinterpret_cast<const volatile int*>(conv + j) : 0;
+    cnt += __popc(__ballot_sync(kFull, c > 0 && (c < t || (c == t && j < i))));
+  }
+  return cnt >= M;
+}
+
+// Done-count of a pair's shot; the caller that finishes last (returns true) runs the epilogue. All
+// of the pair's records must be written before the call.
+__device__ __forceinline__ bool pair_finish(unsigned int* done, int K, int lane) {
+  __threadfence();
+  unsigned int old = 0;
+  if (lane == 0) old = atomicAdd(done, 1u);
+  old = __shfl_sync(kFull, old, 0);
+  __threadfence();
+  return old == (unsigned int)(K - 1);
+}
+
+// LLR^i / ||LLR^i||_2 of a posterior (Sec. III.D.2 step 5; finite entries only, the norm's sum of
+// squares in the canonical order: 32 strided partial sums combined at distances 16 .. 1), added to
+// acc[v], which starts from +0 when `first`.
+__device__ inline void llr_term_add(const float* post, float* acc, int n, bool first, int lane) {
+  float part = 0.0f;
+  for (int v = lane; v < n; v += 32) {
+    const float x = post[v];
+    part = __fadd_rn(part, ((__float_as_uint(x) & 0x7f800000u) != 0x7f800000u) ? __fmul_rn(x, x) : 0.0f);
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) part = __fadd_rn(part, __shfl_xor_sync(kFull, part, off));
+  const float nrm = __fsqrt_rn(part);
+  for (int v = lane; v < n; v += 32) {
+    const float x = post[v];
+    const bool fin = (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+    const float term = fin ? (nrm == 0.0f ? 0.0f : __fdiv_rn(x, nrm)) : x;
+    acc[v] = __fadd_rn(first ? 0.0f : acc[v], term);
+  }
+}
+
+// The shot's outcome from its members' records (see above). Returns whether the shot's logical flips
+// differ from the given observables (warp-uniform).
+__device__ inline bool pair_epilogue(const BpArgs& a, const Tables& t, uint32_t shot, int slot, int lane) {
+  const int K = t.K, M = t.M, T = t.T, n = t.n, nw = t.nw, kw = t.kw;
+  const int* conv = a.pconv + (size_t)slot * a.pair_K;
+  const float* Wr = a.pW + (size_t)slot * a.pair_K;
+  // rank of each converged member among the converged ones by (iteration, member); candidates have
+  // rank < M. Lane l examines members l, l + 32, ...
+  int nconv = 0, best = -1, tM = T;
+  float bestW = 0.0f;
+  int best_rank = 1 << 30;
+  for (int j0 = 0; j0 < K; j0 += 32) {
+    const int j = j0 + lane;
+    const int cj = j < K ? __ldcg(conv + j) : 0;
+    int rank = 0;
+    for (int q = 0; q < K; ++q) {
+      const int cq = __ldcg(conv + q);
+      rank += (cq > 0 && (cq < cj || (cq == cj && q < j))) ? 1 : 0;
+    }
+    const bool cand = cj > 0 && rank < M;
+    nconv += __popc(__ballot_sync(kFull, cj > 0));
+    if (cand && rank == M - 1) tM = cj;
+    if (cand) {
+      const float w = __ldcg(Wr + j);
+      if (best < 0 || w < bestW || (w == bestW && rank < best_rank)) { best = j; bestW = w; best_rank = rank; }
+    }
+  }
+  // warp reductions: the first minimum of W over the candidates (by rank), and the M-th iteration
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const int ob = __shfl_xor_sync(kFull, best, off), orank = __shfl_xor_sync(kFull, best_rank, off);
+    const float ow = __shfl_xor_sync(kFull, bestW, off);
+    const int otm = __shfl_xor_sync(kFull, tM, off);
+    if (ob >= 0 && (best < 0 || ow < bestW || (ow == bestW && orank < best_rank))) { best = ob; bestW = ow; best_rank = orank; }
+    tM = min(tM, otm);
+  }
+  const int ncand = min(nconv, M);
+  uint32_t* out_corr = a.corr + (size_t)shot * a.corr_stride;
+  if (ncand > 0) {
+    const uint32_t* bits = a.pbits + ((size_t)slot * a.pair_K + best) * a.bnd.nw;
+    for (int w = lane; w < nw; w += 32) out_corr[w] = __ldcg(bits + w);
+    if (a.want_soft) {
+      const float* src = a.ppost + ((size_t)slot * a.pair_K + best) * a.bnd.n;
+      float* dst = a.soft + (size_t)shot * a.soft_stride;
+      for (int v = lane; v < n; v += 32) dst[v] = __ldcg(src + v);
+    }
+    uint32_t fail = 0;
+    for (int rb = 0; rb < kw; ++rb) {
+      const int r = 32 * rb + lane;
+      uint32_t par = 0;
+      if (r < t.k)
+        for (int e = __ldg(t.lrowptr + r); e < __ldg(t.lrowptr + r + 1); ++e) {
+          const int j = __ldg(t.lcolidx + e);
+          par ^= (__ldcg(bits + (j >> 5)) >> (j & 31)) & 1u;
+        }
+      const uint32_t word = __ballot_sync(kFull, par != 0);
+      if (a.logical && lane == 0) a.logical[(size_t)shot * a.log_stride + rb] = word;
+      if (a.obs) fail |= word ^ a.obs[(size_t)shot * a.log_stride + rb];
+    }
+    if (a.stats && lane == 0) {
+      vibe_shot_stats st;
+      st.status = VIBE_STATUS_OK; st.lsd_invoked = 0; st.n_converged = (uint8_t)ncand;
+      st.chosen_member = (uint8_t)best; st.iters = (uint16_t)(ncand == M ? tM : T);
+      st.largest_cluster = 0; st.n_clusters = 0;
+      a.stats[shot] = st;
+    }
+    return fail != 0u;
+  } else {
+    // (1/K) sum over the members, in index order from +0, of their recorded terms -> LSD
+    uint32_t q = 0;
+    if (lane == 0) q = atomicAdd(a.lsd_count, 1u);
+    q = __shfl_sync(kFull, q, 0);
+    if (lane == 0) a.lsd_shots[q] = shot;
+    float* dst = a.lsd_soft + (size_t)q * a.bnd.n;
+    const float kf = (float)K;
+    const float* terms = a.pterms + (size_t)slot * a.pair_K * a.bnd.n;
+    for (int v = lane; v < n; v += 32) {
+      float acc = 0.0f;
+      for (int i = 0; i < K; ++i) acc = __fadd_rn(acc, __ldcg(terms + (size_t)i * a.bnd.n + v));
+      dst[v] = __fdiv_rn(acc, kf);
+    }
+    return false;   // LSD decides, and counts, this shot
+  }
+}
 
 // A handle's resident problem and launch configuration, as other host files see it (vibe_api.cu).
 struct HandleView {

@@ -45,7 +45,7 @@ class vibe_params(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("M", ctypes.c_int32),
                 ("lsd_order", ctypes.c_int32), ("msg_fp16", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("bp_engine", ctypes.c_int32), ("n_flood", ctypes.c_int32),
-                ("member_alpha", ctypes.c_void_p)]
+                ("member_alpha", ctypes.c_void_p), ("pair_mode", ctypes.c_int32)]
 
 
 ENGINE_AUTO, ENGINE_IMAGE, ENGINE_SUMMARY = 0, 1, 2
@@ -222,7 +222,7 @@ class Decoder:
     """One resident decoding problem: vibe_create at construction, vibe_destroy on close()."""
 
     def __init__(self, dem, K, schedules=None, T=30, alpha=0.625, M=None, lsd_order=0, msg_fp16=False, seed=0,
-                 engine=ENGINE_AUTO, n_flood=0, member_alpha=None):
+                 engine=ENGINE_AUTO, n_flood=0, member_alpha=None, pair_mode=False):
         if M is None:
             M = 1 if K == 1 else min(5, K)
         self.dem = dem
@@ -233,7 +233,8 @@ class Decoder:
         if ma is not None and ma.shape != (K,):
             raise ValueError("member_alpha needs one factor per member")
         self.params = vibe_params(int(T), float(alpha), int(M), int(lsd_order), int(bool(msg_fp16)), int(seed),
-                                  int(engine), int(n_flood), None if ma is None else ma.ctypes.data)
+                                  int(engine), int(n_flood), None if ma is None else ma.ctypes.data,
+                                  int(bool(pair_mode)))
         self.handle = vibe_create(dem.H, dem.L, dem.priors, K, schedules, self.params)
         self.params.member_alpha = None   # vibe_create copied the factors
 

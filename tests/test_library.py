@@ -46,11 +46,11 @@ def test_library_is_sm103a_only():
 
 def _params(V, **kw):
     p = dict(max_iter=20, alpha=0.625, M=1, lsd_order=0, msg_fp16=0, seed=0, bp_engine=0, n_flood=0,
-             member_alpha=None)
+             member_alpha=None, pair_mode=0)
     p.update(kw)
     ma = p["member_alpha"]
     return V.vibe_params(p["max_iter"], p["alpha"], p["M"], p["lsd_order"], p["msg_fp16"], p["seed"],
-                         p["bp_engine"], p["n_flood"], None if ma is None else ma.ctypes.data)
+                         p["bp_engine"], p["n_flood"], None if ma is None else ma.ctypes.data, p["pair_mode"])
 
 
 def _err(V, H, L, priors, K, sched, params):
@@ -88,6 +88,7 @@ def test_host_validation_rejects_bad_input(V):
     assert _err(V, H, L, pr, 1, None, _params(V, msg_fp16=2))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, bp_engine=3))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, bp_engine=-1))[0] == V.VIBE_ERR_INVALID
+    assert _err(V, H, L, pr, 1, None, _params(V, pair_mode=2))[0] == V.VIBE_ERR_INVALID
     # flooding members: 0..K, FP32 messages and the image engine only
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=2))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, msg_fp16=1))[0] == V.VIBE_ERR_UNSUPPORTED
