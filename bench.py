@@ -8,7 +8,7 @@ stream and a 256 MB buffer is written between timed steps to flush L2.
 The JSON line's headline (`value`) is the d=9 colour-code phenomenological workload (9 noisy + 1
 perfect round, p = q = 0.01; m = 300, n = 819; K = 16 seeded schedules, T = 30, M = 5, LSD-0),
 10^6 shots per step, with FP16 messages, end-to-end host-buffer throughput, the CPU oracle timed on
-the host cores, and the FP64-oracle logical error rate beside it. Two more legs ride on the same
+the host cores, and the FP64-oracle logical error rate beside it. Three more legs ride on the same
 line (skip them with --legs none):
 
   circuit_d11   the circuit-level d=11 colour code (11 rounds, Si1000 noise at p = 1e-3; m = 990,
@@ -16,7 +16,11 @@ line (skip them with --legs none):
                 5 with FP32, one timed step of 3648 shots each (twice the persistent grid);
   mixed         colour codes d = 5..15 under circuit-level noise at p in {1, 2, 3, 5} per mille (24
                 problems, 6 graph structures), K = 32, T = 20, FP16, shots of all problems interleaved
-                at random and decoded by one mixed launch replayed from a CUDA graph.
+                at random and decoded by one mixed launch replayed from a CUDA graph;
+  service       the streaming service (Poisson arrivals, 8 GB budget): per-request p50/p99/p99.9
+                latency in shot mode and in pair mode (one warp per (shot, member) pair) for the
+                headline problem at 200,000 requests/s and for the circuit-level d=9 + d=13 mix at
+                2*10^6 requests/s (saturating one GPU) and at 20 requests/s.
 
 Every leg carries a roofline for its kernels (`rooflines`): the BP kernels against the measured HBM
 copy bandwidth in algorithmic bytes (2*E*b per executed sweep plus per-shot I/O), the image
@@ -128,8 +132,10 @@ def measured_peaks():
 
 
 def ler_ci(fails, shots):
+    """Logical error rate with a 2-sigma binomial interval; the variance is floored at 1/shots so that
+    zero failures still give an interval of width (an upper bound of about 2/shots)."""
     p = fails / shots if shots else 0.0
-    sd = (p * (1 - p) / shots) ** 0.5 if shots else 0.0
+    sd = (max(p * (1 - p), 1.0 / shots) / shots) ** 0.5 if shots else 0.0
     return {"ler": p, "two_sigma": [max(0.0, p - 2 * sd), p + 2 * sd], "failures": int(fails), "shots": int(shots)}
 
 
@@ -393,6 +399,34 @@ def mixed_leg(V, dev, peaks, peak_src):
     return leg, []
 
 
+def service_leg(V):
+    """Streaming service (Poisson arrivals, 8 GB device-memory budget), per-request latency in shot mode
+    and in pair mode: the headline problem at 200,000 requests/s; config 5's circuit-level d=9 + d=13
+    mix (K=32, T=50, FP16, LSD-0) at its 2*10^6 requests/s, where one GPU is saturated; and the same mix
+    at 20 requests/s, below what it sustains, where the per-request BP latency shows."""
+    import torch
+    from paper_2508_15743_gb300 import service as S
+    runs = [("pheno_d9_200k", ["pheno_d9"], False, 200_000.0, 400_000),
+            ("circuit_d9_d13_2M", ["circuit_d9", "circuit_d13"], True, 2_000_000.0, 1000),
+            ("circuit_d9_d13_20", ["circuit_d9", "circuit_d13"], True, 20.0, 200)]
+    out = {}
+    for label, names, fp16, rate, count in runs:
+        for pair in (False, True):
+            svc, backend, decs, dems = S.build_service(names, 8 << 30, fp16, 65_536, 2, 0.0005, 5, pair)
+            arrivals, problems, syn, obs = S.make_requests(dems, count, rate, 5)
+            rep, corr, logi, stats = svc.run(arrivals, problems, syn, observables=obs)
+            out[f"{label}_{'pair' if pair else 'shot'}"] = {
+                "mix": names, "fp16": fp16, "rate_hz": rate, "requests": rep.requests,
+                "throughput_per_s": rep.throughput, "latency_ms": rep.latency_ms,
+                "ler": rep.failures / rep.requests, "mean_batch": rep.mean_batch,
+                "max_batch": svc.budget["max_batch"], "device_bytes_used": svc.budget["used_bytes"]}
+            backend.close()
+            for d in decs:
+                d.close()
+            torch.cuda.synchronize()
+    return out
+
+
 def run_case(args):
     """One warm-up and one decode of a named case, for profiling."""
     import torch
@@ -586,7 +620,7 @@ def run_vibe(args):
                                        fp32_inside_two_sigma=bool(ref64["two_sigma"][0] <= line["ler"]["ler"]
                                                                   <= ref64["two_sigma"][1]))
     if rank == 0 and args.legs != "none":
-        legs = args.legs.split(",") if args.legs != "all" else ["circuit_d11", "mixed"]
+        legs = args.legs.split(",") if args.legs != "all" else ["circuit_d11", "mixed", "service"]
         if "circuit_d11" in legs:
             leg, rl = circuit_leg(V, dev, peaks, peak_src, cpu=world == 1 and not args.no_cpu_baseline)
             line["circuit_d11"] = leg
@@ -596,6 +630,8 @@ def run_vibe(args):
             leg, rl = mixed_leg(V, dev, peaks, peak_src)
             line["mixed"] = leg
             line["gpu_launches"] += 3
+        if "service" in legs:
+            line["service"] = service_leg(V)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -612,7 +648,7 @@ def main():
     ap.add_argument("--impl", default="vibe", choices=["vibe", "reference"])
     ap.add_argument("--shots", type=int, default=0, help="override shots per GPU (default: the workload's 10^6)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="all", help="all, none, or a comma list of circuit_d11,mixed")
+    ap.add_argument("--legs", default="all", help="all, none, or a comma list of circuit_d11,mixed,service")
     ap.add_argument("--case", default="", help="run one named profiling case and exit")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -220,14 +220,16 @@ def _problem_specs():
         "codecap_d5": (lambda: D.build_workload("cc666_d5_codecap"), 1, 20, 1, True),
         "pheno_d9": (lambda: D.build_workload("cc666_d9_pheno"), 16, 30, 5, False),
         "circuit_d9": (lambda: C.circuit_dem(9, 9, 0.001, noise="si1000", basis="X"), 32, 50, 5, False),
-        "circuit_d13": (lambda: C.circuit_dem(13, 13, 0.001, noise="si1000", basis="X"), 32, 50, 5, False),
+        "circuit_d13": (lambda: C.circuit_dem(13, 13, 0.001, noise="si1000", basis="X"), 32, 50, 7, False),
     }
 
 
 def build_service(names, budget_bytes: int, fp16: bool, max_batch: int, pipelines: int = 2,
-                  max_wait_s: float = 0.0005, seed: int = 0):
+                  max_wait_s: float = 0.0005, seed: int = 0, pair_mode: bool = False):
     """Creates the resident problems, sizes the micro-batches to the device-memory budget, warms the
-    pipelines up and returns (service, backend, decoders, dems)."""
+    pipelines up and returns (service, backend, decoders, dems). pair_mode decodes each shot's members
+    at the same time on different warps (vibe_params.pair_mode): same outputs, lower latency per
+    request when the GPU is not saturated."""
     import torch
 
     from . import dem as D
@@ -239,7 +241,8 @@ def build_service(names, budget_bytes: int, fp16: bool, max_batch: int, pipeline
         build, K, T, M, natural = specs[name]
         dm = build()
         dems.append(dm)
-        decs.append(V.Decoder(dm, K, D.schedules(dm.n, K, seed + i, natural=natural), T=T, M=M, msg_fp16=fp16))
+        decs.append(V.Decoder(dm, K, D.schedules(dm.n, K, seed + i, natural=natural), T=T, M=M, msg_fp16=fp16,
+                              pair_mode=pair_mode))
     mw = max(d.mw for d in decs)
     nw = max(d.nw for d in decs)
     kw = max(d.kw for d in decs)
@@ -260,9 +263,11 @@ def build_service(names, budget_bytes: int, fp16: bool, max_batch: int, pipeline
     for p in range(pipelines):   # grow every workspace to the batch size before serving
         backend.launch(p, np.zeros(mb, np.int32), np.zeros((mb, mw), np.uint32))
     torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
     svc = StreamingService(backend, capacity=pipelines * mb, max_batch=mb, max_wait_s=max_wait_s)
     svc.budget = dict(budget_bytes=int(budget_bytes), fixed_bytes=int(fixed), per_shot_bytes=int(per_shot),
-                      max_batch=mb, pipelines=pipelines)
+                      max_batch=mb, pipelines=pipelines, used_bytes=int(max(free0 - free2, 0)),
+                      pair_mode=bool(pair_mode))
     return svc, backend, decs, dems
 
 
@@ -298,10 +303,11 @@ def main():
     ap.add_argument("--max-wait-us", type=float, default=500.0)
     ap.add_argument("--pipelines", type=int, default=2)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--pair-mode", action="store_true", help="one warp per (shot, member) pair")
     args = ap.parse_args()
     names = args.mix.split(",")
     svc, backend, decs, dems = build_service(names, int(args.budget_gb * 2**30), args.fp16, args.max_batch,
-                                             args.pipelines, args.max_wait_us * 1e-6, args.seed)
+                                             args.pipelines, args.max_wait_us * 1e-6, args.seed, args.pair_mode)
     arrivals, problems, syn, obs = make_requests(dems, args.requests, args.rate, args.seed)
     rep, corr, logi, stats = svc.run(arrivals, problems, syn, observables=obs)
     rep.extra = dict(mix=names, rate=args.rate, fp16=args.fp16, budget=svc.budget,

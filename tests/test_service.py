@@ -140,11 +140,11 @@ def test_make_requests_is_seeded_and_mixes_problems():
             assert not (syn[rows][:, D.words(dm.m) - 1] >> rem).any()
 
 
-def test_case_runner_binomial_interval():
-    from paper_2508_15743_gb300 import cases
-    r = cases._ler(100, 10_000)
+def test_bench_binomial_interval():
+    import bench
+    r = bench.ler_ci(100, 10_000)
     assert r["ler"] == 0.01 and r["failures"] == 100 and r["shots"] == 10_000
     half = 2 * np.sqrt(0.01 * 0.99 / 10_000)
     assert np.isclose(r["two_sigma"][0], 0.01 - half) and np.isclose(r["two_sigma"][1], 0.01 + half)
-    z = cases._ler(0, 1000)           # no failures: the interval still has width
+    z = bench.ler_ci(0, 1000)           # no failures: the interval still has width
     assert z["two_sigma"][0] == 0.0 and z["two_sigma"][1] > 0.0
