@@ -61,9 +61,9 @@ typedef struct {
   uint64_t seed;     /* seeds the schedules when vibe_create gets schedules == NULL */
   int32_t bp_engine; /* BP kernel: VIBE_ENGINE_AUTO, _IMAGE or _SUMMARY (same results) */
   int32_t n_flood;   /* members 0 .. n_flood-1 use Algorithm 1's parallel (flooding) schedule instead of
-                        a serial one (their schedules are ignored); 0 <= n_flood <= K. Supported on the
-                        image engine with FP32 messages; otherwise vibe_create returns
-                        VIBE_ERR_UNSUPPORTED */
+                        a serial one (their schedules are ignored); 0 <= n_flood <= K. With FP16
+                        storage only the stored variable-to-check messages are rounded. Image engine
+                        only (the summary engine returns VIBE_ERR_UNSUPPORTED) */
   const float* member_alpha; /* NULL, or K host floats in (0, 1] (copied): member i scales its
                         check-to-variable messages by member_alpha[i] instead of alpha, an ensemble
                         mixing heuristics (Sec. V); results, ranking and LLR average are otherwise
@@ -73,13 +73,27 @@ typedef struct {
                         and its BP latency is that of its slowest member, not the sum (latency). The
                         outputs are identical; pair mode does more sweeps in total (members run until
                         they see M earlier candidates) and keeps every member's record per shot */
+  int32_t n_layered; /* members n_flood .. n_flood+n_layered-1 use a layered schedule (Sec. V names
+                        layered schedules between serial and parallel without defining one; read as
+                        row-layered min-sum): the checks are split into layers by greedy colouring in
+                        ascending check order (a check joins the smallest layer holding no earlier
+                        check that shares a column with it); each iteration takes the layers in order,
+                        every check of the layer computes its check-to-variable messages from the
+                        current variable-to-check ones, then every column of those checks recomputes
+                        its variable-to-check messages from its current check-to-variable messages
+                        (zero before a member's first iteration); the posterior follows the last layer.
+                        n_flood + n_layered <= K; schedules of these members are ignored. Image engine
+                        only, FP32 or FP16 storage (only the variable-to-check messages are rounded) */
 } vibe_params;
 
-/* BP engines; both run one warp per shot and give the same bits. IMAGE: the member's whole message
- * image in shared memory; fast for problems whose image is small (code capacity, phenomenological).
- * SUMMARY: an exact 16-byte smallest/second-smallest/holders/sign summary per check in shared memory
- * and the messages in global memory; for circuit-level problems whose image does not fit. AUTO takes
- * IMAGE when at least 8 warps per SM fit, else SUMMARY. */
+/* BP engines; both run one warp per shot (per (shot, member) pair in pair mode) and give the same bits.
+ * IMAGE: the member's whole message image in shared memory; fast for problems whose image is small
+ * (code capacity, phenomenological). SUMMARY: the messages in global memory in schedule order and,
+ * per check, a summary in shared memory (smallest and second-smallest magnitude with their holders, a
+ * lower bound on the other holders' magnitudes, the sign parity; 16 bytes, 8 with FP16 messages); a
+ * check whose summary cannot answer a query exactly is rescanned from the messages
+ * (VIBE_CNT_RESCANS). For circuit-level problems whose image does not fit. AUTO takes IMAGE when at
+ * least 8 warps per SM fit, else SUMMARY. */
 #define VIBE_ENGINE_AUTO 0
 #define VIBE_ENGINE_IMAGE 1
 #define VIBE_ENGINE_SUMMARY 2
@@ -171,6 +185,14 @@ int vibe_get_wavefronts(vibe_handle* h, int32_t member, uint32_t* order_out,
                         uint32_t* level_offsets_out, int32_t* nlevels_out);
 
 /*
+ * vibe_get_layers -- the check layers of the layered schedule as built on the device (n_layered > 0):
+ *   layer_of_check_out (host, m int32, may be NULL) receives each check's layer, *nlayer_out (may be
+ *   NULL) the number of layers. Synchronous.
+ *   Errors: VIBE_ERR_INVALID (NULL handle, or a handle without layered members), VIBE_ERR_CUDA.
+ */
+int vibe_get_layers(vibe_handle* h, int32_t* layer_of_check_out, int32_t* nlayer_out);
+
+/*
  * vibe_profile -- start (enable != 0) or stop recording CUDA events around every kernel that
  * vibe_decode launches on the caller's stream; clears the totals. vibe_profile_read waits for the
  * last recorded event and returns the summed device time (ms) of the BP ensemble kernel and of the
@@ -209,19 +231,41 @@ int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, 
                         uint32_t* d_logical, vibe_shot_stats* d_stats, void* stream);
 
 /*
- * vibe_autotune -- times the decode of a sample batch (d_syndromes: B >= 1 shots, device) on each BP
- * engine the problem fits (VIBE_ENGINE_IMAGE; VIBE_ENGINE_SUMMARY in both of its warp-state layouts,
- * decision bits in shared memory or in global memory) with a few persistent-grid sizes
- * (occupancy maximum, 3/4 and 1/2 of it for BP; maximum and half for LSD) and keeps the fastest
- * engine and sizes for this handle. Decoding results do not depend on the engine or the grid sizes
- * (shots are independent; each shot's arithmetic is fixed), only the time does. Synchronous;
- * allocates a B-shot output buffer for the duration of the call and grows the workspace. Tune a
- * handle before adding it to a vibe_batch: a batch copies the descriptor it sees at creation. The
- * chosen engine and sizes (CTAs per SM) are returned when the pointers are not NULL.
+ * vibe_autotune -- times the decode of a sample batch (d_syndromes: B >= 1 shots, device) and keeps the
+ * fastest launch configuration for this handle. For each BP engine the problem fits
+ * (VIBE_ENGINE_IMAGE, VIBE_ENGINE_SUMMARY) it searches, one knob after the other: pair or shot mode
+ * (one warp per (shot, member) pair, or one warp per shot -- the pair_mode given at creation is only
+ * the starting point), the BP kernel's persistent grid (occupancy maximum, 3/4 and 1/2 CTAs per SM),
+ * and the LSD kernel's CTA size (64, 128 or 256 threads: warps that reduce the columns of different
+ * clusters at the same time) with its grid (maximum and half). Every candidate is timed on a second
+ * decode of the sample, unless its first decode took over twice the best time so far (a mode whose
+ * first candidate fails that way is dropped). Decoding results do not depend on any of these knobs (shots are
+ * independent and each shot's arithmetic is fixed), only the time does. Synchronous; allocates a
+ * B-shot output buffer for the duration of the call and grows the workspace. A vibe_batch copies the
+ * descriptor (engine) it sees at creation and has its own launch: tune it with vibe_batch_autotune.
+ * The choices (engine, BP CTAs per SM, LSD CTAs per SM, LSD threads per CTA) are returned through the
+ * pointers that are not NULL; vibe_get_launch reports the whole launch.
  *   Errors: VIBE_ERR_INVALID, VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
  */
 int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream, int32_t* engine,
-                  int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm);
+                  int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm, int32_t* lsd_threads);
+
+/* Launch configuration of a handle or a batch (vibe_get_launch). */
+typedef struct {
+  int32_t engines;           /* bit 0: the image engine's kernel runs, bit 1: the summary engine's */
+  int32_t pair_mode;         /* 1: one warp per (shot, member) pair; 0: one warp per shot */
+  int32_t bp_blocks_per_sm;  /* image-engine CTAs per SM of its persistent grid (0 if it does not run) */
+  int32_t bpx_blocks_per_sm; /* summary-engine CTAs per SM (0 if it does not run) */
+  int32_t lsd_blocks_per_sm; /* LSD CTAs per SM */
+  int32_t lsd_threads;       /* threads per LSD CTA */
+  int32_t num_sms;           /* the device's SM count (grids are CTAs per SM x this) */
+} vibe_launch;
+
+/*
+ * vibe_get_launch -- the launch configuration of exactly one of h or b (the other NULL) into *out.
+ *   Errors: VIBE_ERR_INVALID.
+ */
+int vibe_get_launch(const vibe_handle* h, const vibe_batch* b, vibe_launch* out);
 
 /*
  * Mixed batches. The paper decodes one detector error model per run; a decoding service often holds
@@ -232,8 +276,9 @@ int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* 
  *
  * vibe_batch_create -- handles[0..count) (1 <= count <= 64, non-NULL, created on the current
  *   device, all with the same msg_fp16) are referenced, not copied: they must outlive the batch and
- *   must not be destroyed first. The batch owns a device copy of their descriptors and its own
- *   workspace (summary-engine problems run the packed state layout in a batch; results are the same). Errors: VIBE_ERR_INVALID (bad count/handles, mixed devices or message precisions,
+ *   must not be destroyed first. The batch owns a device copy of their descriptors (each problem keeps
+ *   its handle's BP engine) and its own launch and workspace; it starts in handles[0]'s shot or pair
+ *   mode with occupancy-maximal grids. Errors: VIBE_ERR_INVALID (bad count/handles, mixed devices or message precisions,
  *   device not current), VIBE_ERR_UNSUPPORTED (the largest problem's state with the batch's
  *   descriptor table does not fit in shared memory), VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
  */
@@ -256,6 +301,17 @@ int vibe_batch_decode(vibe_batch* b, const int32_t* d_problem, const uint32_t* d
                       int64_t B, uint32_t* d_corrections, int32_t corr_stride, uint32_t* d_logical,
                       int32_t log_stride, vibe_shot_stats* d_stats, const uint32_t* d_observables,
                       uint64_t* d_counters, void* stream);
+
+/*
+ * vibe_batch_autotune -- vibe_autotune's launch search (shot or pair mode, the persistent grid of each
+ * BP engine the batch runs, LSD CTA size and grid) for a batch, timed on a sample of mixed shots
+ * (d_problem, d_syndromes, syn_stride as for vibe_batch_decode; B >= 1). Each problem keeps the engine
+ * its handle had when the batch was created. Results do not depend on the choice. Synchronous;
+ * allocates a B-shot output buffer for the duration of the call. Read the choice with vibe_get_launch.
+ *   Errors: VIBE_ERR_INVALID (NULL pointers, B < 1, stride too small), VIBE_ERR_NOMEM, VIBE_ERR_CUDA.
+ */
+int vibe_batch_autotune(vibe_batch* b, const int32_t* d_problem, const uint32_t* d_syndromes, int32_t syn_stride,
+                        int64_t B, void* stream);
 
 /* vibe_batch_destroy -- frees the batch's device memory; the handles stay valid. NULL is accepted. */
 int vibe_batch_destroy(vibe_batch* b);

@@ -80,6 +80,7 @@ struct Launch {
   int device = 0, num_sms = 0;
   int bp_blocks_per_sm = 0, bpx_blocks_per_sm = 0, lsd_blocks_per_sm = 0;
   int pair_mode = 0;                // one warp per (shot, member) pair (vibe_params.pair_mode)
+  int lsd_threads = vibe::kLsdThreads;   // threads per LSD CTA (tuned: 64, 128 or 256)
   bool warp_engine() const { return (bnd.engines & 1) != 0; }
   bool cta_engine() const { return (bnd.engines & 2) != 0; }
   int bp_grid() const { return warp_engine() ? std::max(1, bp_blocks_per_sm * num_sms) : 0; }
@@ -93,20 +94,17 @@ struct Launch {
   long long pair_shot_bytes(bool soft) const {
     return (long long)bnd.K * (8LL + 4LL * bnd.nw + 4LL * bnd.n * (soft ? 2 : 1)) + 4;
   }
-  // pair mode: shots per launch -- enough pairs for two per warp, within kPairBytes of records
-  long long pair_chunk(bool soft) const {
-    const long long warps = (long long)bp_grid() * vibe::kBpWarpsPerCta + (long long)bpx_grid() * vibe::kBpxWarpsPerCta;
-    const long long want = std::max(8LL, (2 * warps + bnd.K - 1) / std::max(1, bnd.K));
-    const long long cap = std::max(1LL, kPairBytes / pair_shot_bytes(soft));
-    return std::min(want, cap);
-  }
-  static constexpr long long kPairBytes = 1LL << 30;
+  // pair mode: shots per launch -- as many as kPairBytes of member records hold, so that a large batch
+  // keeps every warp busy across shots (a launch ends with its slowest pair) and a small one runs whole
+  long long pair_chunk(bool soft) const { return std::max(1LL, kPairBytes / pair_shot_bytes(soft)); }
+  static constexpr long long kPairBytes = 8LL << 30;
 };
 
 // Device memory a decode uses besides its inputs and outputs; grown on demand, reused afterwards.
 struct Workspace {
   long long chunk = 0, chunk_max = 0;
   long long pk_nw = 0, pk_n = 0;   // pair records' sizes per shot the buffers were made for
+  long long lsd_words = 0;         // LSD scratch words per CTA the buffer was made for
   int bp_warps = 0, lsd_ctas = 0;
   long long bpx_bytes = 0;
   unsigned int* ctrl = nullptr;   // [0] next shot (image engine), [1] LSD count, [2] next LSD shot,
@@ -133,7 +131,7 @@ struct Workspace {
     ctrl = nullptr; lsd_shots = nullptr; lsd_soft = nullptr; bp_scratch = nullptr; bpx_scratch = nullptr;
     lsd_scratch = nullptr;
     pconv = nullptr; pW = nullptr; pbits = nullptr; pterms = nullptr; ppost = nullptr; pdone = nullptr;
-    chunk = 0; bp_warps = 0; lsd_ctas = 0; bpx_bytes = 0; pair_shots = 0; pair_soft = false;
+    chunk = 0; bp_warps = 0; lsd_ctas = 0; bpx_bytes = 0; pair_shots = 0; pair_soft = false; lsd_words = 0;
   }
   int ensure(const Launch& L, long long need, bool soft) {
     const long long ps = L.pair_mode ? std::min(need, L.pair_chunk(soft)) : 0;
@@ -142,7 +140,9 @@ struct Workspace {
     const long long xb = (long long)L.bpx_grid() * vibe::kBpxWarpsPerCta * L.bpx_pitch(soft);
     const bool pair_ok = !L.pair_mode || (ps <= pair_shots && (!soft || pair_soft) && L.bnd.K * L.bnd.nw <= pk_nw &&
                                           L.bnd.K * L.bnd.n <= pk_n);
-    if (ctrl && want <= chunk && warps <= bp_warps && L.lsd_grid() <= lsd_ctas && xb <= bpx_bytes && pair_ok)
+    const bool lsd_ok = (long long)L.lsd_grid() * vibe::lsd_scratch_words(L.bnd, L.lsd_threads) <=
+                        (long long)lsd_ctas * lsd_words;
+    if (ctrl && want <= chunk && warps <= bp_warps && lsd_ok && xb <= bpx_bytes && pair_ok)
       return VIBE_OK;
     const long long c = std::max(want, chunk);
     const long long xkeep = std::max(xb, bpx_bytes);
@@ -153,7 +153,9 @@ struct Workspace {
     VIBE_CUDA(dalloc(&lsd_soft, (size_t)c * b.n), "workspace");
     VIBE_CUDA(dalloc(&bp_scratch, (size_t)warps * (size_t)(2 + b.M) * b.n), "workspace");
     VIBE_CUDA(dalloc(&bpx_scratch, (size_t)xkeep), "workspace");
-    VIBE_CUDA(dalloc(&lsd_scratch, (size_t)L.lsd_grid() * (size_t)vibe::lsd_scratch_words(b)), "workspace");
+    VIBE_CUDA(dalloc(&lsd_scratch, (size_t)L.lsd_grid() * (size_t)vibe::lsd_scratch_words(b, L.lsd_threads)),
+              "workspace");
+    lsd_words = vibe::lsd_scratch_words(b, L.lsd_threads);
     if (L.pair_mode) {
       const size_t S = (size_t)ps;
       VIBE_CUDA(dalloc(&pconv, S * b.K), "workspace");
@@ -272,8 +274,8 @@ int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, c
     l.counters = q.counters;
     l.lsd_count = ws.ctrl + 1; l.lsd_shots = ws.lsd_shots; l.lsd_soft = ws.lsd_soft; l.lsd_next = ws.ctrl + 2;
     l.scratch = ws.lsd_scratch;
-    l.scratch_pitch = vibe::lsd_scratch_words(L.bnd);
-    VIBE_CUDA(vibe::launch_lsd(l, L.lsd_grid(), s), "LSD kernel launch");
+    l.scratch_pitch = vibe::lsd_scratch_words(L.bnd, L.lsd_threads);
+    VIBE_CUDA(vibe::launch_lsd(l, L.lsd_grid(), L.lsd_threads, s), "LSD kernel launch");
     if (e2) cudaEventRecord(e2, s);
     prof.bp_launches++;
     prof.lsd_launches++;
@@ -302,7 +304,7 @@ int size_launch(Launch& L) {
   }
   if (vibe::lsd_smem_bytes(L.bnd, L.ndem) > (size_t)optin)
     return fail(VIBE_ERR_UNSUPPORTED, "LSD state of one shot does not fit in shared memory");
-  VIBE_CUDA(vibe::lsd_occupancy(L.bnd, L.ndem, &L.lsd_blocks_per_sm), "LSD occupancy");
+  VIBE_CUDA(vibe::lsd_occupancy(L.bnd, L.ndem, L.lsd_threads, &L.lsd_blocks_per_sm), "LSD occupancy");
   if (L.lsd_blocks_per_sm < 1) return fail(VIBE_ERR_UNSUPPORTED, "the LSD kernel cannot be resident");
   return VIBE_OK;
 }
@@ -332,6 +334,93 @@ Bounds bounds_over(const Tables* ts, int count) {
   return b;
 }
 
+// Searches the launch knobs that leave every result unchanged (shots, and within a shot the members'
+// arithmetic, are fixed; only their placement on the GPU moves) for the fastest decode of the sample q:
+// pair or shot mode (one warp per (shot, member) pair, or one per shot), then each present BP engine's
+// persistent grid (occupancy maximum, 3/4, 1/2 CTAs per SM), then the LSD CTA size (64, 128, 256
+// threads) with its grid (maximum, half). A candidate is timed on a first decode (the workspace grown
+// beforehand) and, unless that took more than twice the best time so far, on a second one, which
+// counts; a mode whose first candidate is rejected that way is dropped. L keeps the fastest; best_ms
+// its time.
+int tune_launch(Launch& L, Workspace& ws, Profiler& prof, const Batch& q, cudaStream_t s, float& best_ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  VIBE_CUDA(cudaEventCreate(&e0), "autotune");
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(cudaGetLastError(), "autotune"); }
+  const Launch base = L;
+  Launch keep = base;
+  float best = 1e30f;
+  int rc = VIBE_OK;
+  auto timed = [&](float& ms) -> int {
+    cudaEventRecord(e0, s);
+    const int r = run_decode(L, ws, prof, q, s);
+    if (r != VIBE_OK) return r;
+    cudaEventRecord(e1, s);
+    VIBE_CUDA(cudaEventSynchronize(e1), "autotune");
+    cudaEventElapsedTime(&ms, e0, e1);
+    return VIBE_OK;
+  };
+  // times the current L; ms = 0 marks a rejected candidate
+  auto time_once = [&](float& ms) -> int {
+    int r = ws.ensure(L, q.B, q.soft != nullptr);
+    if (r != VIBE_OK) return r;
+    float first = 0.f;
+    if ((r = timed(first)) != VIBE_OK) return r;
+    if (first > 2.f * best) { ms = 0.f; return VIBE_OK; }
+    if ((r = timed(ms)) != VIBE_OK) return r;
+    if (ms < best) { best = ms; keep = L; }
+    return VIBE_OK;
+  };
+  // one BP grid knob: the occupancy maximum and two fractions of it; leaves the fastest in cfg.
+  // dropped: the first candidate was rejected
+  auto grid_search = [&](int& cfg, bool& dropped) -> int {
+    const int mx = cfg;
+    const int cand[] = {mx, (mx * 3 + 3) / 4, (mx + 1) / 2};
+    int pick = mx;
+    float pick_ms = 1e30f;
+    dropped = false;
+    for (int i = 0; i < 3; ++i) {
+      if (i > 0 && std::max(1, cand[i]) == std::max(1, cand[i - 1])) continue;
+      cfg = std::max(1, cand[i]);
+      float ms = 0.f;
+      const int r = time_once(ms);
+      if (r != VIBE_OK) return r;
+      if (ms == 0.f && i == 0) { dropped = true; break; }
+      if (ms > 0.f && ms < pick_ms) { pick_ms = ms; pick = cfg; }
+    }
+    cfg = pick;
+    return VIBE_OK;
+  };
+  for (int pm = 1; pm >= 0 && rc == VIBE_OK; --pm) {
+    L = base;
+    L.pair_mode = pm;
+    bool dropped = false;
+    if (L.warp_engine()) rc = grid_search(L.bp_blocks_per_sm, dropped);
+    if (rc == VIBE_OK && !dropped && L.cta_engine()) rc = grid_search(L.bpx_blocks_per_sm, dropped);
+  }
+  const int nts[] = {64, 128, 256};
+  for (int ni = 0; ni < 3 && rc == VIBE_OK; ++ni) {
+    L = keep;
+    L.lsd_threads = nts[ni];
+    int mx = 0;
+    if (vibe::lsd_occupancy(L.bnd, L.ndem, nts[ni], &mx) != cudaSuccess || mx < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const int cand[] = {mx, std::max(1, mx / 2)};
+    for (int i = 0; i < 2 && rc == VIBE_OK; ++i) {
+      if (i > 0 && cand[1] == cand[0]) continue;
+      L.lsd_blocks_per_sm = cand[i];
+      float ms = 0.f;
+      rc = time_once(ms);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L = rc == VIBE_OK ? keep : base;
+  best_ms = best;
+  return rc;
+}
+
 }  // namespace
 
 struct vibe_handle {
@@ -350,6 +439,8 @@ struct vibe_handle {
   void* msg_init = nullptr;
   uint32_t *xcol = nullptr, *xrmap = nullptr;
   uint2* xrec = nullptr;
+  int32_t *layer_ptr = nullptr, *layer_chk = nullptr, *layer_vptr = nullptr, *layer_var = nullptr,
+          *nlayer_d = nullptr;
   float4* xsum = nullptr;
   unsigned long long* tmp_counters = nullptr;
   // host-buffer staging
@@ -371,6 +462,7 @@ struct vibe_handle {
     cudaFree(rowptr); cudaFree(colidx); cudaFree(colptr); cudaFree(rowidx); cudaFree(lrowptr); cudaFree(lcolidx);
     cudaFree(nlev); cudaFree(csc_ent); cudaFree(sched); cudaFree(lvl_off); cudaFree(perm); cudaFree(lam); cudaFree(alpha_m);
     cudaFree(msg_init); cudaFree(xcol); cudaFree(xrec); cudaFree(xrmap); cudaFree(xsum); cudaFree(d_desc);
+    cudaFree(layer_ptr); cudaFree(layer_chk); cudaFree(layer_vptr); cudaFree(layer_var); cudaFree(nlayer_d);
     cudaSetDevice(prev);
   }
 };
@@ -437,10 +529,11 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
     return fail(VIBE_ERR_INVALID, "bp_engine must be VIBE_ENGINE_AUTO, _IMAGE or _SUMMARY");
   if (p->n_flood < 0 || p->n_flood > K) return fail(VIBE_ERR_INVALID, "n_flood must be in 0..K");
   if (p->pair_mode != 0 && p->pair_mode != 1) return fail(VIBE_ERR_INVALID, "pair_mode must be 0 or 1");
-  if (p->n_flood > 0 && p->msg_fp16)
-    return fail(VIBE_ERR_UNSUPPORTED, "flooding members run with FP32 messages only");
-  if (p->n_flood > 0 && p->bp_engine == VIBE_ENGINE_SUMMARY)
-    return fail(VIBE_ERR_UNSUPPORTED, "flooding members run on the image engine only");
+  if (p->n_layered < 0 || p->n_layered > K - p->n_flood)
+    return fail(VIBE_ERR_INVALID, "n_layered must be in 0..K - n_flood");
+  const bool other_schedules = p->n_flood > 0 || p->n_layered > 0;
+  if (other_schedules && p->bp_engine == VIBE_ENGINE_SUMMARY)
+    return fail(VIBE_ERR_UNSUPPORTED, "flooding and layered members run on the image engine only");
   if (p->member_alpha)
     for (int i = 0; i < K; ++i)
       if (!(p->member_alpha[i] > 0.f && p->member_alpha[i] <= 1.f))
@@ -487,6 +580,7 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   t.DP = maxcol <= 4 ? 4 : maxcol <= 8 ? 8 : maxcol <= 16 ? 16 : 32;
   t.mw = (m + 31) / 32; t.nw = (n + 31) / 32; t.kw = (k + 31) / 32; t.W = t.mw;
   t.T = p->max_iter; t.M = p->M; t.lsd_order = p->lsd_order; t.alpha = p->alpha; t.n_flood = p->n_flood;
+  t.n_layered = p->n_layered;
   vibe::bp_warp_smem_bytes(&t, p->msg_fp16);
   t.XD = vibe::bpx_degree_bucket(maxcol);
   t.XP = (t.XD + 3) / 4 * 4;
@@ -503,14 +597,16 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
     t.engine = VIBE_ENGINE_SUMMARY;
     if (vibe::bp_cta_smem_bytes(bw, 0) <= (size_t)optin &&
         vibe::bp_occupancy(bw, 0, p->msg_fp16, &blocks) == cudaSuccess &&
-        (blocks * vibe::kBpWarpsPerCta >= 8 || (p->n_flood > 0 && blocks >= 1) || (t.XD == 0 && blocks >= 1)))
+        (blocks * vibe::kBpWarpsPerCta >= 8 || (other_schedules && blocks >= 1) || (t.XD == 0 && blocks >= 1)))
       t.engine = VIBE_ENGINE_IMAGE;
-    if (p->n_flood > 0 && t.engine != VIBE_ENGINE_IMAGE)
-      return bail(fail(VIBE_ERR_UNSUPPORTED, "flooding members need the image engine; the message image does not fit"));
+    if (other_schedules && t.engine != VIBE_ENGINE_IMAGE)
+      return bail(fail(VIBE_ERR_UNSUPPORTED,
+                       "flooding and layered members need the image engine; the message image does not fit"));
   }
   const int Lnnz = L->rowptr[k];
   const size_t msg_bytes = (size_t)m * t.RP * (p->msg_fp16 ? 2 : 4);
-  const size_t lev_scratch = std::max<size_t>(2 * (size_t)n + E, (size_t)K * ((size_t)m + 3 * (size_t)n + 1));
+  const size_t lev_scratch = std::max<size_t>(std::max<size_t>(2 * (size_t)n + E, 2 * (size_t)m + 2),
+                                              (size_t)K * ((size_t)m + 3 * (size_t)n + 1));
   int32_t* scratch = nullptr;
   cudaStream_t s = nullptr;
 #define VIBE_TRY(call, what) \
@@ -536,6 +632,13 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
   VIBE_TRY(dalloc(&h->xrmap, t.XP ? (size_t)K * E : 0), "tables");
   VIBE_TRY(dalloc(&h->xsum, m), "tables");
   VIBE_TRY(dalloc(&h->d_desc, 1), "tables");
+  if (p->n_layered > 0) {
+    VIBE_TRY(dalloc(&h->layer_ptr, (size_t)m + 1), "tables");
+    VIBE_TRY(dalloc(&h->layer_chk, (size_t)m), "tables");
+    VIBE_TRY(dalloc(&h->layer_vptr, (size_t)m + 1), "tables");
+    VIBE_TRY(dalloc(&h->layer_var, (size_t)E), "tables");
+    VIBE_TRY(dalloc(&h->nlayer_d, 1), "tables");
+  }
   VIBE_TRY(dalloc(&scratch, lev_scratch), "tables");
   VIBE_TRY(dalloc(&h->tmp_counters, VIBE_NUM_COUNTERS), "tables");
   VIBE_TRY(cudaMemcpyAsync(h->rowptr, H->rowptr, sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, s), "upload");
@@ -556,6 +659,14 @@ int vibe_create(const vibe_csr* H, const vibe_csr* L, const double* priors, int3
                               h->colptr, h->rowidx, h->csc_ent, h->msg_init, h->sched, h->lvl_off, h->nlev, h->xcol,
                               h->xrec, h->xrmap, h->xsum, scratch, s),
            "graph builder");
+  if (p->n_layered > 0) {
+    VIBE_TRY(vibe::build_layers(h->rowptr, h->colidx, h->colptr, h->rowidx, m, h->layer_ptr, h->layer_chk,
+                                h->layer_vptr, h->layer_var, h->nlayer_d, scratch, s),
+             "layer builder");
+    VIBE_TRY(cudaMemcpyAsync(&t.nlayer, h->nlayer_d, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "layer builder");
+    VIBE_TRY(cudaStreamSynchronize(s), "layer builder");
+    t.layer_ptr = h->layer_ptr; t.layer_chk = h->layer_chk; t.layer_vptr = h->layer_vptr; t.layer_var = h->layer_var;
+  }
   t.rowptr = h->rowptr; t.colidx = h->colidx; t.colptr = h->colptr; t.rowidx = h->rowidx;
   t.csc_ent = h->csc_ent; t.lam = h->lam; t.alpha_m = h->alpha_m; t.msg_init = h->msg_init; t.sched = h->sched; t.lvl_off = h->lvl_off;
   t.nlev = h->nlev; t.lrowptr = h->lrowptr; t.lcolidx = h->lcolidx;
@@ -652,6 +763,19 @@ int vibe_get_wavefronts(vibe_handle* h, int32_t member, uint32_t* order_out, uin
   return VIBE_OK;
 }
 
+int vibe_get_layers(vibe_handle* h, int32_t* layer_of_check_out, int32_t* nlayer_out) {
+  if (!h || h->t.n_layered < 1) return fail(VIBE_ERR_INVALID, "NULL handle or no layered members");
+  const Tables& t = h->t;
+  if (nlayer_out) *nlayer_out = t.nlayer;
+  if (!layer_of_check_out) return VIBE_OK;
+  std::vector<int32_t> ptr(t.nlayer + 1), chk(t.m);
+  VIBE_CUDA(cudaMemcpy(ptr.data(), h->layer_ptr, sizeof(int32_t) * (t.nlayer + 1), cudaMemcpyDeviceToHost), "layers");
+  VIBE_CUDA(cudaMemcpy(chk.data(), h->layer_chk, sizeof(int32_t) * t.m, cudaMemcpyDeviceToHost), "layers");
+  for (int l = 0; l < t.nlayer; ++l)
+    for (int q = ptr[l]; q < ptr[l + 1]; ++q) layer_of_check_out[chk[q]] = l;
+  return VIBE_OK;
+}
+
 int vibe_profile(vibe_handle* h, int32_t enable) {
   if (!h) return fail(VIBE_ERR_INVALID, "NULL handle");
   h->prof.on = enable != 0;
@@ -686,8 +810,8 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
 // Moves handle h to BP engine `engine` (descriptor on the device, bounds, launch sizes); the handle is
 // unchanged if the engine cannot run this problem.
 static int set_engine(vibe_handle* h, int engine) {
-  if (engine == VIBE_ENGINE_SUMMARY && h->t.n_flood > 0)
-    return fail(VIBE_ERR_UNSUPPORTED, "flooding members run on the image engine only");
+  if (engine == VIBE_ENGINE_SUMMARY && (h->t.n_flood > 0 || h->t.n_layered > 0))
+    return fail(VIBE_ERR_UNSUPPORTED, "flooding and layered members run on the image engine only");
   if (engine == VIBE_ENGINE_SUMMARY && h->t.XD == 0)
     return fail(VIBE_ERR_UNSUPPORTED, "the summary engine takes columns of at most 16 checks");
   Tables t = h->t;
@@ -704,58 +828,52 @@ static int set_engine(vibe_handle* h, int engine) {
 }
 
 int vibe_autotune(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, void* stream, int32_t* engine_out,
-                  int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm) {
+                  int32_t* bp_blocks_per_sm, int32_t* lsd_blocks_per_sm, int32_t* lsd_threads_out) {
   if (!h || !d_syndromes || B < 1) return fail(VIBE_ERR_INVALID, "NULL handle/syndromes or empty sample");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int start_engine = h->t.engine;
+  const Launch start = h->L;
   uint32_t* corr = nullptr;
   VIBE_CUDA(dalloc(&corr, (size_t)B * h->t.nw), "autotune");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_engine = start_engine, best_bp = 0, best_lsd = 0;
   int rc = VIBE_OK;
+  float best = 1e30f;
+  int best_engine = start_engine;
+  Launch best_L = start;
   const int cand_engine[] = {VIBE_ENGINE_IMAGE, VIBE_ENGINE_SUMMARY};
   for (int ci = 0; ci < 2 && rc == VIBE_OK; ++ci) {
-    const int engine = cand_engine[ci];
-    if (set_engine(h, engine) != VIBE_OK) continue;   // the problem does not fit
-    int& bp_cfg = h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm;
-    const int bp_max = bp_cfg, lsd_max = h->L.lsd_blocks_per_sm;
-    const int bp_try[] = {bp_max, (bp_max * 3 + 3) / 4, (bp_max + 1) / 2};
-    const int lsd_try[] = {lsd_max, std::max(1, lsd_max / 2)};
-    for (int bi = 0; bi < 3 && rc == VIBE_OK; ++bi)
-      for (int li = 0; li < 2 && rc == VIBE_OK; ++li) {
-        bp_cfg = std::max(1, bp_try[bi]);
-        h->L.lsd_blocks_per_sm = std::max(1, lsd_try[li]);
-        const Tables& t = h->t;
-        Batch q{nullptr, d_syndromes, t.mw, B, corr, t.nw, nullptr, t.kw, nullptr, nullptr, t.n, nullptr, nullptr};
-        if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;   // warm-up (and workspace)
-        cudaEventRecord(e0, s);
-        if ((rc = run_decode(h->L, h->ws, h->prof, q, s)) != VIBE_OK) break;
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms; best_engine = engine;
-          best_bp = bp_cfg; best_lsd = h->L.lsd_blocks_per_sm;
-        }
-      }
+    h->L = start;
+    if (set_engine(h, cand_engine[ci]) != VIBE_OK) continue;   // the problem does not fit this engine
+    const Tables& t = h->t;
+    Batch q{nullptr, d_syndromes, t.mw, B, corr, t.nw, nullptr, t.kw, nullptr, nullptr, t.n, nullptr, nullptr};
+    float ms = 0.f;
+    if ((rc = tune_launch(h->L, h->ws, h->prof, q, s, ms)) != VIBE_OK) break;
+    if (ms < best) { best = ms; best_engine = cand_engine[ci]; best_L = h->L; }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaFree(corr);
+  h->L = start;
   if (rc != VIBE_OK) {
     set_engine(h, start_engine);
     return rc;
   }
   if ((rc = set_engine(h, best_engine)) != VIBE_OK) return rc;
-  (h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm) = best_bp;
-  h->L.lsd_blocks_per_sm = best_lsd;
+  h->L = best_L;   // same engine, so the same problem descriptor and bounds
   if (engine_out) *engine_out = best_engine;
-  if (bp_blocks_per_sm) *bp_blocks_per_sm = best_bp;
-  if (lsd_blocks_per_sm) *lsd_blocks_per_sm = best_lsd;
+  if (bp_blocks_per_sm) *bp_blocks_per_sm = h->L.warp_engine() ? h->L.bp_blocks_per_sm : h->L.bpx_blocks_per_sm;
+  if (lsd_blocks_per_sm) *lsd_blocks_per_sm = h->L.lsd_blocks_per_sm;
+  if (lsd_threads_out) *lsd_threads_out = h->L.lsd_threads;
+  return VIBE_OK;
+}
+
+int vibe_get_launch(const vibe_handle* h, const vibe_batch* b, vibe_launch* out) {
+  if ((!h) == (!b) || !out) return fail(VIBE_ERR_INVALID, "give exactly one of handle and batch, and an output");
+  const Launch& L = h ? h->L : b->L;
+  out->engines = L.bnd.engines;
+  out->pair_mode = L.pair_mode;
+  out->bp_blocks_per_sm = L.warp_engine() ? L.bp_blocks_per_sm : 0;
+  out->bpx_blocks_per_sm = L.cta_engine() ? L.bpx_blocks_per_sm : 0;
+  out->lsd_blocks_per_sm = L.lsd_blocks_per_sm;
+  out->lsd_threads = L.lsd_threads;
+  out->num_sms = L.num_sms;
   return VIBE_OK;
 }
 
@@ -777,7 +895,6 @@ int vibe_batch_create(vibe_handle* const* handles, int32_t count, vibe_batch** o
     const vibe_handle* h = handles[i];
     if (h->device != h0->device) return fail(VIBE_ERR_INVALID, "handles live on different devices");
     if (h->L.msg_fp16 != h0->L.msg_fp16) return fail(VIBE_ERR_INVALID, "handles mix FP16 and FP32 messages");
-    if (h->L.pair_mode != h0->L.pair_mode) return fail(VIBE_ERR_INVALID, "handles mix pair mode and shot mode");
     desc[i] = h->t;
   }
   const Bounds b = bounds_over(desc.data(), count);
@@ -822,6 +939,21 @@ int vibe_batch_decode(vibe_batch* b, const int32_t* d_problem, const uint32_t* d
   Batch q{d_problem, d_syndromes, syn_stride, B, d_corrections, corr_stride, d_logical, log_stride, d_stats, nullptr,
           b->L.bnd.n, d_observables, reinterpret_cast<unsigned long long*>(d_counters)};
   return run_decode(b->L, b->ws, b->prof, q, static_cast<cudaStream_t>(stream));
+}
+
+int vibe_batch_autotune(vibe_batch* b, const int32_t* d_problem, const uint32_t* d_syndromes, int32_t syn_stride,
+                        int64_t B, void* stream) {
+  if (!b || !d_problem || !d_syndromes || B < 1) return fail(VIBE_ERR_INVALID, "NULL batch/inputs or empty sample");
+  if (B > 0x7fffffffLL) return fail(VIBE_ERR_INVALID, "sample too large");
+  if (syn_stride < b->L.bnd.W) return fail(VIBE_ERR_INVALID, "syndrome stride smaller than the largest problem's words");
+  uint32_t* corr = nullptr;
+  VIBE_CUDA(dalloc(&corr, (size_t)B * b->L.bnd.nw), "autotune");
+  Batch q{d_problem, d_syndromes, syn_stride, B, corr, b->L.bnd.nw, nullptr, b->L.bnd.kw, nullptr, nullptr,
+          b->L.bnd.n, nullptr, nullptr};
+  float ms = 0.f;
+  const int rc = tune_launch(b->L, b->ws, b->prof, q, static_cast<cudaStream_t>(stream), ms);
+  cudaFree(corr);
+  return rc;
 }
 
 int vibe_batch_destroy(vibe_batch* b) {

@@ -44,6 +44,8 @@ struct Msg<float> {
   __device__ __forceinline__ static uint32_t sign(uint32_t sg) { return sg >> 31; }
   __device__ __forceinline__ static void set_inf(float* p) { *p = __int_as_float(0x7f800000); }
   __device__ __forceinline__ static void store(float* p, float x) { *p = x; }
+  __device__ __forceinline__ static float value(float x) { return x; }
+  static constexpr int kSpc = 4;   // slots per 16-byte chunk of a row
 };
 
 template <>
@@ -66,6 +68,8 @@ struct Msg<__half> {
     if (h == 0x8000u) h = 0;
     *reinterpret_cast<unsigned short*>(p) = h;
   }
+  __device__ __forceinline__ static float value(__half x) { return __half2float(x); }
+  static constexpr int kSpc = 8;
 };
 
 __device__ __forceinline__ bool is_finite_bits(float x) {
@@ -222,6 +226,104 @@ __device__ __forceinline__ void flood_sweep(const Tables& t, float alpha, float*
   __syncwarp();
 }
 
+// One iteration of a schedule over check layers, with the check-to-variable messages in their own
+// float image cv (same slot layout as the message image msgs): the layered schedule (the oracle's
+// reading R10; layers from the graph builder) or, with flood set, the parallel schedule as a single
+// layer of all checks (Algorithm 1's other branch, reading R8), which FP16 message storage needs:
+// there the check-to-variable messages of an iteration are float temporaries and only the stored
+// variable-to-check messages are rounded.
+// Per layer, a check pass (lane per check of the layer: smallest and second-smallest magnitude, the
+// slot of the smallest and the sign parity of the row's variable-to-check messages give each edge's
+// minimum and sign product over the other edges, scaled by alpha and signed by the syndrome bit) and a
+// column pass (lane per column of the layer's checks, which share no column: the serial update's
+// exclusion sums over the column's current cv entries, stored as its new variable-to-check messages).
+// Then every posterior (lambda plus the column's cv entries in ascending check order), decision and
+// check parity. cv holds zeros when a layered member starts (init in run_member).
+template <typename MT, int DP>
+__device__ __forceinline__ void layer_sweep(const Tables& t, float alpha, bool flood, MT* msgs, float* cv,
+                                            uint8_t* dec8, const uint8_t* s8, uint8_t* par8, float* lpost,
+                                            int lane) {
+  const int m = t.m, n = t.n;
+  const uint32_t RP = (uint32_t)t.RP;
+  const int nl = flood ? 1 : t.nlayer;
+  for (int l = 0; l < nl; ++l) {
+    const int c0 = flood ? 0 : __ldg(t.layer_ptr + l), c1 = flood ? m : __ldg(t.layer_ptr + l + 1);
+    for (int q = c0 + lane; q < c1; q += 32) {
+      const int c = flood ? q : __ldg(t.layer_chk + q);
+      const int deg = __ldg(t.rowptr + c + 1) - __ldg(t.rowptr + c);
+      const MT* row = msgs + (size_t)c * RP;
+      float* crow = cv + (size_t)c * RP;
+      float m1 = __int_as_float(0x7f800000), m2 = m1;
+      int a1 = -1;
+      uint32_t sx = 0;
+      for (int j = 0; j < deg; ++j) {
+        const float x = Msg<MT>::value(row[row_position((uint32_t)c, (uint32_t)j, (int)RP, Msg<MT>::kSpc)]);
+        const float ax = fabsf(x);
+        sx ^= __float_as_uint(x) >> 31;
+        if (ax < m1) { m2 = m1; m1 = ax; a1 = j; }
+        else if (ax < m2) m2 = ax;
+      }
+      for (int j = 0; j < deg; ++j) {
+        const uint32_t pos = row_position((uint32_t)c, (uint32_t)j, (int)RP, Msg<MT>::kSpc);
+        const float x = Msg<MT>::value(row[pos]);
+        const uint32_t neg = (sx ^ (__float_as_uint(x) >> 31) ^ (uint32_t)s8[c]) & 1u;
+        const float mag = __fmul_rn(alpha, j == a1 ? m2 : m1);
+        crow[pos] = neg ? -mag : mag;
+      }
+    }
+    __syncwarp();
+    const int v0 = flood ? 0 : __ldg(t.layer_vptr + l), v1 = flood ? n : __ldg(t.layer_vptr + l + 1);
+    for (int q = v0 + lane; q < v1; q += 32) {
+      const int v = flood ? q : __ldg(t.layer_var + q);
+      const int deg = __ldg(t.colptr + v + 1) - __ldg(t.colptr + v);
+      uint32_t slot[DP];
+      float c2v[DP];
+#pragma unroll
+      for (int k = 0; k < DP; ++k) {
+        slot[k] = 0u;
+        c2v[k] = 0.0f;
+        if (k < deg) {
+          const uint32_t ent = __ldg(t.csc_ent + (size_t)v * t.DP + k);
+          slot[k] = (ent >> 9) * RP + (ent & 0xffu);
+          c2v[k] = cv[slot[k]];
+        }
+      }
+      float pre = __ldg(t.lam + v);   // lambda + m_0 + ... + m_{k-1}, the shared head of every exclusion sum
+#pragma unroll
+      for (int k = 0; k < DP; ++k) {
+        if (k < deg) {
+          float a = pre;
+#pragma unroll
+          for (int k2 = k + 1; k2 < DP; ++k2)
+            if (k2 < deg) a = __fadd_rn(a, c2v[k2]);
+          Msg<MT>::store(msgs + slot[k], a);
+          pre = __fadd_rn(pre, c2v[k]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  for (int v = lane; v < n; v += 32) {
+    const int deg = __ldg(t.colptr + v + 1) - __ldg(t.colptr + v);
+    float L = __ldg(t.lam + v);
+#pragma unroll
+    for (int k = 0; k < DP; ++k)
+      if (k < deg) {
+        const uint32_t ent = __ldg(t.csc_ent + (size_t)v * t.DP + k);
+        L = __fadd_rn(L, cv[(ent >> 9) * RP + (ent & 0xffu)]);
+      }
+    dec8[v] = L <= 0.0f ? 1u : 0u;
+    if (lpost) lpost[v] = L;
+  }
+  __syncwarp();
+  for (int c = lane; c < m; c += 32) {
+    uint32_t p = s8[c];
+    for (int e = __ldg(t.rowptr + c); e < __ldg(t.rowptr + c + 1); ++e) p ^= dec8[__ldg(t.colidx + e)];
+    par8[c] = (uint8_t)p;
+  }
+  __syncwarp();
+}
+
 // Blocks per SM the register budget targets: FP16 states are small enough for 24 warps per SM,
 // FP32 states (twice the message bytes) fill shared memory at about 16-18.
 template <typename MT>
@@ -262,6 +364,13 @@ __device__ __forceinline__ int run_member(const Tables& t, int i, int budget, bo
     uint32_t* p32 = reinterpret_cast<uint32_t*>(par8);
     for (int q = lane; q < m4; q += 32) p32[q] = s32[q];
   }
+  const bool layered = i >= t.n_flood && i < t.n_flood + t.n_layered;
+  float* cv = t.off_cv >= 0 ? reinterpret_cast<float*>(base + t.off_cv) : nullptr;
+  if (layered) {   // the layered member's check-to-variable messages start at zero
+    uint4* c4 = reinterpret_cast<uint4*>(cv);
+    const int cv_vec = (int)(((size_t)m * t.RP * 4) / 16);
+    for (int q = lane; q < cv_vec; q += 32) c4[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
   __syncwarp();
 
   const uint32_t* sch = t.sched + (size_t)i * n;
@@ -275,14 +384,16 @@ __device__ __forceinline__ int run_member(const Tables& t, int i, int budget, bo
     // the posterior is needed after the last possible sweep of a member that may end without
     // converging (LLR average) and, for soft output, after every sweep
     float* lp = (want_soft || (it == T && keep_last)) ? lpost : nullptr;
-    bool flooded = false;
-    if constexpr (std::is_same<MT, float>::value) {
-      if (i < t.n_flood) {   // parallel schedule (the host allows it with FP32 messages only)
-        flood_sweep<DP>(t, alpha, msgs, dec8, s8, par8, lp, lane);
-        flooded = true;
-      }
+    bool swept = false;   // by a schedule other than the member's serial one
+    if (i < t.n_flood) {   // parallel schedule
+      if constexpr (std::is_same<MT, float>::value) flood_sweep<DP>(t, alpha, msgs, dec8, s8, par8, lp, lane);
+      else layer_sweep<MT, DP>(t, alpha, true, msgs, cv, dec8, s8, par8, lp, lane);
+      swept = true;
+    } else if (layered) {
+      layer_sweep<MT, DP>(t, alpha, false, msgs, cv, dec8, s8, par8, lp, lane);
+      swept = true;
     }
-    for (int l = 0; l < nl && !flooded; ++l) {
+    for (int l = 0; l < nl && !swept; ++l) {
       const uint32_t b = __ldg(lo + l), e = __ldg(lo + l + 1);
       for (uint32_t idx = b + lane; idx < e; idx += 32) {
         const uint32_t ent = __ldg(sch + idx);
@@ -713,6 +824,11 @@ size_t bp_warp_smem_bytes(Tables* t, int msg_fp16) {
   o = align16(o + m4);
   t->off_cand = (int)o;
   o = align16(o + (size_t)t->M * t->nw * 4);
+  t->off_cv = -1;
+  if (t->n_layered > 0 || (t->n_flood > 0 && msg_fp16)) {
+    t->off_cv = (int)o;
+    o = align16(o + (size_t)t->m * t->RP * 4);
+  }
   t->warp_smem = (int)o;
   return o;
 }

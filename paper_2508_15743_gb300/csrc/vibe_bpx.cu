@@ -6,8 +6,10 @@
 // Why a warp per (shot, member). The wavefront levels of a random serial order on these graphs are
 // short: a column conflicts with every column of its ~4 checks (~600 others), so a sweep of the d=11
 // problem has ~1000 levels of ~32 columns. One warp matches that width and synchronises with
-// __syncwarp. Each warp decodes one shot at a time (persistent, shots from a global counter), running
-// the members one after another with the iteration budget of the correction limit (Sec. III.D.2).
+// __syncwarp. In shot mode each warp decodes one shot at a time (persistent, shots from a global
+// counter), running the members one after another with the iteration budget of the correction limit
+// (Sec. III.D.2); in pair mode each warp takes one (shot, member) pair at a time, and the last member
+// of a shot to finish runs the shot's selection and epilogue.
 //
 // Check-node state: a 16-byte summary per check in shared memory.
 //   x, y   the values m1 <= m2 held by up to two "holder" edges of the row (their positions p1, p2
@@ -38,8 +40,9 @@
 // schedule position (bit k: sign of the message to its k-th check; bit 31: decision). Messages are
 // read only by rescans, through a per-member map from each CSR entry of H to its message slot.
 //
-// Pipeline: each lane fetches the column data (schedule record -> checks with row positions, prior,
-// state word) two chunks ahead; none of it is written by the chunks in between.
+// Pipeline: each lane copies the column data (checks with row positions, prior, state word) into a
+// shared-memory ring one chunk ahead of its update, and the schedule records that locate it two
+// chunks ahead; none of it is written by the chunks in between.
 //
 // Arithmetic equals the oracle's bit for bit: same per-node operation order (__fadd_rn/__fmul_rn), min
 // and sign exact, FP16 storage with -0 stored as +0.
@@ -197,8 +200,8 @@ struct Top3 {
   }
 };
 
-// Summary storage of a message type: 12 bytes per check for FP32 messages, 8 for FP16.
-constexpr int kAhead = 1;   // chunks of column data in flight ahead of the update (1 or 2)
+// Chunks of column data in flight ahead of the update (1 or 2); schedule records go one chunk further.
+constexpr int kAhead = 1;
 
 template <typename MT>
 __device__ __forceinline__ SumIO<MT> sum_io(unsigned char* p);

@@ -256,6 +256,74 @@ cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cuda
   return cudaGetLastError();
 }
 
+// Check layers of the layered schedule (the oracle's reading R10): check c, in ascending order,
+// joins the smallest layer that holds no earlier check sharing a column with it. One CTA: the checks
+// are placed one after another (each placement depends on all earlier ones), the threads mark the
+// layers of c's earlier neighbours with the stamp c and find the smallest unmarked one.
+// scratch: layer_of[m] | stamp[m + 1]
+__global__ void k_layers(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                         const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx, int m,
+                         int32_t* layer_ptr, int32_t* layer_chk, int32_t* layer_vptr, int32_t* layer_var,
+                         int32_t* nlayer_out, int32_t* scratch) {
+  int32_t* layer_of = scratch;
+  int32_t* stamp = scratch + m;   // stamp[l] == c: layer l is taken for check c
+  __shared__ int s_nl, s_best;
+  for (int l = threadIdx.x; l <= m; l += blockDim.x) stamp[l] = -1;
+  if (threadIdx.x == 0) { s_nl = 0; s_best = 0x7fffffff; }
+  __syncthreads();
+  for (int c = 0; c < m; ++c) {
+    for (int e = rowptr[c] + threadIdx.x; e < rowptr[c + 1]; e += blockDim.x) {
+      const int v = colidx[e];
+      for (int k = colptr[v]; k < colptr[v + 1]; ++k) {
+        const int c2 = rowidx[k];   // ascending in the column
+        if (c2 >= c) break;
+        stamp[layer_of[c2]] = c;
+      }
+    }
+    __syncthreads();
+    const int nl = s_nl;
+    for (int l = threadIdx.x; l <= nl; l += blockDim.x)   // layer nl is always free
+      if (stamp[l] != c) atomicMin(&s_best, l);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      layer_of[c] = s_best;
+      if (s_best == nl) s_nl = nl + 1;
+      s_best = 0x7fffffff;
+    }
+    __syncthreads();
+  }
+  const int nl = s_nl;
+  // group: counts, offsets, checks ascending within a layer, then each layer's columns
+  if (threadIdx.x == 0) {
+    for (int l = 0; l <= nl; ++l) { layer_ptr[l] = 0; layer_vptr[l] = 0; }
+    for (int c = 0; c < m; ++c) {
+      layer_ptr[layer_of[c] + 1] += 1;
+      layer_vptr[layer_of[c] + 1] += rowptr[c + 1] - rowptr[c];
+    }
+    for (int l = 0; l < nl; ++l) { layer_ptr[l + 1] += layer_ptr[l]; layer_vptr[l + 1] += layer_vptr[l]; }
+    for (int l = 0; l < nl; ++l) stamp[l] = 0;   // fill counters per layer
+    for (int c = 0; c < m; ++c) {
+      const int l = layer_of[c];
+      layer_chk[layer_ptr[l] + stamp[l]++] = c;
+    }
+    // column offset of each check inside layer_var, kept in layer_of (no longer needed as a layer id)
+    for (int l = 0; l < nl; ++l) {
+      int o = layer_vptr[l];
+      for (int q = layer_ptr[l]; q < layer_ptr[l + 1]; ++q) {
+        const int c = layer_chk[q];
+        layer_of[c] = o;
+        o += rowptr[c + 1] - rowptr[c];
+      }
+    }
+    *nlayer_out = nl;
+  }
+  __syncthreads();
+  for (int c = 0; c < m; ++c) {
+    const int o = layer_of[c], b = rowptr[c], d = rowptr[c + 1] - b;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) layer_var[o + j] = colidx[b + j];
+  }
+}
+
 cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m, int n, int K, const uint32_t* d_perm,
                          int RP, int DP, int XP, int msg_fp16, const float* d_lam, int32_t* d_colptr, int32_t* d_rowidx,
                          uint32_t* d_csc_ent, void* d_msg_init, uint32_t* d_sched, uint32_t* d_lvl_off, int32_t* d_nlev,
@@ -290,6 +358,15 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
     k_xrmap<<<grid_for((long long)K * n, 256), 256, 0, s>>>(d_xrec, (long long)K * n, n, E, XP, d_xcol, d_rowptr,
                                                             d_xrmap);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t build_layers(const int32_t* d_rowptr, const int32_t* d_colidx, const int32_t* d_colptr,
+                         const int32_t* d_rowidx, int m, int32_t* d_layer_ptr, int32_t* d_layer_chk,
+                         int32_t* d_layer_vptr, int32_t* d_layer_var, int32_t* d_nlayer, int32_t* d_scratch,
+                         cudaStream_t s) {
+  k_layers<<<1, 256, 0, s>>>(d_rowptr, d_colidx, d_colptr, d_rowidx, m, d_layer_ptr, d_layer_chk, d_layer_vptr,
+                             d_layer_var, d_nlayer, d_scratch);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ namespace vibe {
 
 constexpr int kBpWarpsPerCta = 2;   // image engine: warps per CTA, one shot per warp
 constexpr int kBpxWarpsPerCta = 1;  // summary engine: warps per CTA, one shot per warp
-constexpr int kLsdThreads = 128;    // LSD kernel: threads per CTA, one LSD shot per CTA at a time
+constexpr int kLsdThreads = 128;    // LSD kernel: default threads per CTA (64, 128 or 256), one shot per CTA
 constexpr int kMaxRowDeg = 255;     // position of an edge inside its check row fits in 8 bits
 constexpr int kMaxColDeg = 32;
 constexpr int kMaxDems = 64;        // decoding problems in one mixed launch
@@ -46,8 +46,12 @@ struct Tables {
   int W;         // words of a bit vector over the checks: ceil(m/32)
   int T, M, lsd_order;
   int n_flood;   // members 0 .. n_flood-1 run the parallel (flooding) schedule
+  int n_layered; // members n_flood .. n_flood+n_layered-1 run the layered schedule
+  int nlayer;    // check layers of the layered schedule (0 unless n_layered > 0)
   float alpha;   // the shared factor (alpha_m holds the one each member uses)
   int off_msg, off_dec, off_s, off_par, off_cand, warp_smem;   // image engine: per-warp shared memory, bytes
+  int off_cv;    // image engine: float image of check-to-variable messages (layered members, flooding
+                 // members with FP16 storage), laid out like the message image; -1 when unused
   int engine;    // VIBE_ENGINE_IMAGE or VIBE_ENGINE_SUMMARY
   // summary engine: column-degree bound XD (4, 6, 8 or 16; 0 when a column has more than 16 checks and
   // the engine cannot run the problem), xcol pitch XP, shared memory of one warp (the m check
@@ -68,6 +72,11 @@ struct Tables {
   const int32_t* nlev;     // K level counts
   const int32_t* lrowptr;  // L CSR
   const int32_t* lcolidx;
+  // layered schedule (only when n_layered > 0)
+  const int32_t* layer_ptr;   // nlayer+1 offsets into layer_chk
+  const int32_t* layer_chk;   // m checks grouped by layer, ascending within a layer
+  const int32_t* layer_vptr;  // nlayer+1 offsets into layer_var
+  const int32_t* layer_var;   // E: per layer, the columns of its checks in layer_chk order (each at most once)
   // summary engine
   const uint32_t* xcol;    // n*XP: (check << 8) | position of the edge in the check's CSR row, ascending check
   const uint2* xrec;       // K*n: (sched entry, offset of the column's first message in the member's
@@ -340,6 +349,13 @@ cudaError_t build_tables(const int32_t* d_rowptr, const int32_t* d_colidx, int m
                          uint32_t* d_xcol, uint2* d_xrec, uint32_t* d_xrmap, float4* d_xsum, int32_t* d_scratch,
                          cudaStream_t s);
 cudaError_t seeded_schedules(uint32_t* d_perm, int n, int K, uint64_t seed, cudaStream_t s);
+// Check layers of the layered schedule (greedy colouring in ascending check order) from the CSR and
+// CSC of H: layer_ptr (m+1 entries), layer_chk (m), layer_vptr (m+1), layer_var (E), the layer count in
+// *d_nlayer; scratch: 2*m + 2 ints.
+cudaError_t build_layers(const int32_t* d_rowptr, const int32_t* d_colidx, const int32_t* d_colptr,
+                         const int32_t* d_rowidx, int m, int32_t* d_layer_ptr, int32_t* d_layer_chk,
+                         int32_t* d_layer_vptr, int32_t* d_layer_var, int32_t* d_nlayer, int32_t* d_scratch,
+                         cudaStream_t s);
 
 // K1: persistent BP + ensemble selection (vibe_bp.cu)
 size_t bp_warp_smem_bytes(Tables* t, int msg_fp16);   // fills t's layout fields, returns its size
@@ -360,8 +376,8 @@ cudaError_t bpx_occupancy(const Bounds& b, int ndem, int msg_fp16, int* blocks_p
 // columns and move to the CTA's global scratch above that.
 __host__ __device__ inline bool lsd_cols_in_smem(const Bounds& b) { return b.n <= 6144; }
 size_t lsd_smem_bytes(const Bounds& b, int ndem);
-long long lsd_scratch_words(const Bounds& b);
-cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s);
-cudaError_t lsd_occupancy(const Bounds& b, int ndem, int* blocks_per_sm);
+long long lsd_scratch_words(const Bounds& b, int threads);   // per CTA of `threads` threads
+cudaError_t launch_lsd(const LsdArgs& a, int grid, int threads, cudaStream_t s);
+cudaError_t lsd_occupancy(const Bounds& b, int ndem, int threads, int* blocks_per_sm);
 
 }  // namespace vibe

@@ -17,6 +17,7 @@
 // thread) because it is short (one pick per invalid cluster). Every loop is bounded: at most n + 1
 // rounds (each adds a column), list walks bounded by list lengths.
 #include <algorithm>
+#include <type_traits>
 
 #include "vibe_internal.cuh"
 
@@ -178,10 +179,10 @@ __device__ int merge_clusters(const LsdShared& S, int a, int b, int n) {
   return s;
 }
 
-template <int WP>
-__global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
+template <int WP, int NT>
+__global__ void __launch_bounds__(NT) k_lsd(const LsdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kLsdThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = NT / 32;
   // arrays sized by the launch's bounds; each shot uses the first m / n entries of its problem
   // combination records cover the first 32 * CW columns of a cluster in reliability order
   const int mB = a.bnd.m, nB = a.bnd.n, WB = a.bnd.W, nwB = a.bnd.nw, CWB = min((a.bnd.n + 31) / 32, 32 * WP);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(a.dems);
     uint32_t* dst = reinterpret_cast<uint32_t*>(sdem);
     const int words = a.ndem * (int)(sizeof(Tables) / 4);
-    for (int q = tid; q < words; q += kLsdThreads) dst[q] = __ldg(src + q);
+    for (int q = tid; q < words; q += NT) dst[q] = __ldg(src + q);
   }
   uint32_t* combrow = basis + (size_t)mB * WB;                              // m * CW
   const size_t sort_off = ((size_t)mB * WB + (size_t)mB * CWB + 1) & ~(size_t)1;   // 8-byte aligned
@@ -252,18 +253,18 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     const float* vsoft = a.lsd_soft + (size_t)q * nB;
     const uint32_t* syn = a.syn + (size_t)shot * a.syn_stride;
 
-    for (int j = tid; j < n; j += kLsdThreads) {
+    for (int j = tid; j < n; j += NT) {
       S.key[j] = reliability_key(vsoft[j]);
       S.col_root[j] = -1;
       S.col_next[j] = -1;
       S.pend_next[j] = -1;
     }
-    for (int w = tid; w < W; w += kLsdThreads) {
+    for (int w = tid; w < W; w += NT) {
       const int rem = m - 32 * w;
       S.sbits[w] = __ldg(syn + w) & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
     }
-    for (int w = tid; w < nw; w += kLsdThreads) S.ebits[w] = 0u;
-    for (int c = tid; c < m; c += kLsdThreads) {
+    for (int w = tid; w < nw; w += NT) S.ebits[w] = 0u;
+    for (int c = tid; c < m; c += NT) {
       const bool flipped = (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u;
       S.ck_par[c] = flipped ? c : -1;
       S.valid[c] = 0; S.dirty[c] = 0; S.rank[c] = 0;
@@ -276,11 +277,11 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
 
     for (int round = 0; round <= n + 1; ++round) {
       // A: reset the pick of every invalid cluster
-      for (int c = tid; c < m; c += kLsdThreads)
+      for (int c = tid; c < m; c += NT)
         if (S.ck_par[c] == c && !S.valid[c]) S.best[c] = ~0ull;
       __syncthreads();
       // B: best free column adjacent to each invalid cluster
-      for (int c = tid; c < m; c += kLsdThreads) {
+      for (int c = tid; c < m; c += NT) {
         if (S.ck_par[c] < 0) continue;
         const int r = find_root(S.ck_par, c, m);
         if (S.valid[r]) continue;
@@ -525,9 +526,9 @@ __global__ void __launch_bounds__(kLsdThreads) k_lsd(const LsdArgs a) {
     // outputs
     const bool limit = status == 1 && S.flags[5] != 0;
     const bool solved = status == 1 && !limit;
-    for (int w = tid; w < nw; w += kLsdThreads) a.corr[(size_t)shot * a.corr_stride + w] = solved ? S.ebits[w] : 0u;
+    for (int w = tid; w < nw; w += NT) a.corr[(size_t)shot * a.corr_stride + w] = solved ? S.ebits[w] : 0u;
     if (a.want_soft)
-      for (int j = tid; j < n; j += kLsdThreads) a.soft[(size_t)shot * a.soft_stride + j] = vsoft[j];
+      for (int j = tid; j < n; j += NT) a.soft[(size_t)shot * a.soft_stride + j] = vsoft[j];
     if (warp == 0) {
       uint32_t fail = 0;
       for (int rb = 0; rb < t.kw; ++rb) {
@@ -574,19 +575,39 @@ int lsd_wp(const Bounds& b) {
   return wp;
 }
 
-template <int P>
+template <int P, int NT>
 cudaError_t lsd_launch_one(const LsdArgs& a, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t err = ensure_dyn_smem<k_lsd<P>>(smem);
+  cudaError_t err = ensure_dyn_smem<k_lsd<P, NT>>(smem);
   if (err != cudaSuccess) return err;
-  k_lsd<P><<<grid, kLsdThreads, smem, s>>>(a);
+  k_lsd<P, NT><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int P>
+template <int P, int NT>
 cudaError_t lsd_occupancy_one(size_t smem, int* out) {
-  cudaError_t err = ensure_dyn_smem<k_lsd<P>>(smem);
+  cudaError_t err = ensure_dyn_smem<k_lsd<P, NT>>(smem);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_lsd<P>, kLsdThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_lsd<P, NT>, NT, smem);
+}
+
+template <typename Fn>
+cudaError_t by_wp_nt(int wp, int nt, Fn&& f) {
+  auto with_nt = [&](auto p) -> cudaError_t {
+    switch (nt) {
+      case 64: return f(p, std::integral_constant<int, 64>{});
+      case 128: return f(p, std::integral_constant<int, 128>{});
+      case 256: return f(p, std::integral_constant<int, 256>{});
+      default: return cudaErrorInvalidValue;
+    }
+  };
+  switch (wp) {
+    case 1: return with_nt(std::integral_constant<int, 1>{});
+    case 2: return with_nt(std::integral_constant<int, 2>{});
+    case 4: return with_nt(std::integral_constant<int, 4>{});
+    case 8: return with_nt(std::integral_constant<int, 8>{});
+    case 16: return with_nt(std::integral_constant<int, 16>{});
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -597,36 +618,26 @@ size_t lsd_smem_bytes(const Bounds& b, int ndem) {
          a16(4 * (size_t)b.nw) + a16(32) + 2 * a16(m) + a16((size_t)ndem * sizeof(Tables));
 }
 
-long long lsd_scratch_words(const Bounds& b) {
+long long lsd_scratch_words(const Bounds& b, int threads) {
   const long long CW = std::min<long long>((b.n + 31) / 32, 32LL * lsd_wp(b));
   const long long head = ((long long)b.m * b.W + (long long)b.m * CW + 1) & ~1LL;
-  const long long free_rows = (long long)(kLsdThreads / 32) * (kFreeRows + 1) * CW;
+  const long long free_rows = (long long)(threads / 32) * (kFreeRows + 1) * CW;
   const long long cols = lsd_cols_in_smem(b) ? 0 : 4LL * b.n;
   return (head + 4LL * b.n + free_rows + cols + 2 + 1) & ~1LL;   // even: every CTA's slice stays 8-byte aligned
 }
 
-cudaError_t launch_lsd(const LsdArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_lsd(const LsdArgs& a, int grid, int threads, cudaStream_t s) {
   const size_t smem = lsd_smem_bytes(a.bnd, a.ndem);
-  switch (lsd_wp(a.bnd)) {
-    case 1: return lsd_launch_one<1>(a, grid, smem, s);
-    case 2: return lsd_launch_one<2>(a, grid, smem, s);
-    case 4: return lsd_launch_one<4>(a, grid, smem, s);
-    case 8: return lsd_launch_one<8>(a, grid, smem, s);
-    case 16: return lsd_launch_one<16>(a, grid, smem, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return by_wp_nt(lsd_wp(a.bnd), threads, [&](auto p, auto nt) {
+    return lsd_launch_one<decltype(p)::value, decltype(nt)::value>(a, grid, smem, s);
+  });
 }
 
-cudaError_t lsd_occupancy(const Bounds& b, int ndem, int* blocks_per_sm) {
+cudaError_t lsd_occupancy(const Bounds& b, int ndem, int threads, int* blocks_per_sm) {
   const size_t smem = lsd_smem_bytes(b, ndem);
-  switch (lsd_wp(b)) {
-    case 1: return lsd_occupancy_one<1>(smem, blocks_per_sm);
-    case 2: return lsd_occupancy_one<2>(smem, blocks_per_sm);
-    case 4: return lsd_occupancy_one<4>(smem, blocks_per_sm);
-    case 8: return lsd_occupancy_one<8>(smem, blocks_per_sm);
-    case 16: return lsd_occupancy_one<16>(smem, blocks_per_sm);
-    default: return cudaErrorInvalidValue;
-  }
+  return by_wp_nt(lsd_wp(b), threads, [&](auto p, auto nt) {
+    return lsd_occupancy_one<decltype(p)::value, decltype(nt)::value>(smem, blocks_per_sm);
+  });
 }
 
 }  // namespace vibe

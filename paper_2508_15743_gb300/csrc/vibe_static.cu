@@ -80,7 +80,7 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   const int lsd_grid = v.lsd_grid < v.num_sms ? v.lsd_grid : v.num_sms;
   const size_t ctrl_b = 256;
   const size_t bp_b = up256((size_t)bp_grid * vibe::kBpWarpsPerCta * 2 * (size_t)t.n * sizeof(float));
-  const size_t lsd_b = up256((size_t)lsd_grid * (size_t)vibe::lsd_scratch_words(v.bnd) * sizeof(uint32_t));
+  const size_t lsd_b = up256((size_t)lsd_grid * (size_t)vibe::lsd_scratch_words(v.bnd, vibe::kLsdThreads) * sizeof(uint32_t));
   const size_t fixed = ctrl_b + bp_b + lsd_b;
   const size_t per_shot = (size_t)t.n * sizeof(float) + sizeof(uint32_t);
   const long long max_b = fixed + 512 < kStaticBytes ? (long long)((kStaticBytes - fixed - 512) / per_shot) : 0;
@@ -124,7 +124,7 @@ extern "C" int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, 
   l.obs = nullptr; l.counters = nullptr;
   l.lsd_count = ctrl + 1; l.lsd_shots = lsd_shots; l.lsd_soft = lsd_soft; l.lsd_next = ctrl + 2;
   l.scratch = lsd_scratch;
-  l.scratch_pitch = vibe::lsd_scratch_words(v.bnd);
-  if ((e = vibe::launch_lsd(l, lsd_grid, s)) != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
+  l.scratch_pitch = vibe::lsd_scratch_words(v.bnd, vibe::kLsdThreads);
+  if ((e = vibe::launch_lsd(l, lsd_grid, vibe::kLsdThreads, s)) != cudaSuccess) return vibe::set_error(VIBE_ERR_CUDA, cudaGetErrorString(e));
   return VIBE_OK;
 }

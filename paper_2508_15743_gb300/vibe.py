@@ -45,7 +45,7 @@ class vibe_params(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("M", ctypes.c_int32),
                 ("lsd_order", ctypes.c_int32), ("msg_fp16", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("bp_engine", ctypes.c_int32), ("n_flood", ctypes.c_int32),
-                ("member_alpha", ctypes.c_void_p), ("pair_mode", ctypes.c_int32)]
+                ("member_alpha", ctypes.c_void_p), ("pair_mode", ctypes.c_int32), ("n_layered", ctypes.c_int32)]
 
 
 ENGINE_AUTO, ENGINE_IMAGE, ENGINE_SUMMARY = 0, 1, 2
@@ -67,16 +67,22 @@ def _load():
     lib.vibe_decode_noalloc.restype = ctypes.c_int
     lib.vibe_get_wavefronts.argtypes = [vp, i32, vp, vp, vp]
     lib.vibe_get_wavefronts.restype = ctypes.c_int
+    lib.vibe_get_layers.argtypes = [vp, vp, vp]
+    lib.vibe_get_layers.restype = ctypes.c_int
     lib.vibe_profile.argtypes = [vp, i32]
     lib.vibe_profile.restype = ctypes.c_int
     lib.vibe_profile_read.argtypes = [vp, vp, vp, vp, vp]
     lib.vibe_profile_read.restype = ctypes.c_int
-    lib.vibe_autotune.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+    lib.vibe_autotune.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
     lib.vibe_autotune.restype = ctypes.c_int
     lib.vibe_batch_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
     lib.vibe_batch_create.restype = ctypes.c_int
     lib.vibe_batch_decode.argtypes = [vp, vp, vp, i32, i64, vp, i32, vp, i32, vp, vp, vp, vp]
     lib.vibe_batch_decode.restype = ctypes.c_int
+    lib.vibe_batch_autotune.argtypes = [vp, vp, vp, i32, i64, vp]
+    lib.vibe_batch_autotune.restype = ctypes.c_int
+    lib.vibe_get_launch.argtypes = [vp, vp, vp]
+    lib.vibe_get_launch.restype = ctypes.c_int
     lib.vibe_batch_destroy.argtypes = [vp]
     lib.vibe_batch_destroy.restype = ctypes.c_int
     lib.vibe_destroy.argtypes = [vp]
@@ -170,6 +176,14 @@ def vibe_get_wavefronts(h, member, n):
     return order, offs[:nl.value + 1].copy(), nl.value
 
 
+def vibe_get_layers(h, m):
+    """(layer of each of the m checks as int32 [m], number of layers) of a handle with layered members."""
+    layer = np.zeros(m, np.int32)
+    nl = ctypes.c_int32(0)
+    _check(_lib.vibe_get_layers(h, layer.ctypes.data, ctypes.addressof(nl)))
+    return layer, nl.value
+
+
 def vibe_profile(h, enable):
     _check(_lib.vibe_profile(h, int(bool(enable))))
 
@@ -183,11 +197,11 @@ def vibe_profile_read(h):
 
 
 def vibe_autotune(h, d_syndromes, B, stream=None):
-    """Returns the (engine, BP CTAs per SM, LSD CTAs per SM) the tuner kept for this handle."""
-    eng, bp, lsd = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    """Returns the (engine, BP CTAs per SM, LSD CTAs per SM, LSD threads per CTA) the tuner kept."""
+    eng, bp, lsd, nt = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     _check(_lib.vibe_autotune(h, _ptr(d_syndromes), int(B), _stream_ptr(stream), ctypes.addressof(eng),
-                              ctypes.addressof(bp), ctypes.addressof(lsd)))
-    return eng.value, bp.value, lsd.value
+                              ctypes.addressof(bp), ctypes.addressof(lsd), ctypes.addressof(nt)))
+    return eng.value, bp.value, lsd.value, nt.value
 
 
 def vibe_destroy(h):
@@ -209,6 +223,24 @@ def vibe_batch_decode(b, d_problem, d_syndromes, syn_stride, B, d_corrections, c
                                   _ptr(d_stats), _ptr(d_observables), _ptr(d_counters), _stream_ptr(stream)))
 
 
+def vibe_batch_autotune(b, d_problem, d_syndromes, syn_stride, B, stream=None):
+    _check(_lib.vibe_batch_autotune(b, _ptr(d_problem), _ptr(d_syndromes), int(syn_stride), int(B),
+                                    _stream_ptr(stream)))
+
+
+class vibe_launch(ctypes.Structure):
+    _fields_ = [("engines", ctypes.c_int32), ("pair_mode", ctypes.c_int32), ("bp_blocks_per_sm", ctypes.c_int32),
+                ("bpx_blocks_per_sm", ctypes.c_int32), ("lsd_blocks_per_sm", ctypes.c_int32),
+                ("lsd_threads", ctypes.c_int32), ("num_sms", ctypes.c_int32)]
+
+
+def vibe_get_launch(h=None, b=None):
+    """The launch configuration of a handle or a batch, as a dict."""
+    out = vibe_launch()
+    _check(_lib.vibe_get_launch(h, b, ctypes.byref(out)))
+    return {f: getattr(out, f) for f, _ in vibe_launch._fields_}
+
+
 def vibe_batch_destroy(b):
     if b:
         _check(_lib.vibe_batch_destroy(b))
@@ -222,7 +254,7 @@ class Decoder:
     """One resident decoding problem: vibe_create at construction, vibe_destroy on close()."""
 
     def __init__(self, dem, K, schedules=None, T=30, alpha=0.625, M=None, lsd_order=0, msg_fp16=False, seed=0,
-                 engine=ENGINE_AUTO, n_flood=0, member_alpha=None, pair_mode=False):
+                 engine=ENGINE_AUTO, n_flood=0, member_alpha=None, pair_mode=False, n_layered=0):
         if M is None:
             M = 1 if K == 1 else min(5, K)
         self.dem = dem
@@ -234,7 +266,7 @@ class Decoder:
             raise ValueError("member_alpha needs one factor per member")
         self.params = vibe_params(int(T), float(alpha), int(M), int(lsd_order), int(bool(msg_fp16)), int(seed),
                                   int(engine), int(n_flood), None if ma is None else ma.ctypes.data,
-                                  int(bool(pair_mode)))
+                                  int(bool(pair_mode)), int(n_layered))
         self.handle = vibe_create(dem.H, dem.L, dem.priors, K, schedules, self.params)
         self.params.member_alpha = None   # vibe_create copied the factors
 
@@ -278,6 +310,9 @@ class Decoder:
     def wavefronts(self, member):
         return vibe_get_wavefronts(self.handle, member, self.n)
 
+    def layers(self):
+        return vibe_get_layers(self.handle, self.m)
+
     def profile(self, enable=True):
         vibe_profile(self.handle, enable)
 
@@ -286,6 +321,9 @@ class Decoder:
 
     def autotune(self, syndromes, stream=None):
         return vibe_autotune(self.handle, syndromes, int(syndromes.shape[0]), stream)
+
+    def launch(self):
+        return vibe_get_launch(h=self.handle)
 
 
 class MixedBatch:
@@ -322,6 +360,14 @@ class MixedBatch:
                           out["corrections"].shape[1], out["logical"], out["logical"].shape[1], out["stats"],
                           observables, counters, stream)
         return out
+
+    def autotune(self, problem, syndromes, stream=None):
+        """Times a sample of mixed shots and keeps the fastest launch; returns it (see launch())."""
+        vibe_batch_autotune(self.handle, problem, syndromes, syndromes.shape[1], int(syndromes.shape[0]), stream)
+        return self.launch()
+
+    def launch(self):
+        return vibe_get_launch(b=self.handle)
 
 
 def stats_to_numpy(stats_tensor):

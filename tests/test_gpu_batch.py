@@ -186,8 +186,8 @@ def test_autotune_keeps_results(V):
     s, _ = D.sample(dm, 4000, 9)
     syn_t = torch.from_numpy(s.view(np.int32)).cuda()
     before = dec.decode(syn_t)["corrections"].cpu().numpy()
-    eng, bp, lsd = dec.autotune(syn_t)
-    assert eng in (V.ENGINE_IMAGE, V.ENGINE_SUMMARY) and bp >= 1 and lsd >= 1
+    eng, bp, lsd, nt = dec.autotune(syn_t)
+    assert eng in (V.ENGINE_IMAGE, V.ENGINE_SUMMARY) and bp >= 1 and lsd >= 1 and nt in (64, 128, 256)
     after = dec.decode(syn_t)["corrections"].cpu().numpy()
     assert np.array_equal(before, after)
     dec.close()
@@ -201,12 +201,48 @@ def test_autotune_may_switch_engine_and_keeps_results(V):
     syn_t = torch.from_numpy(s.view(np.int32)).cuda()
     before = dec.decode(syn_t)
     b_corr, b_st = before["corrections"].cpu().numpy(), V.stats_to_numpy(before["stats"])
-    eng, bp, lsd = dec.autotune(syn_t)
-    assert eng in (V.ENGINE_IMAGE, V.ENGINE_SUMMARY)
+    eng, bp, lsd, nt = dec.autotune(syn_t)
+    assert eng in (V.ENGINE_IMAGE, V.ENGINE_SUMMARY) and nt in (64, 128, 256)
     after = dec.decode(syn_t)
     assert np.array_equal(b_corr, after["corrections"].cpu().numpy())
     assert np.array_equal(b_st, V.stats_to_numpy(after["stats"]))
     dec.close()
+
+
+def test_batch_autotune_keeps_results(V):
+    """The batch tuner's launch search (shot/pair mode, BP grids, LSD CTA size and grid) changes the
+    time only: stats, corrections and logical flips are the same before and after it."""
+    probs = [(C.circuit_dem(5, 5, 0.003, noise="si1000", basis="X"), 8, 3, 20, V.ENGINE_SUMMARY),
+             (D.phenomenological_dem(5, 5, 0.02, 0.02), 8, 3, 15, V.ENGINE_IMAGE),
+             (C.circuit_dem(7, 7, 0.002, noise="si1000", basis="X"), 8, 3, 20, V.ENGINE_SUMMARY)]
+    decs = [V.Decoder(dm, K, D.schedules(dm.n, K, 80 + i), T=T, M=M, msg_fp16=True, engine=eng)
+            for i, (dm, K, M, T, eng) in enumerate(probs)]
+    mb = V.MixedBatch(decs)
+    rng = np.random.default_rng(12)
+    B = 2000
+    pid = rng.integers(0, len(probs), B).astype(np.int32)
+    mw = max(d.mw for d in decs)
+    syn = np.zeros((B, mw), np.uint32)
+    for i, (dm, *_r) in enumerate(probs):
+        rows = np.nonzero(pid == i)[0]
+        syn[rows] = pad_words(D.sample(dm, len(rows), 90 + i)[0], mw)
+    pid_t = torch.from_numpy(pid).cuda()
+    syn_t = torch.from_numpy(syn.view(np.int32)).cuda()
+    before = mb.decode(pid_t, syn_t)
+    b = {k: v.cpu().numpy() for k, v in before.items()}
+    start = mb.launch()
+    assert start["engines"] == 3 and start["lsd_threads"] == 128
+    got = mb.autotune(pid_t, syn_t)
+    assert got == mb.launch()
+    assert got["pair_mode"] in (0, 1) and got["lsd_threads"] in (64, 128, 256)
+    assert 1 <= got["bp_blocks_per_sm"] <= start["bp_blocks_per_sm"]
+    assert 1 <= got["bpx_blocks_per_sm"] <= start["bpx_blocks_per_sm"]
+    after = mb.decode(pid_t, syn_t)
+    for k in ("corrections", "logical", "stats"):
+        assert np.array_equal(b[k], after[k].cpu().numpy()), k
+    mb.close()
+    for d in decs:
+        d.close()
 
 
 def test_mixed_batch_in_a_cuda_graph(V):

@@ -46,11 +46,12 @@ def test_library_is_sm103a_only():
 
 def _params(V, **kw):
     p = dict(max_iter=20, alpha=0.625, M=1, lsd_order=0, msg_fp16=0, seed=0, bp_engine=0, n_flood=0,
-             member_alpha=None, pair_mode=0)
+             member_alpha=None, pair_mode=0, n_layered=0)
     p.update(kw)
     ma = p["member_alpha"]
     return V.vibe_params(p["max_iter"], p["alpha"], p["M"], p["lsd_order"], p["msg_fp16"], p["seed"],
-                         p["bp_engine"], p["n_flood"], None if ma is None else ma.ctypes.data, p["pair_mode"])
+                         p["bp_engine"], p["n_flood"], None if ma is None else ma.ctypes.data, p["pair_mode"],
+                         p["n_layered"])
 
 
 def _err(V, H, L, priors, K, sched, params):
@@ -89,10 +90,13 @@ def test_host_validation_rejects_bad_input(V):
     assert _err(V, H, L, pr, 1, None, _params(V, bp_engine=3))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, bp_engine=-1))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, pair_mode=2))[0] == V.VIBE_ERR_INVALID
-    # flooding members: 0..K, FP32 messages and the image engine only
+    # flooding and layered members: n_flood + n_layered <= K, the image engine only
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=2))[0] == V.VIBE_ERR_INVALID
-    assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, msg_fp16=1))[0] == V.VIBE_ERR_UNSUPPORTED
+    assert _err(V, H, L, pr, 1, None, _params(V, n_layered=2))[0] == V.VIBE_ERR_INVALID
+    assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, n_layered=1))[0] == V.VIBE_ERR_INVALID
+    assert _err(V, H, L, pr, 1, None, _params(V, n_layered=-1))[0] == V.VIBE_ERR_INVALID
     assert _err(V, H, L, pr, 1, None, _params(V, n_flood=1, bp_engine=2))[0] == V.VIBE_ERR_UNSUPPORTED
+    assert _err(V, H, L, pr, 1, None, _params(V, n_layered=1, bp_engine=2))[0] == V.VIBE_ERR_UNSUPPORTED
     # per-member scaling factors: one per member (checked by the binding), each in (0, 1] (the library)
     with pytest.raises(ValueError):
         V.Decoder(dm, 2, None, T=5, M=1, member_alpha=np.array([0.5, 0.5, 0.5], np.float32))
@@ -116,6 +120,13 @@ def test_column_degree_limit_is_reported(V):
     L = D.CSR.from_rows([[0]], 34)
     code, msg = _err(V, H, L, np.full(34, 0.1), 1, None, _params(V))
     assert code == V.VIBE_ERR_UNSUPPORTED and "32" in msg
+
+
+def test_get_launch_wants_exactly_one_object(V):
+    import ctypes
+    out = V.vibe_launch()
+    assert V._lib.vibe_get_launch(None, None, ctypes.byref(out)) == V.VIBE_ERR_INVALID
+    assert V._lib.vibe_batch_autotune(None, None, None, 1, 1, None) == V.VIBE_ERR_INVALID
 
 
 def test_decode_rejects_null_handle(V):
