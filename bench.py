@@ -283,7 +283,10 @@ def timed_decode(V, dec, syn_d, obs_d, dev, steps=1):
 
 
 def circuit_leg(V, dev, peaks, peak_src, cpu=True):
-    """Config 3: d=11 circuit-level colour code, K=64, T=50, M=5; FP32/FP16 LSD-0 and FP32 LSD-5."""
+    """Config 3: d=11 circuit-level colour code, K=64, T=50, M=5; FP32 in shot and pair mode, FP16 in pair
+    mode (LSD-0) and FP32 with LSD-5 in pair mode. Pair mode runs a shot's members on separate warps,
+    so a batch of a few shots per warp does not end with warps waiting on a few LSD-bound shots that run
+    all 64 x 50 sweeps one member after another."""
     import torch
     d, K, T, M, B, seed = 11, 64, 50, 5, 3648, 3
     dm = C.circuit_dem(d, d, 1e-3, noise="si1000", basis="X")
@@ -294,19 +297,26 @@ def circuit_leg(V, dev, peaks, peak_src, cpu=True):
     E = dm.H.nnz
     io = io_bytes_per_shot(dm)
     res, rl, outs = {}, [], {}
-    for label, fp16, order in [("f32", False, 0), ("f16", True, 0), ("f32_lsd5", False, 5)]:
-        dec = V.Decoder(dm, K, perms, T=T, M=M, lsd_order=order, msg_fp16=fp16)
+    for label, fp16, order, pair in [("f32", False, 0, True), ("f32_shot_mode", False, 0, False), ("f16", True, 0, True),
+                                     ("f32_lsd5", False, 5, True)]:
+        dec = V.Decoder(dm, K, perms, T=T, M=M, lsd_order=order, msg_fp16=fp16, pair_mode=pair)
         ms, c, prof, out = timed_decode(V, dec, syn_d, obs_d, dev)
         outs[label] = out["corrections"].clone()
         sweeps = int(c[V.CNT_PAIR_ITERS])
         res[label] = {"value": B / (sum(ms) / 1000.0), "ms_per_step": statistics.mean(ms),
                       "ler": ler_ci(int(c[V.CNT_FAILURES]), B), "lsd_fraction": int(c[V.CNT_LSD]) / B,
                       "sweeps_per_shot": sweeps / B, "rescans_per_sweep": int(c[V.CNT_RESCANS]) / max(1, sweeps),
-                      "bp_ms": prof["bp_ms"], "lsd_ms": prof["lsd_ms"]}
+                      "bp_ms": prof["bp_ms"], "lsd_ms": prof["lsd_ms"], "launch": dec.launch(),
+                      "gpu_launches": int(prof["bp_launches"] + prof["lsd_launches"])}
         if order == 0:
-            rl.append(hbm_roofline("k_bpx (summary engine)", "circuit_d11", "f16" if fp16 else "f32", sweeps, E,
-                                   2 if fp16 else 4, B, io, prof["bp_ms"], float(peaks.get("hbm_gbs", 6800.0)),
-                                   peak_src))
+            rl.append(hbm_roofline("k_bpx (summary engine)", "circuit_d11" + ("" if pair else " shot mode"),
+                                   "f16" if fp16 else "f32", sweeps, E, 2 if fp16 else 4, B, io, prof["bp_ms"],
+                                   float(peaks.get("hbm_gbs", 6800.0)), peak_src))
+            # per launch: pair mode decodes the batch in chunks, one BP launch each (same ratio)
+            nl = max(1, prof["bp_launches"])
+            rl[-1]["bytes_per_launch"] = int(rl[-1]["bytes_per_launch"] / nl)
+            rl[-1]["launch_ms"] = rl[-1]["launch_ms"] / nl
+            rl[-1]["launches"] = int(nl)
         rl.append(lsd_roofline("circuit_d11 " + label, int(c[V.CNT_LSD_WORDOPS]), prof["lsd_ms"], int(c[V.CNT_LSD])))
         dec.close()
     res["f16"]["corrections_differ_vs_f32"] = int((outs["f16"] != outs["f32"]).any(dim=1).sum().item()) / B
@@ -314,7 +324,8 @@ def circuit_leg(V, dev, peaks, peak_src, cpu=True):
     res["f16"]["ler_inside_f32_two_sigma"] = bool(f32["two_sigma"][0] <= res["f16"]["ler"]["ler"] <= f32["two_sigma"][1])
     leg = {"workload": f"circuit_d11: colour code d=11, 11 rounds, Si1000 p=1e-3 (X memory), m={dm.m}, n={dm.n}, "
                        f"E={E}; K={K} seeded serial schedules, T={T}, M={M}, alpha=0.625; {B} shots per step "
-                       f"(seed {seed}), one timed step per precision after an all-zero warm-up batch",
+                       f"(seed {seed}), one timed step per row after an all-zero warm-up batch; rows in pair mode "
+                       f"unless named shot mode (same bits)",
            "shots_per_step": B, **res}
     if cpu:
         import oracle
@@ -361,8 +372,6 @@ def mixed_leg(V, dev, peaks, peak_src):
     syn_d = torch.from_numpy(syn.view(np.int32)).to(dev)
     obs_d = torch.from_numpy(obs.view(np.int32)).to(dev)
     cnt = torch.zeros(8, dtype=torch.int64, device=dev)
-    out = mb.decode(pid_d, torch.zeros_like(syn_d), observables=obs_d, counters=cnt)   # workspace, modules
-    torch.cuda.synchronize()
     # launch search on a disjoint sample (shot/pair mode, BP grids, LSD CTA size and grid)
     tpid = np.ascontiguousarray(pid[: B // 8])
     tsyn = np.zeros((len(tpid), mb.mw), np.uint32)
@@ -373,6 +382,8 @@ def mixed_leg(V, dev, peaks, peak_src):
     start_launch = mb.launch()
     tuned = mb.autotune(torch.from_numpy(tpid).to(dev), torch.from_numpy(tsyn.view(np.int32)).to(dev))
     tune_s = time.time() - t0
+    # the chosen launch's workspace for the full batch and its kernels, before the capture
+    out = mb.decode(pid_d, torch.zeros_like(syn_d), observables=obs_d, counters=cnt)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream(dev)
@@ -451,25 +462,43 @@ def run_case(args):
         "circuit_d11_k16": (lambda: C.circuit_dem(11, 11, 1e-3, noise="si1000", basis="X"), 16, 50, 5, False, 1824, 3),
         "circuit_d11_k16_fp16": (lambda: C.circuit_dem(11, 11, 1e-3, noise="si1000", basis="X"), 16, 50, 5, True, 2432,
                                  3),
+        # short members (at most 4 x 10 sweeps per shot) and one shot per resident warp: a launch of
+        # well under a second for full-section profiler captures
+        "circuit_d11_k4_t10": (lambda: C.circuit_dem(11, 11, 1e-3, noise="si1000", basis="X"), 4, 10, 2, False, 1824,
+                               3),
+        # the XYZ colour-code circuit (each ancilla cycles X, Y, Z plaquette measurements), d=5 and 7
+        "xyz_d5": (lambda: C.circuit_dem(5, 7, 1e-3, noise="si1000", basis="X", schedule="xyz"), 16, 30, 5, False,
+                   100_000, 5),
+        "xyz_d7": (lambda: C.circuit_dem(7, 7, 1e-3, noise="si1000", basis="X", schedule="xyz"), 16, 30, 5, False,
+                   30_000, 7),
+        # the X/Z circuit with the same sizes, rounds, noise and decoder, for comparison
+        "xz_d5": (lambda: C.circuit_dem(5, 7, 1e-3, noise="si1000", basis="X"), 16, 30, 5, False, 100_000, 5),
+        "xz_d7": (lambda: C.circuit_dem(7, 7, 1e-3, noise="si1000", basis="X"), 16, 30, 5, False, 30_000, 7),
     }
     build, K, T, M, fp16, shots, seed = cases[args.case]
     dm = build()
     B = args.shots or shots
-    dec = V.Decoder(dm, K, D.schedules(dm.n, K, seed), T=T, M=M, msg_fp16=fp16)
+    dec = V.Decoder(dm, K, D.schedules(dm.n, K, seed), T=T, M=M, msg_fp16=fp16, pair_mode=args.pair_mode)
     syn, obs = D.sample(dm, B, seed)
     syn_t = torch.from_numpy(syn.view(np.int32)).cuda()
     dec.decode(syn_t[:64])
     torch.cuda.synchronize()
     cnt = torch.zeros(V.VIBE_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    obs_t = torch.from_numpy(obs.view(np.int32)).cuda()
     dec.profile(True)
-    dec.decode(syn_t, counters=cnt)
+    dec.decode(syn_t, observables=obs_t, counters=cnt)
     torch.cuda.synchronize()
     prof = dec.profile_read()
     c = cnt.cpu().numpy()
+    engine = {V.ENGINE_IMAGE: "image", V.ENGINE_SUMMARY: "summary"}
+    launch = dec.launch()
     dec.close()
     print(json.dumps(dict(case=args.case, shots=int(c[V.CNT_SHOTS]), sweeps=int(c[V.CNT_PAIR_ITERS]),
                           lsd=int(c[V.CNT_LSD]), rescans=int(c[V.CNT_RESCANS]), lsd_wordops=int(c[V.CNT_LSD_WORDOPS]),
-                          bp_ms=prof["bp_ms"], lsd_ms=prof["lsd_ms"], n=dm.n, m=dm.m, E=int(dm.H.nnz))))
+                          bp_ms=prof["bp_ms"], lsd_ms=prof["lsd_ms"], n=dm.n, m=dm.m, E=int(dm.H.nnz),
+                          shots_per_s=B / ((prof["bp_ms"] + prof["lsd_ms"]) / 1000.0),
+                          ler=ler_ci(int(c[V.CNT_FAILURES]), B), launch=launch,
+                          engine=engine[1 if launch["engines"] == 1 else 2])))
     return 0
 
 
@@ -655,11 +684,9 @@ def run_vibe(args):
             leg, rl = circuit_leg(V, dev, peaks, peak_src, cpu=world == 1 and not args.no_cpu_baseline)
             line["circuit_d11"] = leg
             line["rooflines"] += rl
-            line["gpu_launches"] += 6
         if "mixed" in legs:
             leg, rl = mixed_leg(V, dev, peaks, peak_src)
             line["mixed"] = leg
-            line["gpu_launches"] += 3
         if "service" in legs:
             line["service"] = service_leg(V)
     if rank == 0:
@@ -680,6 +707,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="all", help="all, none, or a comma list of circuit_d11,mixed,service")
     ap.add_argument("--case", default="", help="run one named profiling case and exit")
+    ap.add_argument("--pair-mode", action="store_true", help="--case: one warp per (shot, member) pair")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -225,7 +225,9 @@ int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp
  *   clears the counters it needs). Calls whose work overlaps on the GPU -- on different streams or
  *   from different threads without ordering -- race on it and must be serialised by the caller.
  *   Errors: VIBE_ERR_INVALID (NULL handle/pointers, B < 0, handle's device not current),
- *   VIBE_ERR_UNSUPPORTED (batch too large), VIBE_ERR_CUDA. B = 0 performs only the set-up above.
+ *   VIBE_ERR_UNSUPPORTED (batch too large, or a handle on the summary engine, whose per-warp message
+ *   arrays leave no useful grid in 64 MiB), VIBE_ERR_CUDA. B = 0 performs only the set-up above.
+ *   Always runs one warp per shot, whatever the handle's pair_mode (same results).
  */
 int vibe_decode_noalloc(vibe_handle* h, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
                         uint32_t* d_logical, vibe_shot_stats* d_stats, void* stream);

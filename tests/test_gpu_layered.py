@@ -33,13 +33,15 @@ def problems():
         "pheno_d9": D.build_workload("cc666_d9_pheno"),
         "pheno_d5": D.phenomenological_dem(5, 5, 0.02, 0.02),
         "circuit_d5": C.circuit_dem(5, 5, 0.003, noise="si1000", basis="X"),
+        "circuit_d3": C.circuit_dem(3, 3, 0.004, noise="si1000", basis="X"),
     }
 
 
 @pytest.mark.parametrize("name", ["codecap_d5", "pheno_d9", "circuit_d5"])
 def test_device_layers_equal_the_oracle(V, name):
     dm = problems()[name]
-    dec = V.Decoder(dm, 2, D.schedules(dm.n, 2, 1), T=5, M=1, n_layered=1, engine=V.ENGINE_IMAGE)
+    # FP16 storage: the d=5 circuit's rows of up to ~170 entries need it for the image to fit
+    dec = V.Decoder(dm, 2, D.schedules(dm.n, 2, 1), T=5, M=1, n_layered=1, engine=V.ENGINE_IMAGE, msg_fp16=True)
     got, nl = dec.layers()
     ref, rnl = oracle.check_layers(dm)
     assert nl == rnl
@@ -72,7 +74,7 @@ def run_both(V, dm, K, M, T, n_flood, n_layered, fp16, shots, seed, pair=False, 
     ("codecap_d5", 3000, 1, 1, 20, 0, 1),
     ("pheno_d9", 1200, 8, 3, 30, 2, 3),
     ("pheno_d5", 2000, 6, 3, 15, 0, 6),
-    ("circuit_d5", 300, 4, 2, 20, 1, 2),
+    ("circuit_d3", 900, 6, 2, 20, 1, 3),
 ])
 def test_layered_members_match_oracle(V, fp16, name, shots, K, M, T, n_flood, n_layered):
     st = run_both(V, problems()[name], K, M, T, n_flood, n_layered, fp16, shots, 40)
