@@ -8,15 +8,18 @@ stream and a 256 MB buffer is written between timed steps to flush L2.
 The JSON line's headline (`value`) is the d=9 colour-code phenomenological workload (9 noisy + 1
 perfect round, p = q = 0.01; m = 300, n = 819; K = 16 seeded schedules, T = 30, M = 5, LSD-0),
 10^6 shots per step, with FP16 messages, end-to-end host-buffer throughput, the CPU oracle timed on
-the host cores, and the FP64-oracle logical error rate beside it. Three more legs ride on the same
+the host cores, and the FP64-oracle logical error rate beside it (the launch vibe_create sizes;
+--tune runs the launch search first). Three more legs ride on the same
 line (skip them with --legs none):
 
   circuit_d11   the circuit-level d=11 colour code (11 rounds, Si1000 noise at p = 1e-3; m = 990,
-                n = 32422): K = 64, T = 50, M = 5, LSD-0 with FP32 and FP16 messages and LSD order
-                5 with FP32, one timed step of 3648 shots each (twice the persistent grid);
+                n = 32422): K = 64, T = 50, M = 5; LSD-0 with FP32 messages in pair mode and in shot
+                mode, with FP16 messages in pair mode, and LSD order 5 with FP32 in pair mode; one timed
+                step of 3648 shots each;
   mixed         colour codes d = 5..15 under circuit-level noise at p in {1, 2, 3, 5} per mille (24
                 problems, 6 graph structures), K = 32, T = 20, FP16, shots of all problems interleaved
-                at random and decoded by one mixed launch replayed from a CUDA graph;
+                at random; the batch's launch is tuned on a 96-shot sample, then one mixed decode is
+                captured in a CUDA graph and replayed;
   service       the streaming service (Poisson arrivals, 8 GB budget): per-request p50/p99/p99.9
                 latency in shot mode and in pair mode (one warp per (shot, member) pair) for the
                 headline problem at 200,000 requests/s and for the circuit-level d=9 + d=13 mix at
@@ -57,6 +60,23 @@ SM_COUNT_NOMINAL = 152
 SM_CLOCK_GHZ = 2.07          # maximum SM clock of the part (the recipe's figure)
 SMEM_BYTES_PER_CLK = 128     # shared-memory bandwidth per SM and clock (32 banks x 4 bytes)
 INT_OPS_PER_CLK = 128        # 32-bit integer lanes per SM and clock
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu capture of each BP kernel with
+# FP32 messages, per unit of work, for the rooflines' `traffic`: the image engine per shot (its DRAM
+# traffic is the per-shot I/O and LSD hand-off), the summary engine per executed sweep (its messages,
+# tables and rescans). Scaled to a launch by the units it processed; the captures and their commands
+# are in profiles/.
+PROFILED_TRAFFIC = {
+    "k_bp": {"per": "shot", "bytes": 4737024 / 20000, "profile": "profiles/k_bp_cc666_d9_pheno_full.md"},
+    "k_bpx": {"per": "sweep", "bytes": 615048462000 / 61857, "profile": "profiles/k_bpx_circuit_d11_k4_t10_full.md"},
+}
+
+
+def profiled_traffic(kernel, precision, shots, sweeps):
+    """DRAM bytes per launch from the capture of `kernel` (FP32 only), or None."""
+    rec = PROFILED_TRAFFIC.get(kernel)
+    if precision != "f32" or rec is None or rec["bytes"] is None:
+        return None
+    return int(rec["bytes"] * (shots if rec["per"] == "shot" else sweeps))
 
 
 def dist_env():
@@ -311,10 +331,13 @@ def circuit_leg(V, dev, peaks, peak_src, cpu=True):
         if order == 0:
             rl.append(hbm_roofline("k_bpx (summary engine)", "circuit_d11" + ("" if pair else " shot mode"),
                                    "f16" if fp16 else "f32", sweeps, E, 2 if fp16 else 4, B, io, prof["bp_ms"],
-                                   float(peaks.get("hbm_gbs", 6800.0)), peak_src))
+                                   float(peaks.get("hbm_gbs", 6800.0)), peak_src,
+                                   traffic=profiled_traffic("k_bpx", "f16" if fp16 else "f32", B, sweeps)))
             # per launch: pair mode decodes the batch in chunks, one BP launch each (same ratio)
             nl = max(1, prof["bp_launches"])
             rl[-1]["bytes_per_launch"] = int(rl[-1]["bytes_per_launch"] / nl)
+            if rl[-1]["traffic"] is not None:
+                rl[-1]["traffic"] = int(rl[-1]["traffic"] / nl)
             rl[-1]["launch_ms"] = rl[-1]["launch_ms"] / nl
             rl[-1]["launches"] = int(nl)
         rl.append(lsd_roofline("circuit_d11 " + label, int(c[V.CNT_LSD_WORDOPS]), prof["lsd_ms"], int(c[V.CNT_LSD])))
@@ -373,7 +396,7 @@ def mixed_leg(V, dev, peaks, peak_src):
     obs_d = torch.from_numpy(obs.view(np.int32)).to(dev)
     cnt = torch.zeros(8, dtype=torch.int64, device=dev)
     # launch search on a disjoint sample (shot/pair mode, BP grids, LSD CTA size and grid)
-    tpid = np.ascontiguousarray(pid[: B // 8])
+    tpid = np.ascontiguousarray(pid[:96])
     tsyn = np.zeros((len(tpid), mb.mw), np.uint32)
     for i, dm in enumerate(dems):
         rows = np.nonzero(tpid == i)[0]
@@ -540,13 +563,18 @@ def run_vibe(args):
     results = {}
     for label, fp16 in [("f32", False), ("f16", True)]:
         dec = V.Decoder(dm, w["K"], perms, T=w["T"], alpha=w["alpha"], M=w["M"], msg_fp16=fp16)
-        # launch search on a disjoint 32768-shot sample before warm-up
-        tsyn = torch.from_numpy(D.sample(dm, 32768, w["seed"] + 777 + 1000 * rank)[0].view(np.int32)).to(dev)
-        t0 = time.time()
-        tuned = dec.autotune(tsyn)
-        tune = {"sample_shots": 32768, "seconds": time.time() - t0, "chosen": dec.launch(),
-                "engine": {V.ENGINE_IMAGE: "image", V.ENGINE_SUMMARY: "summary"}[tuned[0]]}
-        del tsyn
+        # the launch vibe_create sizes (occupancy-maximal grid, one warp per shot); --tune runs the
+        # launch search first, on a disjoint sample a quarter of the step
+        tune = {"tuned": False}
+        if args.tune:
+            ts = max(1, B // 4)
+            tsyn = torch.from_numpy(D.sample(dm, ts, w["seed"] + 777 + 1000 * rank)[0].view(np.int32)).to(dev)
+            t0 = time.time()
+            dec.autotune(tsyn)
+            tune = {"tuned": True, "sample_shots": ts, "seconds": time.time() - t0}
+            del tsyn
+        tune["chosen"] = dec.launch()
+        tune["engine"] = "image" if tune["chosen"]["engines"] == 1 else "summary"
         out = None
         cnt = torch.zeros(8, dtype=torch.int64, device=dev)
         for _ in range(args.warmup):
@@ -618,7 +646,8 @@ def run_vibe(args):
         ms = r["prof"]["bp_ms"] / max(1, r["prof"]["bp_launches"])
         image = r["tune"]["engine"] == "image"
         kname = "k_bp (image engine)" if image else "k_bpx (summary engine)"
-        entry = hbm_roofline(kname, WORKLOAD, label, sweeps, E, b, B, io, ms, hbm_peak, peak_src)
+        entry = hbm_roofline(kname, WORKLOAD, label, sweeps, E, b, B, io, ms, hbm_peak, peak_src,
+                             traffic=profiled_traffic("k_bp" if image else "k_bpx", label, B, sweeps))
         entry["launch"] = r["tune"]["chosen"]
         if image:
             # shared-memory view: each column update scans the whole padded row of each of its checks
@@ -634,11 +663,12 @@ def run_vibe(args):
                                       r["prof"]["lsd_ms"] / max(1, r["prof"]["lsd_launches"]),
                                       int(r["counters"][2]) // args.steps))
     main_rl = dict(rooflines[0])
-    main_rl.pop("smem_row_scans", None)
     main_rl["kernel"] = rooflines[0]["kernel"].replace("(", "(persistent BP ensemble, ")
+    main_rl["metric"] = "algorithmic_bytes_over_hbm_copy_bw"
     main_rl["what"] = ("algorithmic message bytes (2*E*4 per executed sweep plus per-shot I/O) over the measured HBM "
-                       "copy bandwidth; the messages live in shared memory, so DRAM carries only the I/O (traffic) "
-                       "and rooflines[0].smem_row_scans gives the shared-memory view")
+                       "copy bandwidth; the messages live in shared memory, so DRAM carries only the I/O (traffic, "
+                       "from the ncu capture scaled per shot) and smem_row_scans gives the shared-memory view, the "
+                       "kernel's real bound")
     main_rl["lsd_kernel_ms"] = r32["prof"]["lsd_ms"] / max(1, r32["prof"]["lsd_launches"])
     lat, lat16 = r32["step_ms"], r16["step_ms"]
 
@@ -655,9 +685,10 @@ def run_vibe(args):
                  "latency_ms": {"p50": pct(lat16, 0.5), "p99": pct(lat16, 0.99)},
                  "ler": ler_ci(f16_fail, B), "corrections_differ_vs_f32": differ / B},
         "ler": ler_ci(f32_fail, B),
-        "autotune": {"f32": r32["tune"], "f16": r16["tune"],
-                     "knobs": "BP engine (image/summary), shot/pair mode (warps per shot: 1 or K), BP persistent "
-                              "grid, LSD threads per CTA (64/128/256) and LSD grid; results do not depend on them"},
+        "launch": {"f32": r32["tune"], "f16": r16["tune"],
+                   "note": "without --tune: the launch vibe_create sizes (occupancy-maximal grid, one warp per "
+                           "shot); --tune searches BP engine, shot/pair mode, BP grid, LSD CTA size and grid on "
+                           "a quarter-size sample (results do not depend on them)"},
         "lsd_fraction": int(r32["counters"][2]) / (B * args.steps),
         "pair_iters_per_shot": int(r32["counters"][3]) / (B * args.steps),
         "roofline": main_rl,
@@ -708,6 +739,8 @@ def main():
     ap.add_argument("--legs", default="all", help="all, none, or a comma list of circuit_d11,mixed,service")
     ap.add_argument("--case", default="", help="run one named profiling case and exit")
     ap.add_argument("--pair-mode", action="store_true", help="--case: one warp per (shot, member) pair")
+    ap.add_argument("--tune", action="store_true",
+                    help="run the launch search on a sample before timing the headline workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

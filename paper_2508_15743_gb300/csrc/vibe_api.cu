@@ -135,7 +135,7 @@ struct Workspace {
   }
   int ensure(const Launch& L, long long need, bool soft) {
     const long long ps = L.pair_mode ? std::min(need, L.pair_chunk(soft)) : 0;
-    const long long want = std::min(L.pair_mode ? ps : need, chunk_max);
+    const long long want = std::min(need, chunk_max);
     const int warps = L.bp_grid() * vibe::kBpWarpsPerCta;
     const long long xb = (long long)L.bpx_grid() * vibe::kBpxWarpsPerCta * L.bpx_pitch(soft);
     const bool pair_ok = !L.pair_mode || (ps <= pair_shots && (!soft || pair_soft) && L.bnd.K * L.bnd.nw <= pk_nw &&
@@ -213,71 +213,90 @@ struct Batch {
   unsigned long long* counters;
 };
 
+// Decodes q in chunks of up to ws.chunk shots (the LSD hand-off space): the BP kernels over the chunk,
+// then one LSD launch over the shots they queued. In pair mode the BP part of a chunk runs in
+// sub-chunks of up to ws.pair_shots shots (the member records), all queueing into the chunk's LSD
+// launch, so a chunk's slowest LSD shots are waited for once, not once per sub-chunk.
 int run_decode(const Launch& L, Workspace& ws, Profiler& prof, const Batch& q, cudaStream_t s) {
   int rc = ws.ensure(L, q.B, q.soft != nullptr);
   if (rc != VIBE_OK) return rc;
-  const long long step = L.pair_mode ? std::min(ws.chunk, ws.pair_shots) : ws.chunk;
+  const long long step = ws.chunk;
   for (long long b0 = 0; b0 < q.B; b0 += step) {
     const long long nb = std::min(step, q.B - b0);
     VIBE_CUDA(cudaMemsetAsync(ws.ctrl, 0, 8 * sizeof(unsigned int), s), "decode");
-    if (L.pair_mode) {
-      VIBE_CUDA(cudaMemsetAsync(ws.pconv, 0, sizeof(int) * (size_t)nb * L.bnd.K, s), "decode");
-      VIBE_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(unsigned int) * (size_t)nb, s), "decode");
-    }
-    vibe::BpArgs a{};
-    a.one = L.one;
-    a.dems = L.d_desc; a.ndem = L.ndem; a.dem_of_shot = q.dem_of_shot ? q.dem_of_shot + b0 : nullptr;
-    a.bnd = L.bnd;
-    a.want_soft = q.soft != nullptr;
-    a.syn = q.syn + (size_t)b0 * q.syn_stride; a.syn_stride = q.syn_stride;
-    a.nshots = (uint32_t)nb;
-    a.corr = q.corr + (size_t)b0 * q.corr_stride; a.corr_stride = q.corr_stride;
-    a.logical = q.logical ? q.logical + (size_t)b0 * q.log_stride : nullptr; a.log_stride = q.log_stride;
-    a.stats = q.stats ? q.stats + b0 : nullptr;
-    a.soft = q.soft ? q.soft + (size_t)b0 * q.soft_stride : nullptr; a.soft_stride = q.soft_stride;
-    a.obs = q.obs ? q.obs + (size_t)b0 * q.log_stride : nullptr;
-    a.counters = q.counters;
-    a.next_shot = ws.ctrl; a.lsd_count = ws.ctrl + 1; a.lsd_shots = ws.lsd_shots; a.lsd_soft = ws.lsd_soft;
-    a.scratch = ws.bp_scratch;
-    a.scratch_pitch = (long long)(2 + L.bnd.M) * L.bnd.n;
-    a.xscratch = ws.bpx_scratch;
-    a.xscratch_pitch = L.bpx_pitch(a.want_soft != 0);
-    a.next_shot_x = ws.ctrl + 3;
-    a.pair_mode = L.pair_mode;
-    a.pair_K = L.bnd.K;
-    a.pconv = ws.pconv; a.pW = ws.pW; a.pbits = ws.pbits; a.pterms = ws.pterms; a.ppost = ws.ppost;
-    a.pdone = ws.pdone;
-    a.next_pair = ws.ctrl + 4;
-    a.next_pair_x = ws.ctrl + 5;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (prof.on) { e0 = prof.next(); e1 = prof.next(); e2 = prof.next(); }
     if (e0) cudaEventRecord(e0, s);
-    const long long units = L.pair_mode ? nb * L.bnd.K : nb;   // shots, or (shot, member) pairs
-    if (L.warp_engine()) {
-      const int grid = (int)std::min<long long>(L.bp_grid(), (units + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
-      a.flag_bad = 1;
-      VIBE_CUDA(vibe::launch_bp(a, L.msg_fp16, grid, s), "BP kernel launch");
-    }
-    if (L.cta_engine()) {
-      const int grid = (int)std::min<long long>(L.bpx_grid(), (units + vibe::kBpxWarpsPerCta - 1) / vibe::kBpxWarpsPerCta);
-      a.flag_bad = L.warp_engine() ? 0 : 1;
-      VIBE_CUDA(vibe::launch_bpx(a, L.msg_fp16, grid, s), "BP kernel launch");
+    const long long sub = L.pair_mode ? std::min(nb, ws.pair_shots) : nb;
+    for (long long s0 = 0; s0 < nb; s0 += sub) {
+      const long long ns = std::min(sub, nb - s0);
+      const long long o = b0 + s0;
+      if (s0 > 0) {   // the BP work counters start again; the LSD queue keeps filling
+        VIBE_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(unsigned int), s), "decode");
+        VIBE_CUDA(cudaMemsetAsync(ws.ctrl + 3, 0, 3 * sizeof(unsigned int), s), "decode");
+      }
+      if (L.pair_mode) {
+        VIBE_CUDA(cudaMemsetAsync(ws.pconv, 0, sizeof(int) * (size_t)ns * L.bnd.K, s), "decode");
+        VIBE_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(unsigned int) * (size_t)ns, s), "decode");
+      }
+      vibe::BpArgs a{};
+      a.one = L.one;
+      a.dems = L.d_desc; a.ndem = L.ndem; a.dem_of_shot = q.dem_of_shot ? q.dem_of_shot + o : nullptr;
+      a.bnd = L.bnd;
+      a.want_soft = q.soft != nullptr;
+      a.syn = q.syn + (size_t)o * q.syn_stride; a.syn_stride = q.syn_stride;
+      a.nshots = (uint32_t)ns;
+      a.corr = q.corr + (size_t)o * q.corr_stride; a.corr_stride = q.corr_stride;
+      a.logical = q.logical ? q.logical + (size_t)o * q.log_stride : nullptr; a.log_stride = q.log_stride;
+      a.stats = q.stats ? q.stats + o : nullptr;
+      a.soft = q.soft ? q.soft + (size_t)o * q.soft_stride : nullptr; a.soft_stride = q.soft_stride;
+      a.obs = q.obs ? q.obs + (size_t)o * q.log_stride : nullptr;
+      a.counters = q.counters;
+      a.next_shot = ws.ctrl; a.lsd_count = ws.ctrl + 1; a.lsd_shots = ws.lsd_shots; a.lsd_soft = ws.lsd_soft;
+      a.lsd_shot_base = (uint32_t)s0;
+      a.scratch = ws.bp_scratch;
+      a.scratch_pitch = (long long)(2 + L.bnd.M) * L.bnd.n;
+      a.xscratch = ws.bpx_scratch;
+      a.xscratch_pitch = L.bpx_pitch(a.want_soft != 0);
+      a.next_shot_x = ws.ctrl + 3;
+      a.pair_mode = L.pair_mode;
+      a.pair_K = L.bnd.K;
+      a.pconv = ws.pconv; a.pW = ws.pW; a.pbits = ws.pbits; a.pterms = ws.pterms; a.ppost = ws.ppost;
+      a.pdone = ws.pdone;
+      a.next_pair = ws.ctrl + 4;
+      a.next_pair_x = ws.ctrl + 5;
+      const long long units = L.pair_mode ? ns * L.bnd.K : ns;   // shots, or (shot, member) pairs
+      if (L.warp_engine()) {
+        const int grid =
+            (int)std::min<long long>(L.bp_grid(), (units + vibe::kBpWarpsPerCta - 1) / vibe::kBpWarpsPerCta);
+        a.flag_bad = 1;
+        VIBE_CUDA(vibe::launch_bp(a, L.msg_fp16, grid, s), "BP kernel launch");
+      }
+      if (L.cta_engine()) {
+        const int grid =
+            (int)std::min<long long>(L.bpx_grid(), (units + vibe::kBpxWarpsPerCta - 1) / vibe::kBpxWarpsPerCta);
+        a.flag_bad = L.warp_engine() ? 0 : 1;
+        VIBE_CUDA(vibe::launch_bpx(a, L.msg_fp16, grid, s), "BP kernel launch");
+      }
+      prof.bp_launches++;
     }
     if (e1) cudaEventRecord(e1, s);
     vibe::LsdArgs l{};
-    l.dems = L.d_desc; l.ndem = L.ndem; l.dem_of_shot = a.dem_of_shot; l.bnd = L.bnd;
-    l.want_soft = a.want_soft;
-    l.syn = a.syn; l.syn_stride = q.syn_stride;
-    l.corr = a.corr; l.corr_stride = q.corr_stride;
-    l.logical = a.logical; l.log_stride = q.log_stride;
-    l.stats = a.stats; l.soft = a.soft; l.soft_stride = q.soft_stride; l.obs = a.obs;
+    l.dems = L.d_desc; l.ndem = L.ndem; l.dem_of_shot = q.dem_of_shot ? q.dem_of_shot + b0 : nullptr;
+    l.bnd = L.bnd;
+    l.want_soft = q.soft != nullptr;
+    l.syn = q.syn + (size_t)b0 * q.syn_stride; l.syn_stride = q.syn_stride;
+    l.corr = q.corr + (size_t)b0 * q.corr_stride; l.corr_stride = q.corr_stride;
+    l.logical = q.logical ? q.logical + (size_t)b0 * q.log_stride : nullptr; l.log_stride = q.log_stride;
+    l.stats = q.stats ? q.stats + b0 : nullptr;
+    l.soft = q.soft ? q.soft + (size_t)b0 * q.soft_stride : nullptr; l.soft_stride = q.soft_stride;
+    l.obs = q.obs ? q.obs + (size_t)b0 * q.log_stride : nullptr;
     l.counters = q.counters;
     l.lsd_count = ws.ctrl + 1; l.lsd_shots = ws.lsd_shots; l.lsd_soft = ws.lsd_soft; l.lsd_next = ws.ctrl + 2;
     l.scratch = ws.lsd_scratch;
     l.scratch_pitch = vibe::lsd_scratch_words(L.bnd, L.lsd_threads);
     VIBE_CUDA(vibe::launch_lsd(l, L.lsd_grid(), L.lsd_threads, s), "LSD kernel launch");
     if (e2) cudaEventRecord(e2, s);
-    prof.bp_launches++;
     prof.lsd_launches++;
   }
   return VIBE_OK;

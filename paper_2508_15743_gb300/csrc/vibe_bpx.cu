@@ -743,7 +743,7 @@ __device__ __forceinline__ void decode_shot_x(const BpArgs& a, const Tables& t, 
     uint32_t q = 0;
     if (lane == 0) q = atomicAdd(a.lsd_count, 1u);
     q = __shfl_sync(kFull, q, 0);
-    if (lane == 0) a.lsd_shots[q] = shot;
+    if (lane == 0) a.lsd_shots[q] = a.lsd_shot_base + shot;
     float* dst = a.lsd_soft + (size_t)q * a.bnd.n;
     const float kf = (float)K;
     for (int v = lane; v < n; v += 32) dst[v] = __fdiv_rn(acc[v], kf);

@@ -123,8 +123,9 @@ struct BpArgs {
   // work distribution and hand-off to LSD
   unsigned int* next_shot;
   unsigned int* lsd_count;
-  uint32_t* lsd_shots;
+  uint32_t* lsd_shots;         // queued shots, as lsd_shot_base + the shot's index in this launch
   float* lsd_soft;             // pitch bnd.n floats per queued shot
+  uint32_t lsd_shot_base;      // this launch's first shot within the LSD launch that follows
   // image engine, per-warp global scratch: n floats (LLR accumulator), n floats (posterior), M*n floats
   // (candidate posteriors, only with want_soft); pitch in floats
   float* scratch;
@@ -300,7 +301,7 @@ __device__ inline bool pair_epilogue(const BpArgs& a, const Tables& t, uint32_t 
     uint32_t q = 0;
     if (lane == 0) q = atomicAdd(a.lsd_count, 1u);
     q = __shfl_sync(kFull, q, 0);
-    if (lane == 0) a.lsd_shots[q] = shot;
+    if (lane == 0) a.lsd_shots[q] = a.lsd_shot_base + shot;
     float* dst = a.lsd_soft + (size_t)q * a.bnd.n;
     const float kf = (float)K;
     const float* terms = a.pterms + (size_t)slot * a.pair_K * a.bnd.n;
