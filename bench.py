@@ -9,7 +9,7 @@ The JSON line's headline (`value`) is the d=9 colour-code phenomenological workl
 perfect round, p = q = 0.01; m = 300, n = 819; K = 16 seeded schedules, T = 30, M = 5, LSD-0),
 10^6 shots per step, with FP16 messages, end-to-end host-buffer throughput, the CPU oracle timed on
 the host cores, and the FP64-oracle logical error rate beside it (the launch vibe_create sizes;
---tune runs the launch search first). Three more legs ride on the same
+--tune runs the launch search first). Four more legs ride on the same
 line (skip them with --legs none):
 
   circuit_d11   the circuit-level d=11 colour code (11 rounds, Si1000 noise at p = 1e-3; m = 990,
@@ -23,7 +23,9 @@ line (skip them with --legs none):
   service       the streaming service (Poisson arrivals, 8 GB budget): per-request p50/p99/p99.9
                 latency in shot mode and in pair mode (one warp per (shot, member) pair) for the
                 headline problem at 200,000 requests/s and for the circuit-level d=9 + d=13 mix at
-                2*10^6 requests/s (saturating one GPU) and at 20 requests/s.
+                2*10^6 requests/s (saturating one GPU) and at 20 requests/s;
+  tiling488     the square-octagon (4.8.8) colour code at d=9 under the headline's noise and decoder,
+                10^5 shots with FP32 and with FP16 messages.
 
 Every leg carries a roofline for its kernels (`rooflines`): the BP kernels against the measured HBM
 copy bandwidth in algorithmic bytes (2*E*b per executed sweep plus per-shot I/O), the image
@@ -447,6 +449,37 @@ def mixed_leg(V, dev, peaks, peak_src):
     return leg, []
 
 
+def tiling488_leg(V, dev, peaks, peak_src):
+    """The square-octagon (4.8.8) colour code at d=9 under the headline's noise (9 noisy + 1 perfect
+    phenomenological rounds, p = q = 0.01) and decoder (K=16, T=30, M=5): 10^5 shots per precision."""
+    w = D.WORKLOADS["cc488_d9_pheno"]
+    dm = D.build_workload("cc488_d9_pheno")
+    B = w["shots"]
+    syn, obs = D.sample(dm, B, w["seed"])
+    perms = D.schedules(dm.n, w["K"], w["seed"])
+    import torch
+    syn_d = torch.from_numpy(syn.view(np.int32)).to(dev)
+    obs_d = torch.from_numpy(obs.view(np.int32)).to(dev)
+    leg = {"workload": f"cc488_d9_pheno: d=9 4.8.8 colour code (n=49 qubits, 24 plaquettes of weight 4 and 8), "
+                       f"9 noisy + 1 perfect phenomenological rounds, p=q=0.01, m={dm.m}, n={dm.n}, E={dm.H.nnz}; "
+                       f"K=16, T=30, M=5, LSD-0; {B} shots per precision (seed {w['seed']})"}
+    rl, outs = [], {}
+    for label, fp16 in [("f32", False), ("f16", True)]:
+        dec = V.Decoder(dm, w["K"], perms, T=w["T"], alpha=w["alpha"], M=w["M"], msg_fp16=fp16)
+        ms, c, prof, out = timed_decode(V, dec, syn_d, obs_d, dev)
+        outs[label] = out["corrections"].clone()
+        sweeps = int(c[V.CNT_PAIR_ITERS])
+        leg[label] = {"value": B / (sum(ms) / 1000.0), "ms_per_step": statistics.mean(ms),
+                      "ler": ler_ci(int(c[V.CNT_FAILURES]), B), "lsd_fraction": int(c[V.CNT_LSD]) / B,
+                      "sweeps_per_shot": sweeps / B, "launch": dec.launch()}
+        engine = "k_bp (image engine)" if dec.launch()["engines"] == 1 else "k_bpx (summary engine)"
+        rl.append(hbm_roofline(engine, "cc488_d9_pheno", label, sweeps, dm.H.nnz, 2 if fp16 else 4, B,
+                               io_bytes_per_shot(dm), prof["bp_ms"], float(peaks.get("hbm_gbs", 6800.0)), peak_src))
+        dec.close()
+    leg["f16"]["corrections_differ_vs_f32"] = int((outs["f16"] != outs["f32"]).any(dim=1).sum().item()) / B
+    return leg, rl
+
+
 def service_leg(V):
     """Streaming service (Poisson arrivals, 8 GB device-memory budget), per-request latency in shot mode
     and in pair mode: the headline problem at 200,000 requests/s; config 5's circuit-level d=9 + d=13
@@ -494,6 +527,9 @@ def run_case(args):
                    100_000, 5),
         "xyz_d7": (lambda: C.circuit_dem(7, 7, 1e-3, noise="si1000", basis="X", schedule="xyz"), 16, 30, 5, False,
                    30_000, 7),
+        # the square-octagon (4.8.8) colour code under the headline's phenomenological noise and decoder
+        "pheno488_d9": (lambda: D.build_workload("cc488_d9_pheno"), 16, 30, 5, False, 100_000, 2),
+        "pheno488_d9_fp16": (lambda: D.build_workload("cc488_d9_pheno"), 16, 30, 5, True, 100_000, 2),
         # the X/Z circuit with the same sizes, rounds, noise and decoder, for comparison
         "xz_d5": (lambda: C.circuit_dem(5, 7, 1e-3, noise="si1000", basis="X"), 16, 30, 5, False, 100_000, 5),
         "xz_d7": (lambda: C.circuit_dem(7, 7, 1e-3, noise="si1000", basis="X"), 16, 30, 5, False, 30_000, 7),
@@ -710,7 +746,7 @@ def run_vibe(args):
                                        fp32_inside_two_sigma=bool(ref64["two_sigma"][0] <= line["ler"]["ler"]
                                                                   <= ref64["two_sigma"][1]))
     if rank == 0 and args.legs != "none":
-        legs = args.legs.split(",") if args.legs != "all" else ["circuit_d11", "mixed", "service"]
+        legs = args.legs.split(",") if args.legs != "all" else ["circuit_d11", "mixed", "service", "tiling488"]
         if "circuit_d11" in legs:
             leg, rl = circuit_leg(V, dev, peaks, peak_src, cpu=world == 1 and not args.no_cpu_baseline)
             line["circuit_d11"] = leg
@@ -720,6 +756,13 @@ def run_vibe(args):
             line["mixed"] = leg
         if "service" in legs:
             line["service"] = service_leg(V)
+        if "tiling488" in legs:
+            try:
+                leg, rl = tiling488_leg(V, dev, peaks, peak_src)
+                line["tiling488"] = leg
+                line["rooflines"] += rl
+            except Exception as exc:   # a failed side leg must not cost the headline line
+                line["tiling488"] = {"error": repr(exc)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -736,7 +779,8 @@ def main():
     ap.add_argument("--impl", default="vibe", choices=["vibe", "reference"])
     ap.add_argument("--shots", type=int, default=0, help="override shots per GPU (default: the workload's 10^6)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="all", help="all, none, or a comma list of circuit_d11,mixed,service")
+    ap.add_argument("--legs", default="all",
+                    help="all, none, or a comma list of circuit_d11,mixed,service,tiling488")
     ap.add_argument("--case", default="", help="run one named profiling case and exit")
     ap.add_argument("--pair-mode", action="store_true", help="--case: one warp per (shot, member) pair")
     ap.add_argument("--tune", action="store_true",

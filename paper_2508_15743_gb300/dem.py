@@ -132,15 +132,166 @@ def color_code_666(d: int):
     return H, np.asarray(logical, dtype=np.int32), qubits
 
 
-def code_capacity_dem(d: int, p: float) -> DEM:
-    """Code-capacity bit-flip model on the d colour code: H = plaquette incidence, L = boundary logical."""
-    H, logical, _ = color_code_666(d)
+# --------------------------------------------------------------------------------------------
+# Triangular 4.8.8 (square-octagon) colour code (Sec. II.A)
+# --------------------------------------------------------------------------------------------
+#
+# Built on the dual lattice, where the construction is a closed lattice path. The dual of the
+# square-octagon tiling is the square lattice with both diagonals of every cell drawn: an octagon is a
+# lattice point, a square is a cell centre, and each cell splits into four triangles, one per vertex
+# of the tiling (a qubit). Coordinates are doubled so that all of them are integers: octagons at
+# (2a, 2b), squares at (2a+1, 2b+1). Octagons are red when a + b is even and blue otherwise, squares
+# green; the three colours are those of the plaquettes.
+#
+# A colour code with three boundaries is such a triangulated region with one extra "boundary vertex"
+# per boundary, joined to every lattice point along its stretch of the region's boundary: a boundary
+# stretch whose points carry two of the colours belongs to the third colour's boundary vertex. The
+# qubits are the region's triangles (bulk qubits, in three plaquettes), one triangle per boundary edge
+# (boundary qubits, in two) and one triangle at each of the three points where two stretches meet
+# (corner qubits, in one). A plaquette is every qubit around its lattice point.
+#
+# The region of the distance-d code is bounded by a counterclockwise cycle of 3(d-2) lattice edges
+# starting at the square centre (1, 1):
+#   1. d-2 half-diagonal steps eastward in a zigzag through blue octagons at heights 0 and 2 (turning
+#      north-east at height 0 and south-east at height 2, straight on through squares);
+#   2. d-2 axis steps of a staircase through octagons, alternately west and north (west first when
+#      the zigzag ended at height 2 mod 4, north first otherwise);
+#   3. d-2 half-diagonal steps southward in a zigzag through red octagons at x = 0 and 2 (turning
+#      south-east at x = 0 and south-west at x = 2) back to (1, 1).
+# The region is made of the triangles the cycle winds around once; where the staircase touches a
+# zigzag the region is pinched to a single point. Every octagon the cycle turns at holds either 90
+# degrees of region (a weight-4 half octagon on the boundary) or 270 degrees (a whole octagon), and
+# every square it passes straight through holds 180 degrees (a weight-4 square), so the plaquettes
+# are quadrilaterals on the boundary and squares or octagons in the bulk. The result has
+# n = (d^2 + 2d - 1)/2 qubits and (n - 1)/2 plaquettes of weight 4 or 8; tests/test_inputs.py pins
+# the code parameters and the distance.
+
+def _dual_cycle_488(d: int):
+    steps = d - 2
+    cyc = [(1, 1)]
+    x, y = 1, 1
+    dx, dy = 1, -1
+    for _ in range(steps):                       # 1. zigzag east
+        if x % 2 == 0:
+            dx, dy = (1, 1) if y == 0 else (1, -1)
+        x, y = x + dx, y + dy
+        cyc.append((x, y))
+    west = (y % 4) == 2
+    for _ in range(steps):                       # 2. staircase
+        x, y = (x - 2, y) if west else (x, y + 2)
+        west = not west
+        cyc.append((x, y))
+    for _ in range(steps):                       # 3. zigzag south
+        if x % 2 == 0:
+            dx, dy = (1, -1) if x == 0 else (-1, -1)
+        x, y = x + dx, y + dy
+        cyc.append((x, y))
+    if cyc[-1] != (1, 1):
+        raise AssertionError("boundary cycle does not close")
+    return cyc[:-1]
+
+
+def _dual_colour(pt) -> int:
+    """0 red octagon, 1 blue octagon, 2 green square."""
+    if pt[0] % 2:
+        return 2
+    return (pt[0] // 2 + pt[1] // 2) % 2
+
+
+def _winding(cyc, px: float, py: float) -> int:
+    w = 0
+    for k in range(len(cyc)):
+        (x1, y1), (x2, y2) = cyc[k], cyc[(k + 1) % len(cyc)]
+        if (y1 <= py < y2) or (y2 <= py < y1):
+            if x1 + (py - y1) * (x2 - x1) / (y2 - y1) > px:
+                w += 1 if y2 > y1 else -1
+    return w
+
+
+def color_code_488(d: int):
+    """Triangular square-octagon colour code of odd distance d (construction in the comment above).
+
+    Returns (H, L_support, coords, colours): H the plaquette/qubit incidence as a CSR, L_support the
+    sorted qubit indices of a weight-d boundary logical (the qubits along the eastward zigzag, corners
+    included), coords the dual-lattice position of each qubit (its triangle's centroid; a boundary
+    qubit sits on its boundary edge, a corner qubit on its corner point), colours the plaquettes'
+    colours (0 red, 1 blue, 2 green).
+    """
+    if d < 3 or d % 2 == 0:
+        raise ValueError("distance must be odd and >= 3")
+    cyc = _dual_cycle_488(d)
+    F = len(cyc)
+    xs = [p[0] for p in cyc]
+    ys = [p[1] for p in cyc]
+    qubit_pos, qubit_pts = [], []                 # position, lattice points the qubit touches
+    for a in range(min(xs) // 2 - 1, max(xs) // 2 + 1):
+        for b in range(min(ys) // 2 - 1, max(ys) // 2 + 1):
+            c = (2 * a + 1, 2 * b + 1)
+            corners = [(2 * a, 2 * b), (2 * a + 2, 2 * b), (2 * a + 2, 2 * b + 2), (2 * a, 2 * b + 2)]
+            for i in range(4):
+                tri = (c, corners[i], corners[(i + 1) % 4])
+                cx = sum(t[0] for t in tri) / 3.0
+                cy = sum(t[1] for t in tri) / 3.0
+                w = _winding(cyc, cx, cy)
+                if w == 1:
+                    qubit_pos.append((cx, cy))
+                    qubit_pts.append(tri)
+                elif w != 0:
+                    raise AssertionError("boundary cycle winds twice")
+    # a boundary stretch is named by the colour its edges lack
+    lack = [3 - _dual_colour(cyc[k]) - _dual_colour(cyc[(k + 1) % F]) for k in range(F)]
+    edge_qubit = []
+    for k in range(F):
+        u, v = cyc[k], cyc[(k + 1) % F]
+        edge_qubit.append(len(qubit_pos))
+        qubit_pos.append(((u[0] + v[0]) / 2.0, (u[1] + v[1]) / 2.0))
+        qubit_pts.append((u, v))
+    corner_qubit = {}
+    for k in range(F):
+        if lack[k] != lack[(k + 1) % F]:
+            v = cyc[(k + 1) % F]
+            corner_qubit[k] = len(qubit_pos)
+            qubit_pos.append((float(v[0]), float(v[1])))
+            qubit_pts.append((v,))
+    if len(corner_qubit) != 3:
+        raise AssertionError("expected three boundary stretches")
+    # qubits in (y, x) order, plaquettes in (y, x) order of their lattice points
+    order = sorted(range(len(qubit_pos)), key=lambda q: (qubit_pos[q][1], qubit_pos[q][0]))
+    new = {q: i for i, q in enumerate(order)}
+    members = {}
+    for q, pts in enumerate(qubit_pts):
+        for pt in pts:
+            members.setdefault(pt, []).append(new[q])
+    plaq_pts = sorted(members, key=lambda pt: (pt[1], pt[0]))
+    H = CSR.from_rows([members[pt] for pt in plaq_pts], len(order))
+    steps = d - 2
+    logical = [new[edge_qubit[k]] for k in range(steps)]          # the eastward zigzag's edges
+    logical += [new[corner_qubit[F - 1]], new[corner_qubit[steps - 1]]]   # its two corners
+    coords = [qubit_pos[q] for q in order]
+    colours = np.asarray([_dual_colour(pt) for pt in plaq_pts], dtype=np.int8)
+    return H, np.asarray(sorted(logical), dtype=np.int32), coords, colours
+
+
+def _color_code(d: int, tiling: str):
+    if tiling == "666":
+        H, logical, _ = color_code_666(d)
+    elif tiling == "488":
+        H, logical, _, _ = color_code_488(d)
+    else:
+        raise ValueError("tiling must be '666' or '488'")
+    return H, logical
+
+
+def code_capacity_dem(d: int, p: float, tiling: str = "666") -> DEM:
+    """Code-capacity bit-flip model on the d colour code (hexagonal '666' or square-octagon '488'
+    tiling): H = plaquette incidence, L = boundary logical."""
+    H, logical = _color_code(d, tiling)
     L = CSR.from_rows([logical], H.ncols)
     priors = np.full(H.ncols, float(p), dtype=np.float64)
-    return DEM(H, L, priors, name=f"cc666_d{d}_codecap_p{p}", meta={"d": d, "p": p})
+    return DEM(H, L, priors, name=f"cc{tiling}_d{d}_codecap_p{p}", meta={"d": d, "p": p, "tiling": tiling})
 
 
-def phenomenological_dem(d: int, noisy_rounds: int, p: float, q: float) -> DEM:
+def phenomenological_dem(d: int, noisy_rounds: int, p: float, q: float, tiling: str = "666") -> DEM:
     """Phenomenological noise over `noisy_rounds` noisy rounds plus one perfect round.
 
     Rounds r = 0..R-1 with R = noisy_rounds + 1; the last one is perfect. Detector (P, r) is the XOR of
@@ -149,8 +300,9 @@ def phenomenological_dem(d: int, noisy_rounds: int, p: float, q: float) -> DEM:
     round's outcome of P flips with probability q: column (P, r) hits detectors (P, r) and (P, r+1).
     The observable is the boundary logical, flipped by data flips on its support in any round.
     Column order: all data columns (round-major, qubit-minor), then all measurement columns.
+    tiling: '666' (hexagonal) or '488' (square-octagon) colour code.
     """
-    Hc, logical, _ = color_code_666(d)
+    Hc, logical = _color_code(d, tiling)
     nq, mp = Hc.ncols, Hc.nrows
     R = noisy_rounds + 1
     qubit_plaqs = [[] for _ in range(nq)]
@@ -174,8 +326,8 @@ def phenomenological_dem(d: int, noisy_rounds: int, p: float, q: float) -> DEM:
     lcols = [r * nq + qq for r in range(noisy_rounds) for qq in range(nq) if qq in lset]
     L = CSR.from_rows([lcols], n)
     priors = np.concatenate([np.full(noisy_rounds * nq, float(p)), np.full(noisy_rounds * mp, float(q))])
-    return DEM(H, L, priors.astype(np.float64), name=f"cc666_d{d}_pheno_r{noisy_rounds}_p{p}_q{q}",
-               meta={"d": d, "rounds": noisy_rounds, "p": p, "q": q})
+    return DEM(H, L, priors.astype(np.float64), name=f"cc{tiling}_d{d}_pheno_r{noisy_rounds}_p{p}_q{q}",
+               meta={"d": d, "rounds": noisy_rounds, "p": p, "q": q, "tiling": tiling})
 
 
 # --------------------------------------------------------------------------------------------
@@ -272,13 +424,19 @@ WORKLOADS = {
     # d=9 colour code, 9 noisy + 1 perfect phenomenological rounds, p=q=0.01, K=16 random schedules.
     "cc666_d9_pheno": dict(kind="pheno", d=9, rounds=9, p=0.01, q=0.01, K=16, M=5, T=30, alpha=0.625,
                            natural=False, shots=1_000_000, seed=2),
+    # the same decoder and noise on the square-octagon colour code of the same distance
+    "cc488_d9_pheno": dict(kind="pheno", d=9, rounds=9, p=0.01, q=0.01, K=16, M=5, T=30, alpha=0.625,
+                           natural=False, shots=100_000, seed=2, tiling="488"),
+    "cc488_d5_codecap": dict(kind="codecap", d=5, p=0.05, K=1, M=1, T=20, alpha=0.625,
+                             natural=True, shots=10_000, seed=1, tiling="488"),
 }
 
 
 def build_workload(name: str) -> DEM:
     w = WORKLOADS[name]
+    tiling = w.get("tiling", "666")
     if w["kind"] == "codecap":
-        return code_capacity_dem(w["d"], w["p"])
+        return code_capacity_dem(w["d"], w["p"], tiling)
     if w["kind"] == "pheno":
-        return phenomenological_dem(w["d"], w["rounds"], w["p"], w["q"])
+        return phenomenological_dem(w["d"], w["rounds"], w["p"], w["q"], tiling)
     raise KeyError(name)

@@ -59,6 +59,19 @@ def test_single_faults_decode_to_their_logical_class(kind, K, M):
         assert np.array_equal(out["logical"], obs), mode
 
 
+@pytest.mark.parametrize("kind", ["codecap", "pheno"])
+def test_square_octagon_single_faults_decode_to_their_logical_class(kind):
+    """The same fact on the 4.8.8 colour code (distance 5): every single fault, exhaustively."""
+    dm = D.code_capacity_dem(5, 0.05, "488") if kind == "codecap" else D.phenomenological_dem(5, 3, 0.01, 0.01, "488")
+    errs = np.eye(dm.n, dtype=np.uint8)
+    syn, obs = D.syndromes_of(dm, errs)
+    for K, M in [(1, 1), (8, 3)]:
+        perms = D.schedules(dm.n, K, 8, natural=(K == 1))
+        out = oracle.decode(dm, perms, syn, 20, 0.625, M, mode=oracle.FP32)
+        assert _check_valid(dm, syn, out["corrections"])
+        assert np.array_equal(out["logical"], obs)
+
+
 def test_zero_syndrome():
     dm = D.build_workload("cc666_d9_pheno")
     syn = np.zeros((3, D.words(dm.m)), np.uint32)
