@@ -1,4 +1,4 @@
-"""Circuit-level detector error models for the 6.6.6 colour code (seeded-input side).
+"""Circuit-level detector error models for the 6.6.6 and 4.8.8 colour codes (seeded-input side).
 
 The decoding problem of circuit-level noise (Sec. II.B): columns are independent fault mechanisms of
 a syndrome-extraction circuit, rows are detectors (parities of measurement outcomes that are fixed
@@ -13,8 +13,9 @@ plaquette's ancilla:
     Z block: reset ancillas | 6 CNOT layers data -> ancilla | measure ancillas (Z basis)
     X block: reset ancillas | H ancillas | 6 CNOT layers ancilla -> data | H ancillas | measure
 CNOT layer k couples every plaquette with its neighbour in lattice direction k (the six neighbour
-offsets in counter-clockwise order), so no qubit takes part in two gates of one layer. Finally every
-data qubit is measured in basis B.
+offsets in counter-clockwise order), so no qubit takes part in two gates of one layer. On the 4.8.8
+code (dem.color_code_488) the blocks have eight CNOT layers, a proper edge colouring of the
+plaquette/qubit graph. Finally every data qubit is measured in basis B.
 
 Detectors: B-type plaquettes are deterministic from the first round (detector = outcome), the other
 type from the second (detector = XOR of consecutive outcomes); B-type plaquettes get a final detector
@@ -31,7 +32,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .dem import CSR, DEM, color_code_layout
+from .dem import CSR, DEM, color_code_488, color_code_layout
 
 # counter-clockwise lattice directions around a plaquette centre
 _DIRS = ((1, 0), (0, 1), (-1, 1), (-1, 0), (0, -1), (1, -1))
@@ -142,13 +143,65 @@ class _Builder:
         return rec, probs
 
 
+def _edge_colour_layers(sup, n):
+    """CNOT layers for plaquettes with supports `sup` over n data qubits: a proper edge colouring of
+    the bipartite plaquette/qubit graph with as many colours as the largest degree (Konig's theorem;
+    alternating-path recolouring), so that no qubit takes part in two gates of one layer. Returns one
+    list of (data qubit, plaquette) pairs per colour."""
+    deg = max(max(len(x) for x in sup), max(np.bincount([q for x in sup for q in x], minlength=n)))
+    at_p = [dict() for _ in sup]       # plaquette -> {colour: qubit}
+    at_q = [dict() for _ in range(n)]  # qubit -> {colour: plaquette}
+    for P, qs in enumerate(sup):
+        for q in qs:
+            a = next(c for c in range(deg) if c not in at_p[P])
+            b = next(c for c in range(deg) if c not in at_q[q])
+            if a in at_q[q]:
+                # swap a and b along the path q -a- P1 -b- q2 -a- ... (it cannot reach P)
+                path, node, side, col = [], q, "q", a
+                while True:
+                    nxt = (at_q[node] if side == "q" else at_p[node]).get(col)
+                    if nxt is None:
+                        break
+                    path.append((node, nxt, col) if side == "q" else (nxt, node, col))
+                    node, side, col = nxt, ("p" if side == "q" else "q"), (b if col == a else a)
+                for (qq, PP, c) in path:
+                    del at_q[qq][c]
+                    del at_p[PP][c]
+                for (qq, PP, c) in path:
+                    c2 = b if c == a else a
+                    at_q[qq][c2] = PP
+                    at_p[PP][c2] = qq
+            at_p[P][a] = q
+            at_q[q][a] = P
+    return [sorted((q, P) for P in range(len(sup)) for c, q in at_p[P].items() if c == col) for col in range(deg)]
+
+
+def _code_geometry(d, tiling):
+    """(n, plaquette supports, CNOT layers of (data, plaquette) pairs, logical support) of a tiling."""
+    if tiling == "666":
+        qubits, plaqs = color_code_layout(d)
+        qidx = {q: k for k, q in enumerate(qubits)}
+        layers = []
+        for (di, dj) in _DIRS:
+            layers.append([(qidx[(i + di, j + dj)], P) for P, (i, j) in enumerate(plaqs) if (i + di, j + dj) in qidx])
+        sup = [[qidx[(i + di, j + dj)] for (di, dj) in _DIRS if (i + di, j + dj) in qidx] for (i, j) in plaqs]
+        logical = sorted(qidx[q] for q in qubits if q[1] == -1)
+        return len(qubits), sup, layers, logical
+    if tiling == "488":
+        H, logical, _, _ = color_code_488(d)
+        sup = [H.row(P).tolist() for P in range(H.nrows)]
+        return H.ncols, sup, _edge_colour_layers(sup, H.ncols), logical.tolist()
+    raise ValueError("tiling must be '666' or '488'")
+
+
 def _unpack_rows(packed, F):
     """uint64 [r, W] -> uint8 [r, F] bits (fault f is bit f % 64 of word f // 64)."""
     by = packed.astype("<u8").view(np.uint8).reshape(packed.shape[0], -1)
     return np.unpackbits(by, axis=1, bitorder="little")[:, :F]
 
 
-def memory_circuit(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None, schedule="xz") -> dict:
+def memory_circuit(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None, schedule="xz",
+                   tiling="666") -> dict:
     """The colour-code memory circuit as a _Builder plus its detectors and observable.
 
     schedule "xz": every round measures all Z-type then all X-type plaquettes (module docstring).
@@ -159,20 +212,19 @@ def memory_circuit(d: int, rounds: int, p: float, noise="si1000", basis="X", cus
     round 0 (basis B) is deterministic on its own, round 1 (Y) is random, and the final data
     measurement is compared with the last round that measured B.
 
+    tiling: "666" (six CNOT layers in lattice directions) or "488" (the square-octagon code of
+    dem.color_code_488; its eight CNOT layers are a proper edge colouring of the plaquette/qubit
+    graph, in no geometric order).
+
     Returns dict(builder, det_meas: lists of measurement indices, det_type, obs_meas).
     """
     if schedule not in ("xz", "xyz"):
         raise ValueError(schedule)
-    qubits, plaqs = color_code_layout(d)
-    n, mp = len(qubits), len(plaqs)
-    qidx = {q: k for k, q in enumerate(qubits)}
+    n, sup, play, logical = _code_geometry(d, tiling)
+    mp = len(sup)
     anc = [n + P for P in range(mp)]
     nq = n + mp
-    layers = []
-    for (di, dj) in _DIRS:
-        layers.append([(qidx[(i + di, j + dj)], n + P) for P, (i, j) in enumerate(plaqs) if (i + di, j + dj) in qidx])
-    sup = [[qidx[(i + di, j + dj)] for (di, dj) in _DIRS if (i + di, j + dj) in qidx] for (i, j) in plaqs]
-    logical = sorted(qidx[q] for q in qubits if q[1] == -1)
+    layers = [[(q, n + P) for (q, P) in L] for L in play]
     if noise == "si1000":
         w = SI1000
     elif noise == "uniform":
@@ -295,20 +347,22 @@ def memory_circuit(d: int, rounds: int, p: float, noise="si1000", basis="X", cus
     return dict(builder=B, det_meas=det_meas, det_type=det_type, obs_meas=[kd[q] for q in logical])
 
 
-def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None, schedule="xz") -> DEM:
+def circuit_dem(d: int, rounds: int, p: float, noise="si1000", basis="X", custom=None, schedule="xz",
+                tiling="666") -> DEM:
     """Detector error model of `rounds` rounds of the colour-code memory circuit in basis X or Z.
 
     noise: "si1000", "uniform", or "custom" with `custom` a dict of per-location probabilities
     (keys data_x / data_z: flips on data before each round, meas_z / meas_x / meas_y: outcome flips
     of the plaquette measurements, final_meas: flips of the data measurement) for testing.
     schedule: "xz" (X and Z plaquettes every round) or "xyz" (one basis per round, cycling; see
-    memory_circuit).
+    memory_circuit). tiling: "666" or "488" (memory_circuit).
     """
-    circ = memory_circuit(d, rounds, p, noise, basis, custom, schedule)
+    circ = memory_circuit(d, rounds, p, noise, basis, custom, schedule, tiling)
     H, L, pcol, F, undetectable = dem_from_circuit(circ)
     tag = "" if schedule == "xz" else "_xyz"
-    return DEM(H, L, pcol, name=f"cc666_d{d}_circuit{tag}_{noise}_{basis}_r{rounds}_p{p}",
+    return DEM(H, L, pcol, name=f"cc{tiling}_d{d}_circuit{tag}_{noise}_{basis}_r{rounds}_p{p}",
                meta={"d": d, "rounds": rounds, "p": p, "noise": noise, "basis": basis, "faults": F,
+                     "tiling": tiling,
                      "schedule": schedule, "undetectable_logical_prob": undetectable,
                      "det_type": circ["det_type"]})
 

@@ -82,12 +82,14 @@ def _run(circ, rng, fault=None):
     return dets, obs
 
 
-CIRCUITS = [("xz", "X", 2), ("xz", "Z", 2), ("xyz", "X", 5), ("xyz", "Z", 4)]
+# (schedule, basis, rounds, tiling); the d=3 codes of both tilings have 7 data qubits and 3 ancillas
+CIRCUITS = [("xz", "X", 2, "666"), ("xz", "Z", 2, "666"), ("xyz", "X", 5, "666"), ("xyz", "Z", 4, "666"),
+            ("xz", "X", 2, "488"), ("xz", "Z", 2, "488"), ("xyz", "X", 5, "488")]
 
 
-@pytest.mark.parametrize("schedule,basis,rounds", CIRCUITS)
-def test_declared_detectors_are_deterministic(schedule, basis, rounds):
-    circ = C.memory_circuit(3, rounds, 1e-3, "si1000", basis, schedule=schedule)
+@pytest.mark.parametrize("schedule,basis,rounds,tiling", CIRCUITS)
+def test_declared_detectors_are_deterministic(schedule, basis, rounds, tiling):
+    circ = C.memory_circuit(3, rounds, 1e-3, "si1000", basis, schedule=schedule, tiling=tiling)
     runs = [_run(circ, np.random.default_rng(s)) for s in range(8)]
     for dets, obs in runs[1:]:
         assert np.array_equal(dets, runs[0][0])
@@ -98,9 +100,9 @@ def test_declared_detectors_are_deterministic(schedule, basis, rounds):
     assert B.nmeas > len(circ["det_meas"]) - 1
 
 
-@pytest.mark.parametrize("schedule,basis,rounds", CIRCUITS)
-def test_single_faults_flip_what_the_frames_predict(schedule, basis, rounds):
-    circ = C.memory_circuit(3, rounds, 1e-3, "si1000", basis, schedule=schedule)
+@pytest.mark.parametrize("schedule,basis,rounds,tiling", CIRCUITS)
+def test_single_faults_flip_what_the_frames_predict(schedule, basis, rounds, tiling):
+    circ = C.memory_circuit(3, rounds, 1e-3, "si1000", basis, schedule=schedule, tiling=tiling)
     B = circ["builder"]
     faults = B.fault_list()
     rec, _ = B.simulate()

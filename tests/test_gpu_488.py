@@ -53,3 +53,26 @@ def test_square_octagon_matches_oracle(V, case, engine, fp16):
     assert np.array_equal(soft.view(np.uint32), r["soft"].astype(np.float32).view(np.uint32))
     assert st["lsd_invoked"].sum() > 0 and (st["n_converged"] > 0).sum() > 0   # both paths exercised
     dec.close()
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+@pytest.mark.parametrize("engine", ["image", "summary"])
+def test_square_octagon_circuit_level_matches_oracle(V, engine, fp16):
+    """The 4.8.8 d=5 memory circuit (5 rounds, Si1000 p = 3e-3; eight edge-coloured CNOT layers)."""
+    from paper_2508_15743_gb300 import circuit as C
+    dm = C.circuit_dem(5, 5, 0.003, noise="si1000", basis="X", tiling="488")
+    syn, _ = D.sample(dm, 200, 15)
+    perms = D.schedules(dm.n, 8, 15)
+    eng = V.ENGINE_IMAGE if engine == "image" else V.ENGINE_SUMMARY
+    dec = V.Decoder(dm, 8, perms, T=20, alpha=0.625, M=3, msg_fp16=fp16, engine=eng)
+    out = dec.decode(torch.from_numpy(syn.view(np.int32)).cuda(), want_soft=True)
+    torch.cuda.synchronize()
+    r = oracle.decode(dm, perms, syn, 20, 0.625, 3, nthreads=8, mode=oracle.FP16MSG if fp16 else oracle.FP32)
+    assert np.array_equal(out["corrections"].cpu().numpy().view(np.uint32), r["corrections"])
+    assert np.array_equal(out["logical"].cpu().numpy().view(np.uint32), r["logical"])
+    st = V.stats_to_numpy(out["stats"])
+    for f in r["stats"].dtype.names:
+        assert np.array_equal(st[f], r["stats"][f]), f
+    soft = out["soft"].cpu().numpy()
+    assert np.array_equal(soft.view(np.uint32), r["soft"].astype(np.float32).view(np.uint32))
+    dec.close()

@@ -156,12 +156,13 @@ def test_schedules_are_permutations():
 from paper_2508_15743_gb300 import circuit as C  # noqa: E402
 
 
-@pytest.mark.parametrize("d,R", [(3, 2), (5, 4), (9, 9)])
-def test_circuit_builder_reproduces_phenomenological_dem(d, R):
+@pytest.mark.parametrize("d,R,tiling", [(3, 2, "666"), (5, 4, "666"), (9, 9, "666"), (3, 2, "488"), (5, 4, "488"),
+                                         (7, 3, "488")])
+def test_circuit_builder_reproduces_phenomenological_dem(d, R, tiling):
     """Z memory with only data bit flips and Z-measurement flips is the phenomenological model:
     the Pauli-frame builder must give the closed-form matrix, priors and logical, column for column."""
-    dm = C.circuit_dem(d, R, 0.0, noise="custom", basis="Z", custom=dict(data_x=0.01, meas_z=0.02))
-    ph = D.phenomenological_dem(d, R, 0.01, 0.02)
+    dm = C.circuit_dem(d, R, 0.0, noise="custom", basis="Z", custom=dict(data_x=0.01, meas_z=0.02), tiling=tiling)
+    ph = D.phenomenological_dem(d, R, 0.01, 0.02, tiling)
     rows = [i for i, t in enumerate(dm.meta["det_type"]) if t == "Z"]
     A = dm.H.to_dense()
     assert not np.delete(A, rows, axis=0).any(), "X-type detectors see no X errors"
@@ -175,9 +176,10 @@ def test_circuit_builder_reproduces_phenomenological_dem(d, R):
 
 
 @pytest.mark.parametrize("basis", ["X", "Z"])
-def test_circuit_dem_invariants(basis):
-    dm = C.circuit_dem(5, 5, 1e-3, noise="si1000", basis=basis)
-    mp = 9
+@pytest.mark.parametrize("tiling", ["666", "488"])
+def test_circuit_dem_invariants(basis, tiling):
+    dm = C.circuit_dem(5, 5, 1e-3, noise="si1000", basis=basis, tiling=tiling)
+    mp = 9 if tiling == "666" else 8
     assert dm.m == mp * 2 * 5, "B-type: 5 rounds + final; other type: rounds 2..5"
     coldeg = np.bincount(dm.H.colidx, minlength=dm.n)
     assert coldeg.min() >= 1, "every column flips a detector"
@@ -194,15 +196,17 @@ def test_circuit_dem_invariants(basis):
     assert dm.priors.sum() < 5 * 1e-3 * dm.meta["faults"]
 
 
-@pytest.mark.parametrize("schedule", ["xz", "xyz"])
-def test_circuit_single_faults_get_valid_corrections(schedule):
-    """Every single fault of a d=3 circuit DEM gets a correction with H e = s (oracle, exhaustive).
+@pytest.mark.parametrize("schedule,tiling,d", [("xz", "666", 3), ("xyz", "666", 3), ("xz", "488", 3),
+                                               ("xyz", "488", 3), ("xz", "488", 5)])
+def test_circuit_single_faults_get_valid_corrections(schedule, tiling, d):
+    """Every single fault of a small circuit DEM gets a correction with H e = s (oracle, exhaustive).
 
     The logical class is not pinned: the schedule's hook errors give pairs of single faults with the
     same syndrome and different logical effect (circuit distance 2 at d = 3), and Si1000's unequal
     priors let lighter multi-fault explanations win."""
     import oracle
-    dm = C.circuit_dem(3, 3 if schedule == "xz" else 4, 1e-3, noise="si1000", basis="X", schedule=schedule)
+    dm = C.circuit_dem(d, 3 if schedule == "xz" else 4, 1e-3, noise="si1000", basis="X", schedule=schedule,
+                       tiling=tiling)
     errs = np.eye(dm.n, dtype=np.uint8)
     syn, obs = D.syndromes_of(dm, errs)
     perms = D.schedules(dm.n, 8, 1)
@@ -214,7 +218,8 @@ def test_circuit_single_faults_get_valid_corrections(schedule):
     groups = {}
     for j in range(dm.n):
         groups.setdefault(tuple(A[:, j]), set()).add(j in set(dm.L.row(0).tolist()))
-    assert any(len(v) == 2 for v in groups.values()), "hook errors of this schedule (documented)"
+    if tiling == "666":
+        assert any(len(v) == 2 for v in groups.values()), "hook errors of this schedule (documented)"
 
 
 def test_merged_columns_take_the_odd_number_probability():

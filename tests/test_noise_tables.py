@@ -29,11 +29,13 @@ def _table():
 
 
 @pytest.mark.parametrize("noise", ["si1000", "uniform"])
-@pytest.mark.parametrize("schedule,basis,rounds", [("xz", "X", 2), ("xz", "Z", 2), ("xyz", "X", 4)])
-def test_fault_probabilities_follow_the_tables(noise, schedule, basis, rounds):
+@pytest.mark.parametrize("schedule,basis,rounds,tiling", [("xz", "X", 2, "666"), ("xz", "Z", 2, "666"),
+                                                          ("xyz", "X", 4, "666"), ("xz", "X", 2, "488"),
+                                                          ("xyz", "Z", 4, "488")])
+def test_fault_probabilities_follow_the_tables(noise, schedule, basis, rounds, tiling):
     tab = _table()
     p = 1e-3
-    circ = C.memory_circuit(3, rounds, p, noise, basis, schedule=schedule)
+    circ = C.memory_circuit(3, rounds, p, noise, basis, schedule=schedule, tiling=tiling)
     B = circ["builder"]
     mult = {op: tab[(noise, op)] for (model, op) in tab if model == noise}
     seen = set()
