@@ -530,6 +530,11 @@ def run_case(args):
         # the square-octagon (4.8.8) colour code under the headline's phenomenological noise and decoder
         "pheno488_d9": (lambda: D.build_workload("cc488_d9_pheno"), 16, 30, 5, False, 100_000, 2),
         "pheno488_d9_fp16": (lambda: D.build_workload("cc488_d9_pheno"), 16, 30, 5, True, 100_000, 2),
+        # the 4.8.8 memory circuit (edge-coloured CNOT layers), d=5 and 9, Si1000 p = 1e-3
+        "circuit488_d5": (lambda: C.circuit_dem(5, 5, 1e-3, noise="si1000", basis="X", tiling="488"), 16, 30, 5,
+                          False, 30_000, 5),
+        "circuit488_d9": (lambda: C.circuit_dem(9, 9, 1e-3, noise="si1000", basis="X", tiling="488"), 16, 30, 5,
+                          False, 10_000, 9),
         # the X/Z circuit with the same sizes, rounds, noise and decoder, for comparison
         "xz_d5": (lambda: C.circuit_dem(5, 7, 1e-3, noise="si1000", basis="X"), 16, 30, 5, False, 100_000, 5),
         "xz_d7": (lambda: C.circuit_dem(7, 7, 1e-3, noise="si1000", basis="X"), 16, 30, 5, False, 30_000, 7),
