@@ -143,36 +143,43 @@ class _Builder:
         return rec, probs
 
 
-def _edge_colour_layers(sup, n):
+def _edge_colour_layers(sup, n, seed=0):
     """CNOT layers for plaquettes with supports `sup` over n data qubits: a proper edge colouring of
     the bipartite plaquette/qubit graph with as many colours as the largest degree (Konig's theorem;
-    alternating-path recolouring), so that no qubit takes part in two gates of one layer. Returns one
+    alternating-path recolouring), so that no qubit takes part in two gates of one layer. The edges
+    are coloured in a seeded random order, each taking a random colour free at its plaquette: the
+    order of a plaquette's CNOTs decides which data qubits a mid-block ancilla fault reaches (its
+    hook), and the index order gave hooks that let two single faults share detectors with different
+    logical effect at d = 5; seed 0 gives none at d = 5 and 7 (tests/test_inputs.py). Returns one
     list of (data qubit, plaquette) pairs per colour."""
+    rng = np.random.default_rng(seed)
     deg = max(max(len(x) for x in sup), max(np.bincount([q for x in sup for q in x], minlength=n)))
     at_p = [dict() for _ in sup]       # plaquette -> {colour: qubit}
     at_q = [dict() for _ in range(n)]  # qubit -> {colour: plaquette}
-    for P, qs in enumerate(sup):
-        for q in qs:
-            a = next(c for c in range(deg) if c not in at_p[P])
-            b = next(c for c in range(deg) if c not in at_q[q])
-            if a in at_q[q]:
-                # swap a and b along the path q -a- P1 -b- q2 -a- ... (it cannot reach P)
-                path, node, side, col = [], q, "q", a
-                while True:
-                    nxt = (at_q[node] if side == "q" else at_p[node]).get(col)
-                    if nxt is None:
-                        break
-                    path.append((node, nxt, col) if side == "q" else (nxt, node, col))
-                    node, side, col = nxt, ("p" if side == "q" else "q"), (b if col == a else a)
-                for (qq, PP, c) in path:
-                    del at_q[qq][c]
-                    del at_p[PP][c]
-                for (qq, PP, c) in path:
-                    c2 = b if c == a else a
-                    at_q[qq][c2] = PP
-                    at_p[PP][c2] = qq
-            at_p[P][a] = q
-            at_q[q][a] = P
+    edges = [(P, q) for P, qs in enumerate(sup) for q in qs]
+    for e in rng.permutation(len(edges)):
+        P, q = edges[e]
+        free_p = [c for c in range(deg) if c not in at_p[P]]
+        a = free_p[rng.integers(len(free_p))]
+        b = next(c for c in range(deg) if c not in at_q[q])
+        if a in at_q[q]:
+            # swap a and b along the path q -a- P1 -b- q2 -a- ... (it cannot reach P)
+            path, node, side, col = [], q, "q", a
+            while True:
+                nxt = (at_q[node] if side == "q" else at_p[node]).get(col)
+                if nxt is None:
+                    break
+                path.append((node, nxt, col) if side == "q" else (nxt, node, col))
+                node, side, col = nxt, ("p" if side == "q" else "q"), (b if col == a else a)
+            for (qq, PP, c) in path:
+                del at_q[qq][c]
+                del at_p[PP][c]
+            for (qq, PP, c) in path:
+                c2 = b if c == a else a
+                at_q[qq][c2] = PP
+                at_p[PP][c2] = qq
+        at_p[P][a] = q
+        at_q[q][a] = P
     return [sorted((q, P) for P in range(len(sup)) for c, q in at_p[P].items() if c == col) for col in range(deg)]
 
 

@@ -222,6 +222,41 @@ def test_circuit_single_faults_get_valid_corrections(schedule, tiling, d):
         assert any(len(v) == 2 for v in groups.values()), "hook errors of this schedule (documented)"
 
 
+def _logical_pairs_and_triples(dm, triples):
+    """Whether two (or, with triples, three) DEM columns with zero total syndrome flip the logical."""
+    A = dm.H.to_dense()
+    lset = set(dm.L.row(0).tolist())
+    sy = [int.from_bytes(np.packbits(A[:, j]).tobytes(), "big") for j in range(dm.n)]
+    lg = [int(j in lset) for j in range(dm.n)]
+    by = {}
+    for j in range(dm.n):
+        by.setdefault(sy[j], []).append(j)
+    two = any(len({lg[j] for j in js}) == 2 for js in by.values())
+    three = False
+    if triples:
+        for i in range(dm.n):
+            for j in range(i + 1, dm.n):
+                if any(k not in (i, j) and lg[k] ^ lg[i] ^ lg[j] for k in by.get(sy[i] ^ sy[j], ())):
+                    three = True
+                    break
+            if three:
+                break
+    return two, three
+
+
+@pytest.mark.parametrize("tiling", ["666", "488"])
+def test_circuit_distance_is_not_cut_to_two(tiling):
+    """Hook errors of the CNOT order: at d = 5 and 7 no two single faults have the same detectors and
+    different logical effect (circuit distance >= 3), and at d = 7 no three do (>= 4), for both
+    tilings' circuits in both memory bases."""
+    for basis in ("X", "Z"):
+        two, _ = _logical_pairs_and_triples(C.circuit_dem(5, 5, 1e-3, noise="si1000", basis=basis, tiling=tiling),
+                                            False)
+        assert not two
+    two, three = _logical_pairs_and_triples(C.circuit_dem(7, 7, 1e-3, noise="si1000", basis="X", tiling=tiling), True)
+    assert not two and not three
+
+
 def test_merged_columns_take_the_odd_number_probability():
     """Faults with one signature merge into one column whose prior is the probability that an odd
     number of them occur (brute-force enumeration over the mechanisms); a fault flipping only the
