@@ -196,7 +196,9 @@ int vibe_get_layers(vibe_handle* h, int32_t* layer_of_check_out, int32_t* nlayer
  * vibe_profile -- start (enable != 0) or stop recording CUDA events around every kernel that
  * vibe_decode launches on the caller's stream; clears the totals. vibe_profile_read waits for the
  * last recorded event and returns the summed device time (ms) of the BP ensemble kernel and of the
- * LSD kernel since the last vibe_profile call, and how many of each were launched.
+ * LSD kernel since the last vibe_profile call, and how many of each were launched. A decode runs in
+ * chunks, each one LSD launch after its BP launches; in pair mode a chunk's BP part is several
+ * launches (sized by the member records), timed together as the chunk's BP time.
  */
 int vibe_profile(vibe_handle* h, int32_t enable);
 int vibe_profile_read(vibe_handle* h, double* bp_ms, double* lsd_ms, int64_t* bp_launches, int64_t* lsd_launches);
