@@ -17,6 +17,8 @@ Cases (each a JSON file named after it):
 * circuit_d13_k32_t50_fp16_lsd0 -- the d=13 member of the mixed-distance family (p = 1e-3, the
   problem the streaming workload also serves): K=32, T=50, M=7 (the larger correction limit at
   higher distance, Sec. III.D.2 step 3), FP16 messages, LSD-0; 128 seeded shots.
+* circuit_d15_k32_t20_fp16_lsd0 -- the largest problem of the mixed-distance family with its decoder
+  (d=15, p = 2e-3, K=32, T=20, M=7, FP16 messages, LSD-0); 128 seeded shots.
 
 Each file records the problem, the decoder parameters, the seeds, a SHA-256 of the syndromes (so the
 GPU test can confirm it regenerated the same inputs), and per shot: the correction as its set-bit
@@ -55,6 +57,8 @@ CASES = {
                                           rows_from="circuit_d11_k64_t50_fp32_lsd0"),
     "circuit_d13_k32_t50_fp16_lsd0": dict(d=13, p=1e-3, K=32, T=50, M=7, lsd_order=0, mode="fp16",
                                           shots=128, shot_seed=13, sched_seed=113),
+    "circuit_d15_k32_t20_fp16_lsd0": dict(d=15, p=2e-3, K=32, T=20, M=7, lsd_order=0, mode="fp16",
+                                          shots=128, shot_seed=15, sched_seed=115),
 }
 MODES = {"fp32": oracle.FP32, "fp16": oracle.FP16MSG}
 ALPHA = 0.625

@@ -10,7 +10,8 @@ its bytes: equal digests mean every one of the n floats is equal.
 
 Cases: config 3's problem and decoder (d=11 colour code, 11 rounds, Si1000 p = 1e-3, K=64, T=50, M=5)
 with FP32 messages and LSD-0, FP16 messages and LSD-0, and FP32 messages with LSD order 5 on the
-shots that reach LSD; and the d=13 problem of the mixed-distance family (K=32, T=50, M=7, FP16).
+shots that reach LSD; the d=13 problem of the mixed-distance family (K=32, T=50, M=7, FP16); and its
+d=15 problem with its decoder (p = 2e-3, K=32, T=20, M=7, FP16).
 """
 import hashlib
 import json
@@ -28,7 +29,7 @@ torch = pytest.importorskip("torch")
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 CASES = ["circuit_d11_k64_t50_fp32_lsd0", "circuit_d11_k64_t50_fp16_lsd0", "circuit_d11_k64_t50_fp32_lsd5",
-         "circuit_d13_k32_t50_fp16_lsd0"]
+         "circuit_d13_k32_t50_fp16_lsd0", "circuit_d15_k32_t20_fp16_lsd0"]
 
 
 @pytest.fixture(scope="module")
